@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Throughput of the MPCD + rigid-body time step on GB300.
+
+One step = stream + body MD, site thermalisation (Eq. 7), binning, cell sums,
+SRD collision with the cell thermostat, momentum transfer - the whole method
+of arXiv 2604.14307 Sec. II - for every solvent particle and surface site.
+
+Workload at N=1: the large suspension, L=200 (8M cells), density 10 (80M FP32
+solvent particles), phi=0.3 of radius-4 spheres (8952 colloids) discretised
+by 642-site icosphere shells (5.75M sites), SRD 130 deg with the cell-level
+thermostat, dt=0.1, in the P32 form (FP32 state, int64 fixed-point cell sums,
+FP64 bodies).  Inputs are synthetic (uniform solvent, Maxwell-Boltzmann
+velocities, RSA placement).  Under torchrun each rank simulates its own
+replica (different seed): weak scaling, no data-path collective.
+
+Metric: particle-updates/s = (N_solvent + N_sites) * steps / time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s (solvent+sites), FP32-mixed vs FP64 plain; % HBM peak"
+UNIT = "particle-updates/s"
+WORKLOAD = "suspension_L200_phi0.3_r4_642sites_density10_SRD130_thermostat"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-p64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.f.read().splitlines():
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2604_14307_gb300", "csrc", e["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return e if h == e.get("source_sha256") else None
+
+
+def cpu_baseline(steps: int = 8, L: int = 80):
+    """The FP64 oracle as it stands, one host core, on a bounded sample of the
+    workload: an L=80 box with the same density, volume fraction, colloid
+    radius and 642-site shells (5.5M particle-updates per step)."""
+    import oracle as O
+    from paper_2604_14307_gb300 import inputs as I
+    s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1, name="sample")
+    st = I.initial_state(s)
+    osys = O.OracleSystem(s)
+    ost = O.OracleState(osys, st)
+    n = s.n_solvent + s.n_sites
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.step(osys, ost, 1)
+        times.append(time.perf_counter() - t0)
+    return {"value": n / float(np.median(times)), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64-oracle step(s) of an L={L} box with the workload's density, "
+                      f"phi, radius and sites ({n} particle-updates per step), median time",
+            "seconds": float(sum(times))}
+
+
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2604_14307_gb300 import inputs as I
+    L = 60
+    s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1, name="sample")
+    st = I.initial_state(s)
+    osys = O.OracleSystem(s)
+    ost = O.OracleState(osys, st)
+    n = s.n_solvent + s.n_sites
+    O.step(osys, ost, a.warmup)
+    t0 = time.perf_counter()
+    O.step(osys, ost, a.steps)
+    dt = time.perf_counter() - t0
+    v = n * a.steps / dt
+    sample = (f"FP64 oracle, one host core, each step one step of an L={L} box with the "
+              f"workload's density, phi, radius and 642-site shells ({n} particle-updates)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_L": L},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    a = args_()
+    ws, rank, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_14307_gb300 import binding as Bd
+    from paper_2604_14307_gb300 import build_lib
+    from paper_2604_14307_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build_lib.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    L = a.L
+    system = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1 + rank,
+                          name=WORKLOAD)
+    state = I.initial_state(system)
+    n_upd = system.n_solvent + system.n_sites
+
+    sim = Bd.Simulation(system, device=local)
+    sim.set_state(state)
+    tuning = sim.tuning() if a.no_tune else sim.autotune(steps_per_trial=2)
+    sim.step(a.warmup)
+    torch.cuda.synchronize()
+    sim.set_profiling(True)
+    sim.reset_profile()
+
+    # ---------------------------------------------------------------- timed
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(a.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n_upd * a.steps * ws / (ms_max / 1e3)
+    prof = sim.profile()
+    sim.set_profiling(False)
+
+    # roofline of the dominant kernel (the fused solvent pass)
+    hbm, src = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    name, pk = dom
+    per_launch_ms = pk["total_ms"] / max(pk["launches"], 1)
+    achieved = pk["bytes_per_launch"] / (per_launch_ms / 1e3) / 1e9
+    tr = recorded_traffic(name)
+    traffic = None
+    if tr is not None:
+        traffic = float(tr["bytes_per_launch_per_particle"]) * system.n_solvent
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs copy)",
+            "bytes_per_launch": pk["bytes_per_launch"], "ms_per_launch": per_launch_ms,
+            "share_of_step": pk["total_ms"] / ms}
+    launches = a.steps + sum(v["launches"] * (5 if k == "sort" else 1) for k, v in prof.items())
+    # whole-step effective bandwidth: algorithmic bytes of every kernel / step time
+    step_bytes = sum(v["bytes_per_launch"] * v["launches"] for v in prof.values()) / a.steps
+    hbm_eff = {"bytes_per_update": step_bytes / n_upd, "gbs": step_bytes / (ms / a.steps / 1e3) / 1e9}
+    hbm_eff["frac"] = hbm_eff["gbs"] / hbm
+    kernels = {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / max(v["launches"], 1),
+                   "share": v["total_ms"] / ms} for k, v in prof.items()}
+
+    # ------------------------------------------------ end to end (host buffers)
+    hb = sim.host_buffers(pinned=True)
+    step0 = sim.get_state_buffers(hb)
+    state_bytes = sum(v.nbytes for v in hb.values())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_state_buffers(hb, step0)
+    sim.step(a.steps)
+    sim.get_state_buffers(hb)
+    diag = sim.diagnostics()
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    te_t = torch.tensor([te], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    e2e = {"value": n_upd * a.steps * ws / float(te_t.item()), "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes / a.steps, "d2h_bytes_per_step": (state_bytes + 80) / a.steps,
+           "how": "mpcd_set_state from pinned host + mpcd_step(steps) + mpcd_get_state to pinned host "
+                  "+ mpcd_diagnostics, wall clock"}
+    sim.close()
+    del hb
+
+    # ------------------------------------------------------ plain FP64 form
+    p64 = None
+    if not a.no_p64:
+        s64 = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P64, seed=1 + rank, name=WORKLOAD)
+        sim64 = Bd.Simulation(s64, device=local)
+        sim64.set_state(state)
+        k64 = max(3, a.steps // 5)
+        sim64.step(2)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        sim64.step(k64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        p64 = {"value": n_upd * k64 * ws / (ms64 / 1e3), "unit": UNIT, "steps": k64,
+               "ms_per_step": ms64 / k64, "dtype": "f64",
+               "speedup_p32_over_p64": value / (n_upd * k64 * ws / (ms64 / 1e3))}
+        sim64.close()
+    del state
+
+    cpu = None
+    if rank == 0 and not a.no_cpu:
+        cpu = cpu_baseline()
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": L, "density": 10, "phi": 0.3, "colloid_radius": 4.0,
+                       "n_solvent": system.n_solvent, "n_bodies": system.n_bodies,
+                       "n_sites": system.n_sites, "n_cells": system.n_cells,
+                       "form": "P32: FP32 state, int64 fixed-point cell sums, FP64 bodies",
+                       "rule": "SRD alpha=130 + cell-level thermostat", "dt": 0.1,
+                       "l2": "no flush: state per GPU (2.1 GB) is larger than L2 (129 MB)",
+                       "tuning": tuning, "parallelism": f"replicas x{ws} (one box per GPU)"},
+            "roofline": roof, "hbm_effective": hbm_eff, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "p64": p64, "diag_check": {"ke_solvent_per_particle": diag["ke_solvent"] / system.n_solvent},
+        }
+        print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

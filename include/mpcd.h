@@ -1,0 +1,236 @@
+/*
+ * mpcd.h - C ABI of the GB300 (sm_103a) MPCD time step with rigid-body
+ * discrete-particle colloids (Bush, Palmer, Howard, arXiv 2604.14307).
+ *
+ * One step of the method (Sec. II):
+ *   stream    solvent ballistic drift with periodic wrap (Sec. II.A) and one
+ *             velocity-Verlet step of the rigid bodies with the Miller et al.
+ *             quaternion integrator and core-shifted WCA forces (Eq. 1);
+ *   couple    PRE:  surface-site positions from each body's pose and
+ *                   thermalisation of the site velocities (Eq. 7, Sec. II.B.2);
+ *             POST: transfer of the sites' momentum change to the body
+ *                   (Eqs. 3-4) and reset of the sites to rigid motion (Eq. 5);
+ *   collide   random grid shift, cell binning, per-cell mass/momentum/energy
+ *             sums, SRD rotation (or MPCD-AT) with the cell-level thermostat
+ *             (Sec. II.A).
+ * mpcd_step() runs whole steps; it is equivalent to calling, per step,
+ * stream, couple(PRE), collide, couple(POST) in that order.
+ *
+ * Conventions
+ *   - Every call returns an mpcd_status; nothing throws across the ABI.
+ *   - The library owns all device memory of a context (through the optional
+ *     allocator).  Host buffers belong to the caller; they are only read or
+ *     written during the call that receives them.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL is the
+ *     legacy default stream).  Calls enqueue asynchronously on that stream
+ *     unless their comment says they synchronise.  Errors are sticky: after a
+ *     failure every further call on the context returns the same status until
+ *     mpcd_destroy(); mpcd_last_error() describes it.
+ *   - A context is used by one host thread at a time.
+ *   - Lengths are in units of the cell size a = 1; periodic boxes have integer
+ *     edges L (cells per edge) and positions lie in [0, L).  Quaternions are
+ *     (w, x, y, z), unit norm, body -> space.  Angular momenta are space-frame.
+ */
+#ifndef MPCD_H
+#define MPCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpcd_ctx mpcd_ctx;
+
+typedef enum {
+    MPCD_OK = 0,
+    MPCD_ERR_ARG = -1,      /* invalid argument or size; nothing was changed */
+    MPCD_ERR_CUDA = -2,     /* a CUDA runtime call failed (sticky) */
+    MPCD_ERR_OOM = -3,      /* device allocation failed */
+    MPCD_ERR_TIMEOUT = -4,  /* a bounded device wait gave up (sticky) */
+    MPCD_ERR_STATE = -5     /* the device detected an invalid state, e.g. a
+                               particle moved more than one box length in a
+                               step or a cell exceeded 65535 particles */
+} mpcd_status;
+
+enum { MPCD_P64 = 0,   /* FP64 solvent state, FP64 cell sums (plain form) */
+       MPCD_P32 = 1 }; /* FP32 solvent state, int64 fixed-point cell sums,
+                          FP64 bodies */
+enum { MPCD_SRD = 0,   /* stochastic rotation by alpha about a random axis */
+       MPCD_AT = 1 };  /* Andersen-thermostat collision (MPCD-AT) */
+enum { MPCD_PRE = 0, MPCD_POST = 1 };
+
+/* Physical and numerical parameters (Sec. II.A, Sec. III). */
+typedef struct {
+    double kT;            /* temperature of the thermostat and of Eq. 7 */
+    double dt;            /* streaming interval = MD step = collision period */
+    double alpha_deg;     /* SRD rotation angle (130 in the paper) */
+    double m_solvent;     /* solvent particle mass */
+    int32_t rule;         /* MPCD_SRD or MPCD_AT */
+    int32_t thermostat;   /* 1: cell-level thermostat for SRD (AT is intrinsically
+                             thermostatted and ignores it) */
+    int32_t precision;    /* MPCD_P64 or MPCD_P32 */
+    int32_t naive_transfer; /* 1: skip Eq. 7 (negative control of Fig. S1) */
+    uint64_t seed;        /* Philox4x32-10 key */
+    int32_t sort_period;  /* steps between spatial re-sorts of the solvent;
+                             0 = default (20), < 0 = never */
+    int32_t reserved;     /* must be 0 */
+} mpcd_params;
+
+/* A rigid discrete-particle template in its principal-axis frame with its
+ * site centre of mass at the origin (Sec. II.B).  All arrays are copied. */
+typedef struct {
+    int32_t n_sites;
+    const double *b;        /* [n_sites][3] body-frame site offsets */
+    const double *m;        /* [n_sites] site masses (> 0) */
+    int32_t n_centres;
+    const double *centres;  /* [n_centres][3] massless WCA centres (Eq. 1) */
+    double wca_d;           /* centre diameter d; Delta = d - sigma, sigma = 1 */
+} mpcd_shape_desc;
+
+/* One independent periodic box; replicas are simulated together. */
+typedef struct {
+    int32_t L[3];             /* cells per edge (>= 3 each) */
+    int64_t n_solvent;        /* solvent particles of this replica */
+    int32_t n_bodies;
+    const int32_t *body_shape;  /* [n_bodies] shape index (copied) */
+} mpcd_replica_desc;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Both
+ * functions are called on the creating thread; alloc returns NULL on failure. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *user);
+    void (*free)(void *ptr, void *user);
+    void *user;
+} mpcd_allocator;
+
+/* Host-side state, all replicas concatenated in replica order.  Solvent rows
+ * are in tag order (the order given to mpcd_set_state). */
+typedef struct {
+    void *x;        /* [N_s][3] positions: float for MPCD_P32, double for P64 */
+    void *v;        /* [N_s][3] velocities, same type */
+    double *R;      /* [B][3] body centres of mass (site COM) */
+    double *q;      /* [B][4] orientations */
+    double *P;      /* [B][3] linear momenta (Eq. 3) */
+    double *Lm;     /* [B][3] space-frame angular momenta (Eq. 4) */
+    int64_t step;   /* completed steps; keys the random streams */
+} mpcd_host_state;
+
+typedef struct {
+    int64_t n_solvent, n_bodies, n_sites, n_cells;
+    int32_t n_replicas, n_shapes;
+    int64_t device_bytes;     /* bytes the context holds on the device */
+    int32_t sum_words;        /* words per cell of the debug sums (see below) */
+    int32_t param_bytes;      /* bytes per cell of the debug parameters */
+} mpcd_sizes_t;
+
+/* Global diagnostics in FP64 (computed on the device). */
+typedef struct {
+    double p_solvent[3];      /* sum m v over the solvent */
+    double p_bodies[3];       /* sum P over the bodies */
+    double ke_solvent;        /* sum m v^2 / 2 over the solvent */
+    double ke_trans;          /* sum |P|^2 / 2M over the bodies */
+    double ke_rot;            /* sum w.I.w / 2 over the bodies */
+    int64_t step;
+} mpcd_diag;
+
+/* Create a context on CUDA device `device`.  Validates every argument
+ * (MPCD_ERR_ARG), builds the per-shape mass and principal moments, allocates
+ * the device state (MPCD_ERR_OOM) and zeroes it; call mpcd_set_state next.
+ * The paper's cell size a = 1 is the only one supported. */
+int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_desc *shapes,
+                int32_t n_replicas, const mpcd_replica_desc *replicas,
+                const mpcd_allocator *allocator, int32_t device, mpcd_ctx **out);
+
+/* Release every resource of the context.  NULL-safe.  Synchronises. */
+int mpcd_destroy(mpcd_ctx *ctx);
+
+/* Upload a full state from host buffers (pinned or pageable) and compute the
+ * initial WCA forces.  Positions must lie in [0, L). */
+int mpcd_set_state(mpcd_ctx *ctx, const mpcd_host_state *state, void *stream);
+
+/* Download the full state into caller buffers sized by mpcd_sizes().
+ * Solvent rows come back in tag order.  Synchronises the stream. */
+int mpcd_get_state(mpcd_ctx *ctx, mpcd_host_state *state, void *stream);
+
+/* a1 + a9: stream the solvent and advance the bodies by one MD step. */
+int mpcd_stream(mpcd_ctx *ctx, void *stream);
+
+/* MPCD_PRE (a3, a4): site poses and Eq. 7 thermalisation, sites binned into
+ * the cell sums; MPCD_POST (a8): site collision, momentum transfer to the
+ * bodies, step counter advanced.  PRE must precede mpcd_collide and POST
+ * follow it. */
+int mpcd_couple(mpcd_ctx *ctx, int32_t phase, void *stream);
+
+/* a2, a5-a7: grid shift, solvent binning, cell sums, collision parameters,
+ * solvent collision. */
+int mpcd_collide(mpcd_ctx *ctx, void *stream);
+
+/* Run `nsteps` whole steps (>= 0).  Steps are software-pipelined: the
+ * solvent pass of step n also streams and bins for step n+1, so the solvent
+ * arrays are read and written once per step.  Results are identical to the
+ * unpipelined sequence. */
+int mpcd_step(mpcd_ctx *ctx, int64_t nsteps, void *stream);
+
+/* Re-sort the solvent storage by cell for memory locality.  canonical != 0
+ * orders each cell by tag, making the storage order deterministic.  Does not
+ * change any result. */
+int mpcd_sort(mpcd_ctx *ctx, int32_t canonical, void *stream);
+
+/* FP64 diagnostics of the current state.  Synchronises the stream. */
+int mpcd_diagnostics(mpcd_ctx *ctx, mpcd_diag *out, void *stream);
+
+int mpcd_sizes(const mpcd_ctx *ctx, mpcd_sizes_t *out);
+
+/* Message of the sticky error (or "ok").  The string lives in the context. */
+const char *mpcd_last_error(const mpcd_ctx *ctx);
+
+/* Capture buffers for tests.  After mpcd_set_debug(ctx, 1) every collision
+ * keeps a copy of its cell sums before they are consumed.
+ * sums:      [sum_words][n_cells]; P32 words are int64 fixed point:
+ *            w0 = (round(m 2^24) << 16) + 1 summed (count in the low 16 bits),
+ *            w1..3 = round(fl32(m v) 2^40), w4 = round(fl32(m v.v) 2^40) (SRD)
+ *            or w4..6 = round(fl32(m xi) 2^40) (AT); P64 words are doubles
+ *            N, M, m v (3), m v.v (SRD) or m xi (3) (AT).
+ * params:    [n_cells][param_bytes] collision parameters (u, kappa, axis / xibar).
+ * site_cell: [n_sites] replica-local cell of every site.
+ * site_v:    [n_sites][3] site velocities entering the collision (float/double).
+ * shift:     [n_replicas][3] integer grid shift S (s = S 2^-20).
+ * Any pointer may be NULL.  Synchronises the stream. */
+int mpcd_set_debug(mpcd_ctx *ctx, int32_t on);
+int mpcd_debug_cells(mpcd_ctx *ctx, void *sums, void *params, int32_t *site_cell, void *site_v,
+                     int32_t *shift, void *stream);
+
+/* Per-kernel timing with CUDA events on the launching stream.  While on,
+ * mpcd_step() launches kernels one by one (no graph).  get_profile fills up to
+ * `max` entries (name, launches, total ms) and returns how many kernels were
+ * timed; it synchronises. */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    double bytes_per_launch;  /* algorithmic bytes moved by one launch */
+} mpcd_kernel_time;
+int mpcd_set_profiling(mpcd_ctx *ctx, int32_t on);
+int mpcd_get_profile(mpcd_ctx *ctx, mpcd_kernel_time *out, int32_t max);
+int mpcd_reset_profile(mpcd_ctx *ctx);
+
+/* Launch configuration of the solvent pass and the re-sort period.  The
+ * autotuner times candidate configurations on the current state (which it
+ * restores afterwards) and keeps the fastest; set_tuning fixes one directly.
+ * Any field <= 0 keeps its current value. */
+typedef struct {
+    int32_t block;          /* threads per CTA of the solvent pass */
+    int32_t tile;           /* particles per work tile */
+    int32_t ctas_per_sm;    /* persistent CTAs per SM */
+    int32_t sort_period;    /* steps between re-sorts */
+} mpcd_tuning;
+int mpcd_get_tuning(const mpcd_ctx *ctx, mpcd_tuning *out);
+int mpcd_set_tuning(mpcd_ctx *ctx, const mpcd_tuning *t);
+int mpcd_autotune(mpcd_ctx *ctx, int32_t steps_per_trial, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPCD_H */

@@ -647,10 +647,11 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                 M += m;
                 for (int a = 0; a < 3; ++a) { pm[a] += m * v[a]; e2 += m * v[a] * v[a]; }
                 if (p32) {
+                    /* words: count|mass, m v (3), then m v.v (SRD) or m xi (3, AT, below) */
                     float vf[3] = { f32(v[0]), f32(v[1]), f32(v[2]) };
                     int64_t w[5];
                     fixed_terms(f32(m), vf, w);
-                    for (int q = 0; q < 5; ++q) fx[q] += w[q];
+                    for (int q = 0; q < (s->rule == ORC_AT ? 4 : 5); ++q) fx[q] += w[q];
                 }
             }
             double u[3] = { 0, 0, 0 };

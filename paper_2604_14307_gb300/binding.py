@@ -1,0 +1,361 @@
+"""Thin ctypes binding of the C ABI in include/mpcd.h (libmpcd.so).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device memory comes from PyTorch's caching allocator (through
+the ABI's allocator callbacks) and work is enqueued on PyTorch's current CUDA
+stream when PyTorch is available; otherwise the library allocates with
+cudaMalloc and uses the legacy default stream.  If the library cannot be
+loaded, every entry point raises - there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmpcd.so")
+
+MPCD_OK, MPCD_ERR_ARG, MPCD_ERR_CUDA, MPCD_ERR_OOM, MPCD_ERR_TIMEOUT, MPCD_ERR_STATE = 0, -1, -2, -3, -4, -5
+MPCD_PRE, MPCD_POST = 0, 1
+_STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "out of device memory",
+           -4: "device wait timed out", -5: "invalid device state"}
+
+# every function the header declares (the CPU test checks they are exported)
+EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "mpcd_stream",
+           "mpcd_couple", "mpcd_collide", "mpcd_step", "mpcd_sort", "mpcd_diagnostics",
+           "mpcd_sizes", "mpcd_last_error", "mpcd_set_debug", "mpcd_debug_cells",
+           "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
+           "mpcd_set_tuning", "mpcd_autotune"]
+
+
+class MPCDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)} ({status}): {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("kT", C.c_double), ("dt", C.c_double), ("alpha_deg", C.c_double),
+                ("m_solvent", C.c_double), ("rule", C.c_int32), ("thermostat", C.c_int32),
+                ("precision", C.c_int32), ("naive_transfer", C.c_int32), ("seed", C.c_uint64),
+                ("sort_period", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ShapeDesc(C.Structure):
+    _fields_ = [("n_sites", C.c_int32), ("b", C.c_void_p), ("m", C.c_void_p),
+                ("n_centres", C.c_int32), ("centres", C.c_void_p), ("wca_d", C.c_double)]
+
+
+class ReplicaDesc(C.Structure):
+    _fields_ = [("L", C.c_int32 * 3), ("n_solvent", C.c_int64), ("n_bodies", C.c_int32),
+                ("body_shape", C.c_void_p)]
+
+
+AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FreeFn = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", AllocFn), ("free", FreeFn), ("user", C.c_void_p)]
+
+
+class HostState(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("v", C.c_void_p), ("R", C.c_void_p), ("q", C.c_void_p),
+                ("P", C.c_void_p), ("Lm", C.c_void_p), ("step", C.c_int64)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("n_solvent", C.c_int64), ("n_bodies", C.c_int64), ("n_sites", C.c_int64),
+                ("n_cells", C.c_int64), ("n_replicas", C.c_int32), ("n_shapes", C.c_int32),
+                ("device_bytes", C.c_int64), ("sum_words", C.c_int32), ("param_bytes", C.c_int32)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("p_solvent", C.c_double * 3), ("p_bodies", C.c_double * 3),
+                ("ke_solvent", C.c_double), ("ke_trans", C.c_double), ("ke_rot", C.c_double),
+                ("step", C.c_int64)]
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("bytes_per_launch", C.c_double)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("block", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("sort_period", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libmpcd.so; raises if it is missing (build it with build_lib.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run paper_2604_14307_gb300.build_lib.build())")
+        lib = C.CDLL(path)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "mpcd_create": [C.POINTER(Params), i32, vp, i32, vp, vp, i32, C.POINTER(vp)],
+            "mpcd_destroy": [vp],
+            "mpcd_set_state": [vp, C.POINTER(HostState), vp],
+            "mpcd_get_state": [vp, C.POINTER(HostState), vp],
+            "mpcd_stream": [vp, vp],
+            "mpcd_couple": [vp, i32, vp],
+            "mpcd_collide": [vp, vp],
+            "mpcd_step": [vp, i64, vp],
+            "mpcd_sort": [vp, i32, vp],
+            "mpcd_diagnostics": [vp, C.POINTER(Diag), vp],
+            "mpcd_sizes": [vp, C.POINTER(Sizes)],
+            "mpcd_set_debug": [vp, i32],
+            "mpcd_debug_cells": [vp, vp, vp, vp, vp, vp, vp],
+            "mpcd_set_profiling": [vp, i32],
+            "mpcd_get_profile": [vp, vp, i32],
+            "mpcd_reset_profile": [vp],
+            "mpcd_get_tuning": [vp, C.POINTER(Tuning)],
+            "mpcd_set_tuning": [vp, C.POINTER(Tuning)],
+            "mpcd_autotune": [vp, i32, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        lib.mpcd_last_error.argtypes = [vp]
+        lib.mpcd_last_error.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _torch_cuda():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch
+    except Exception:
+        pass
+    return None
+
+
+def current_stream() -> int:
+    t = _torch_cuda()
+    return int(t.cuda.current_stream().cuda_stream) if t is not None else 0
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(n, _user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(n), self.device))
+            except Exception:
+                return None
+
+        def _free(p, _user):
+            try:
+                torch.cuda.caching_allocator_delete(int(p))
+            except Exception:
+                pass
+
+        self._a = AllocFn(_alloc)
+        self._f = FreeFn(_free)
+        self.c = Allocator(self._a, self._f, None)
+
+
+class Simulation:
+    """One MPCD context: all replicas of `system` simulated together on one GPU."""
+
+    def __init__(self, system: I.System, device: int = 0, sort_period: int = 0,
+                 use_torch_allocator: bool = True):
+        self.lib = load()
+        self.system = system
+        p = system.params
+        self.precision = p.precision
+        self.prm = Params(p.kT, p.dt, p.alpha_deg, p.m_solvent, p.rule, p.thermostat,
+                          p.precision, p.naive_transfer, p.seed, sort_period, 0)
+        self._keep = []
+        shapes = (ShapeDesc * max(1, len(system.shapes)))()
+        for k, sh in enumerate(system.shapes):
+            b = np.ascontiguousarray(sh.b, dtype=np.float64)
+            m = np.ascontiguousarray(sh.m, dtype=np.float64)
+            cen = np.ascontiguousarray(sh.centres, dtype=np.float64).reshape(-1, 3)
+            self._keep += [b, m, cen]
+            shapes[k] = ShapeDesc(len(m), b.ctypes.data, m.ctypes.data, len(cen),
+                                  cen.ctypes.data if len(cen) else None, sh.wca_d)
+        reps = (ReplicaDesc * system.n_rep)()
+        for r, rep in enumerate(system.replicas):
+            ids = np.ascontiguousarray(rep.body_shapes, dtype=np.int32)
+            self._keep.append(ids)
+            reps[r] = ReplicaDesc((C.c_int32 * 3)(*rep.L), rep.n_solvent, len(ids),
+                                  ids.ctypes.data if len(ids) else None)
+        self._alloc = None
+        t = _torch_cuda()
+        if use_torch_allocator and t is not None:
+            self._alloc = _TorchAllocator(device)
+        ctx = C.c_void_p()
+        rc = self.lib.mpcd_create(C.byref(self.prm), len(system.shapes), C.cast(shapes, C.c_void_p),
+                                  system.n_rep, C.cast(reps, C.c_void_p),
+                                  C.byref(self._alloc.c) if self._alloc else None, device,
+                                  C.byref(ctx))
+        if rc != MPCD_OK:
+            raise MPCDError(rc, "mpcd_create failed")
+        self.ctx = ctx
+        self.sizes = Sizes()
+        self._check(self.lib.mpcd_sizes(self.ctx, C.byref(self.sizes)))
+        self.real = np.float32 if self.precision == I.P32 else np.float64
+
+    # ------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc < 0:
+            msg = self.lib.mpcd_last_error(self.ctx).decode() if getattr(self, "ctx", None) else ""
+            raise MPCDError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mpcd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @staticmethod
+    def _s(stream):
+        return current_stream() if stream is None else int(stream)
+
+    # ------------------------------------------------------------------
+    def host_buffers(self, pinned: bool = False):
+        """Host state buffers of the right shapes (optionally page-locked via torch)."""
+        ns, nb = self.sizes.n_solvent, self.sizes.n_bodies
+        if pinned and _torch_cuda() is not None:
+            import torch
+            dt = torch.float32 if self.real == np.float32 else torch.float64
+            mk = lambda shp, d=dt: torch.empty(shp, dtype=d).pin_memory()  # noqa: E731
+            t = dict(x=mk((ns, 3)), v=mk((ns, 3)), R=mk((nb, 3), torch.float64),
+                     q=mk((nb, 4), torch.float64), P=mk((nb, 3), torch.float64),
+                     Lm=mk((nb, 3), torch.float64))
+            self._pinned = t
+            return {k: v.numpy() for k, v in t.items()}
+        return dict(x=np.zeros((ns, 3), self.real), v=np.zeros((ns, 3), self.real),
+                    R=np.zeros((nb, 3)), q=np.zeros((nb, 4)), P=np.zeros((nb, 3)),
+                    Lm=np.zeros((nb, 3)))
+
+    def _hs(self, b: dict, step: int) -> HostState:
+        ptr = lambda a: a.ctypes.data if a.size else None  # noqa: E731
+        return HostState(ptr(b["x"]), ptr(b["v"]), ptr(b["R"]), ptr(b["q"]), ptr(b["P"]),
+                         ptr(b["Lm"]), step)
+
+    def set_state_buffers(self, b: dict, step: int = 0, stream=None):
+        hs = self._hs(b, step)
+        self._check(self.lib.mpcd_set_state(self.ctx, C.byref(hs), self._s(stream)))
+
+    def get_state_buffers(self, b: dict, stream=None) -> int:
+        hs = self._hs(b, 0)
+        self._check(self.lib.mpcd_get_state(self.ctx, C.byref(hs), self._s(stream)))
+        return int(hs.step)
+
+    def set_state(self, st: I.State, stream=None):
+        b = dict(x=np.ascontiguousarray(st.x, dtype=self.real), v=np.ascontiguousarray(st.v, dtype=self.real),
+                 R=np.ascontiguousarray(st.R, dtype=np.float64).reshape(-1, 3),
+                 q=np.ascontiguousarray(st.q, dtype=np.float64).reshape(-1, 4),
+                 P=np.ascontiguousarray(st.P, dtype=np.float64).reshape(-1, 3),
+                 Lm=np.ascontiguousarray(st.Lm, dtype=np.float64).reshape(-1, 3))
+        self.set_state_buffers(b, st.step, stream)
+
+    def get_state(self, stream=None) -> I.State:
+        b = self.host_buffers()
+        step = self.get_state_buffers(b, stream)
+        return I.State(x=b["x"].astype(np.float64), v=b["v"].astype(np.float64), R=b["R"], q=b["q"],
+                       P=b["P"], Lm=b["Lm"], step=step)
+
+    # ------------------------------------------------------------------ steps
+    def stream(self, stream=None):
+        self._check(self.lib.mpcd_stream(self.ctx, self._s(stream)))
+
+    def couple(self, phase: int, stream=None):
+        self._check(self.lib.mpcd_couple(self.ctx, phase, self._s(stream)))
+
+    def collide(self, stream=None):
+        self._check(self.lib.mpcd_collide(self.ctx, self._s(stream)))
+
+    def step(self, n: int = 1, stream=None):
+        self._check(self.lib.mpcd_step(self.ctx, int(n), self._s(stream)))
+
+    def sort(self, canonical: bool = False, stream=None):
+        self._check(self.lib.mpcd_sort(self.ctx, int(canonical), self._s(stream)))
+
+    def diagnostics(self, stream=None) -> dict:
+        d = Diag()
+        self._check(self.lib.mpcd_diagnostics(self.ctx, C.byref(d), self._s(stream)))
+        return dict(p_solvent=np.array(d.p_solvent[:]), p_bodies=np.array(d.p_bodies[:]),
+                    ke_solvent=d.ke_solvent, ke_trans=d.ke_trans, ke_rot=d.ke_rot, step=d.step)
+
+    # ------------------------------------------------------------------ debug
+    def set_debug(self, on: bool = True):
+        self._check(self.lib.mpcd_set_debug(self.ctx, int(on)))
+
+    def debug_cells(self, stream=None) -> dict:
+        s = self.sizes
+        sums = np.zeros((s.sum_words, s.n_cells), dtype=np.int64 if self.precision == I.P32 else np.float64)
+        pw = s.param_bytes // (4 if self.precision == I.P32 else 8)
+        params = np.zeros((s.n_cells, pw), dtype=self.real)
+        site_cell = np.zeros(max(1, s.n_sites), dtype=np.int32)
+        site_v = np.zeros((3, max(1, s.n_sites)), dtype=self.real)
+        shift = np.zeros((s.n_replicas, 3), dtype=np.int32)
+        self._check(self.lib.mpcd_debug_cells(self.ctx, sums.ctypes.data, params.ctypes.data,
+                                              site_cell.ctypes.data, site_v.ctypes.data,
+                                              shift.ctypes.data, self._s(stream)))
+        return dict(sums=sums, params=params, site_cell=site_cell[: s.n_sites],
+                    site_v=site_v[:, : s.n_sites].T.astype(np.float64), shift=shift)
+
+    # ----------------------------------------------------------- profiling
+    def set_profiling(self, on: bool = True):
+        self._check(self.lib.mpcd_set_profiling(self.ctx, int(on)))
+
+    def reset_profile(self):
+        self._check(self.lib.mpcd_reset_profile(self.ctx))
+
+    def profile(self) -> dict:
+        arr = (KernelTime * 64)()
+        n = self._check(self.lib.mpcd_get_profile(self.ctx, C.cast(arr, C.c_void_p), 64))
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
+                                           bytes_per_launch=arr[i].bytes_per_launch)
+                for i in range(min(n, 64))}
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        self._check(self.lib.mpcd_get_tuning(self.ctx, C.byref(t)))
+        return dict(block=t.block, tile=t.tile, ctas_per_sm=t.ctas_per_sm, sort_period=t.sort_period)
+
+    def set_tuning(self, block=0, tile=0, ctas_per_sm=0, sort_period=0):
+        t = Tuning(block, tile, ctas_per_sm, sort_period)
+        self._check(self.lib.mpcd_set_tuning(self.ctx, C.byref(t)))
+
+    def autotune(self, steps_per_trial: int = 3, stream=None) -> dict:
+        self._check(self.lib.mpcd_autotune(self.ctx, steps_per_trial, self._s(stream)))
+        return self.tuning()

@@ -1,0 +1,617 @@
+// Rigid-body and surface-site kernels (Sec. II.B and II.B.2 of arXiv 2604.14307).
+//
+// k_body_md     first velocity-Verlet half kick, drift of R, and the Miller et
+//               al. NO_SQUISH free-rotor sequence 3-2-1-2-3 for q and its
+//               conjugate momentum p = 2 q (x) (0, L_body), formed from the
+//               stored space-frame L and converted back; one thread per body.
+// k_body_force  core-shifted WCA (Eq. 1) between the centres of different
+//               bodies of a replica, with torques; one warp per body, FP32
+//               bounding-sphere prefilter, FP64 forces; optional second kick.
+// k_sites_pre   one CTA per body: site positions from the pose, Maxwell-
+//               Boltzmann draws, per-body mean velocity and angular velocity of
+//               the draws, thermalised site velocity of Eq. 7, binning of the
+//               sites into the cell sums.
+// k_sites_post  one CTA per body: site collision with the cell parameters,
+//               segmented reduction of dP = sum m (v' - v) and
+//               dL = sum d x m (v' - v) (Eqs. 3-4) into the body's momenta;
+//               the sites are reset to rigid motion (Eq. 5) implicitly, since
+//               the next step recomputes them from P and L.
+// This file is compiled without fused multiply-add so that the FP64 body and
+// site-position arithmetic rounds the same way as the reference oracle.
+#include "mpcd_internal.cuh"
+
+namespace mpcd {
+
+// ------------------------------------------------------------- quaternions
+__device__ __forceinline__ void quat_mul(const double a[4], const double b[4], double o[4])
+{
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+// rotation matrix of a unit quaternion (w, x, y, z), body -> space
+__device__ __forceinline__ void rotmat(const double q[4], double Q[9])
+{
+    double xx = q[1] * q[1], yy = q[2] * q[2], zz = q[3] * q[3];
+    double xy = q[1] * q[2], xz = q[1] * q[3], yz = q[2] * q[3];
+    double wx = q[0] * q[1], wy = q[0] * q[2], wz = q[0] * q[3];
+    Q[0] = 1.0 - 2.0 * (yy + zz); Q[1] = 2.0 * (xy - wz);       Q[2] = 2.0 * (xz + wy);
+    Q[3] = 2.0 * (xy + wz);       Q[4] = 1.0 - 2.0 * (xx + zz); Q[5] = 2.0 * (yz - wx);
+    Q[6] = 2.0 * (xz - wy);       Q[7] = 2.0 * (yz + wx);       Q[8] = 1.0 - 2.0 * (xx + yy);
+}
+__device__ __forceinline__ void mv(const double Q[9], const double x[3], double o[3])
+{
+    for (int a = 0; a < 3; ++a) o[a] = (Q[3 * a] * x[0] + Q[3 * a + 1] * x[1]) + Q[3 * a + 2] * x[2];
+}
+__device__ __forceinline__ void mtv(const double Q[9], const double x[3], double o[3])
+{
+    for (int a = 0; a < 3; ++a) o[a] = (Q[a] * x[0] + Q[3 + a] * x[1]) + Q[6 + a] * x[2];
+}
+
+// body-frame angular momentum from p: L_body = vec(q* (x) p) / 2
+__device__ __forceinline__ void body_L(const double q[4], const double p[4], double Lb[3])
+{
+    double qc[4] = {q[0], -q[1], -q[2], -q[3]}, t[4];
+    quat_mul(qc, p, t);
+    Lb[0] = 0.5 * t[1]; Lb[1] = 0.5 * t[2]; Lb[2] = 0.5 * t[3];
+}
+__device__ __forceinline__ void p_from_Lb(const double q[4], const double Lb[3], double p[4])
+{
+    double v[4] = {0.0, Lb[0], Lb[1], Lb[2]}, t[4];
+    quat_mul(q, v, t);
+    for (int a = 0; a < 4; ++a) p[a] = 2.0 * t[a];
+}
+
+__device__ __forceinline__ void L_to_p(const double q[4], const double Lm[3], double p[4])
+{
+    double Q[9], Lb[3];
+    rotmat(q, Q);
+    mtv(Q, Lm, Lb);
+    p_from_Lb(q, Lb, p);
+}
+__device__ __forceinline__ void p_to_L(const double q[4], const double p[4], double Lm[3])
+{
+    double Q[9], Lb[3];
+    body_L(q, p, Lb);
+    rotmat(q, Q);
+    mv(Q, Lb, Lm);
+}
+
+// p += 2 h q (x) (0, Q^T tau): torque kick over a half step h
+__device__ __forceinline__ void torque_kick(const double q[4], double p[4], const double T[3], double h)
+{
+    double Q[9], tb[3];
+    rotmat(q, Q);
+    mtv(Q, T, tb);
+    double v[4] = {0.0, tb[0], tb[1], tb[2]}, t[4];
+    quat_mul(q, v, t);
+    for (int a = 0; a < 4; ++a) p[a] += 2.0 * h * t[a];
+}
+
+// free rotation about body axis k (1..3) for time h (Miller et al. 2002)
+__device__ __forceinline__ void rotor(double q[4], double p[4], int k, double h, const double Ih[3])
+{
+    if (Ih[k - 1] == 0.0) return;
+    double Pq[4], Pp[4];
+    if (k == 1) {
+        Pq[0] = -q[1]; Pq[1] = q[0]; Pq[2] = q[3]; Pq[3] = -q[2];
+        Pp[0] = -p[1]; Pp[1] = p[0]; Pp[2] = p[3]; Pp[3] = -p[2];
+    } else if (k == 2) {
+        Pq[0] = -q[2]; Pq[1] = -q[3]; Pq[2] = q[0]; Pq[3] = q[1];
+        Pp[0] = -p[2]; Pp[1] = -p[3]; Pp[2] = p[0]; Pp[3] = p[1];
+    } else {
+        Pq[0] = -q[3]; Pq[1] = q[2]; Pq[2] = -q[1]; Pq[3] = q[0];
+        Pp[0] = -p[3]; Pp[1] = p[2]; Pp[2] = -p[1]; Pp[3] = p[0];
+    }
+    double zeta = (p[0] * Pq[0] + p[1] * Pq[1] + p[2] * Pq[2] + p[3] * Pq[3]) / (4.0 * Ih[k - 1]);
+    double c = cos(zeta * h), s = sin(zeta * h);
+    for (int a = 0; a < 4; ++a) {
+        double nq = c * q[a] + s * Pq[a];
+        double np = c * p[a] + s * Pp[a];
+        q[a] = nq;
+        p[a] = np;
+    }
+}
+
+__device__ __forceinline__ double wrapd(double y, double L, int &bad)
+{
+    if (y >= L) y = y - L;
+    else if (y < 0.0) { y = y + L; if (y >= L) y = 0.0; }
+    bad |= !(y >= 0.0 && y < L);
+    return y;
+}
+__device__ __forceinline__ float wrapf(float y, float L, int &bad)
+{
+    if (y >= L) y = y - L;
+    else if (y < 0.0f) { y = y + L; if (y >= L) y = 0.0f; }
+    bad |= !(y >= 0.0f && y < L);
+    return y;
+}
+
+// --------------------------------------------------------------- body MD
+__global__ void k_body_md(StepArgs a)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bodies) return;
+    DevBody b = a.bodies[i];
+    const DevShape sh = a.shapes[b.shape];
+    const DevReplica r = a.reps[b.rep];
+    const double dt = a.dt;
+    int bad = 0;
+    double p[4];
+    L_to_p(b.q, b.Lm, p);
+    for (int k = 0; k < 3; ++k) b.P[k] += 0.5 * dt * b.F[k];
+    torque_kick(b.q, p, b.T, 0.5 * dt);
+    for (int k = 0; k < 3; ++k) b.R[k] = wrapd(b.R[k] + dt * (b.P[k] / sh.M), (double)r.L[k], bad);
+    rotor(b.q, p, 3, 0.5 * dt, sh.Ihat);
+    rotor(b.q, p, 2, 0.5 * dt, sh.Ihat);
+    rotor(b.q, p, 1, dt, sh.Ihat);
+    rotor(b.q, p, 2, 0.5 * dt, sh.Ihat);
+    rotor(b.q, p, 3, 0.5 * dt, sh.Ihat);
+    double nq = sqrt(b.q[0] * b.q[0] + b.q[1] * b.q[1] + b.q[2] * b.q[2] + b.q[3] * b.q[3]);
+    for (int k = 0; k < 4; ++k) b.q[k] /= nq;
+    p_to_L(b.q, p, b.Lm);
+    DevBody *o = a.bodies + i;
+    for (int k = 0; k < 3; ++k) { o->R[k] = b.R[k]; o->P[k] = b.P[k]; o->Lm[k] = b.Lm[k]; }
+    for (int k = 0; k < 4; ++k) o->q[k] = b.q[k];
+    a.bpos[i] = make_float4((float)b.R[0], (float)b.R[1], (float)b.R[2], (float)sh.bound);
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+__global__ void k_body_pos(StepArgs a)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bodies) return;
+    const DevBody &b = a.bodies[i];
+    a.bpos[i] = make_float4((float)b.R[0], (float)b.R[1], (float)b.R[2], (float)a.shapes[b.shape].bound);
+}
+
+void launch_body_md(const StepArgs &a, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    k_body_md<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
+}
+
+// ------------------------------------------------------------ WCA forces
+__device__ __forceinline__ void min_image(double d[3], const int32_t L[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        double h = 0.5 * L[k];
+        if (d[k] > h) d[k] -= L[k];
+        else if (d[k] < -h) d[k] += L[k];
+    }
+}
+
+__global__ void k_body_force(StepArgs a, int kick)
+{
+    const int wid = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= a.n_bodies) return;
+    const int i = wid;
+    const DevBody bi = a.bodies[i];
+    const DevShape si = a.shapes[bi.shape];
+    const DevReplica r = a.reps[bi.rep];
+    double Qi[9];
+    rotmat(bi.q, Qi);
+    const double rc_extra = 1.122462048309373;   // 2^(1/6) sigma
+    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    const float4 pi = a.bpos[i];
+    const float hx = 0.5f * r.L[0], hy = 0.5f * r.L[1], hz = 0.5f * r.L[2];
+    const float dmax = (float)(si.wca_d + a.max_wca_d) * 0.5f + (float)rc_extra - 1.0f;
+    for (int64_t j = r.body_begin + lane; j < r.body_end; j += 32) {
+        if (j == i) continue;
+        // bounding-sphere prefilter in FP32 on the compact positions (margin 1e-2)
+        const float4 pj = a.bpos[j];
+        float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        dx = dx > hx ? dx - r.L[0] : (dx < -hx ? dx + r.L[0] : dx);
+        dy = dy > hy ? dy - r.L[1] : (dy < -hy ? dy + r.L[1] : dy);
+        dz = dz > hz ? dz - r.L[2] : (dz < -hz ? dz + r.L[2] : dz);
+        const float lim = pi.w + pj.w + dmax + 1e-2f;
+        if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
+        const DevBody bj = a.bodies[j];
+        const DevShape sj = a.shapes[bj.shape];
+        const double dij = 0.5 * (si.wca_d + sj.wca_d);
+        const double delta = dij - 1.0, rcut = delta + rc_extra;
+        double Qj[9];
+        rotmat(bj.q, Qj);
+        for (int ca = 0; ca < si.n_cent; ++ca) {
+            double c_a[3];
+            mv(Qi, a.tcent + 3 * (si.cent_begin + ca), c_a);
+            for (int cc = 0; cc < sj.n_cent; ++cc) {
+                double c_c[3], dv[3];
+                mv(Qj, a.tcent + 3 * (sj.cent_begin + cc), c_c);
+                for (int k = 0; k < 3; ++k) dv[k] = (bi.R[k] + c_a[k]) - (bj.R[k] + c_c[k]);
+                min_image(dv, r.L);
+                double rr = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+                if (rr > rcut) continue;
+                double s = 1.0 / (rr - delta);
+                double s6 = s * s * s * s * s * s;
+                double fm = 4.0 * (12.0 * s6 * s6 - 6.0 * s6) / (rr - delta);
+                double f[3] = {fm * dv[0] / rr, fm * dv[1] / rr, fm * dv[2] / rr};
+                F[0] += f[0]; F[1] += f[1]; F[2] += f[2];
+                T[0] += c_a[1] * f[2] - c_a[2] * f[1];
+                T[1] += c_a[2] * f[0] - c_a[0] * f[2];
+                T[2] += c_a[0] * f[1] - c_a[1] * f[0];
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            F[k] += __shfl_down_sync(0xffffffffu, F[k], o);
+            T[k] += __shfl_down_sync(0xffffffffu, T[k], o);
+        }
+    if (lane == 0) {
+        DevBody *o = a.bodies + i;
+        for (int k = 0; k < 3; ++k) { o->F[k] = F[k]; o->T[k] = T[k]; }
+        if (kick) {
+            double p[4], Lm[3];
+            L_to_p(bi.q, bi.Lm, p);
+            for (int k = 0; k < 3; ++k) o->P[k] = bi.P[k] + 0.5 * a.dt * F[k];
+            torque_kick(bi.q, p, T, 0.5 * a.dt);
+            p_to_L(bi.q, p, Lm);
+            for (int k = 0; k < 3; ++k) o->Lm[k] = Lm[k];
+        }
+    }
+}
+
+void launch_body_force(const StepArgs &a, int kick, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    if (!kick) k_body_pos<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
+    int warps_per_block = 4;
+    k_body_force<<<(a.n_bodies + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(a, kick);
+}
+
+// ---------------------------------------------------------------- sites
+// (x + 1/2) 2^-32 from all 32 bits, relative error <= 2^-24 (never 0; 1 only
+// when x rounds up to 2^32)
+__device__ __forceinline__ float u01f(uint32_t x)
+{
+    return __fmaf_rn(__uint2float_rn(x), 2.3283064365386962890625e-10f, 1.16415321826934814453125e-10f);
+}
+__device__ __forceinline__ double u01d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386962890625e-10; }
+__device__ __forceinline__ void normals3(uint4 w, float n[3])
+{
+    float r1 = sqrtf(-2.0f * logf(u01f(w.x))), r2 = sqrtf(-2.0f * logf(u01f(w.z)));
+    float s1, c1;
+    sincospif(2.0f * u01f(w.y), &s1, &c1);
+    n[0] = r1 * c1; n[1] = r1 * s1; n[2] = r2 * cospif(2.0f * u01f(w.w));
+}
+__device__ __forceinline__ void normals3(uint4 w, double n[3])
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double r1 = sqrt(-2.0 * log(u01d(w.x))), r2 = sqrt(-2.0 * log(u01d(w.z)));
+    double s1, c1;
+    sincos(two_pi * u01d(w.y), &s1, &c1);
+    n[0] = r1 * c1; n[1] = r1 * s1; n[2] = r2 * cos(two_pi * u01d(w.w));
+}
+__device__ __forceinline__ int cell_axis(float x, int S, int L)
+{
+    int c = (__float2int_rd(x * 1048576.0f) - S) >> 20;
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    return ((unsigned)c < (unsigned)L) ? c : 0;   // only a non-finite position gets here; it is flagged
+
+}
+__device__ __forceinline__ int cell_axis(double x, int S, int L)
+{
+    int c = (__double2int_rd(x * 1048576.0) - S) >> 20;
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    return ((unsigned)c < (unsigned)L) ? c : 0;   // only a non-finite position gets here; it is flagged
+
+}
+__device__ __forceinline__ long long q40(float f) { return __float2ll_rn(__fmul_rn(f, 1099511627776.0f)); }
+
+// Site geometry of the two forms.  P32: d = Qf bf in float (three products,
+// two adds), r = fl32(R) + d; P64: d = Q b in double.  Both wrapped into [0, L).
+struct SiteGeomF {
+    float Q[9];
+    __device__ void site(const StepArgs &a, int64_t t, const double R[3], const DevReplica &r, float d[3],
+                         float x[3], int &bad) const
+    {
+        const float *b = a.tbf + 3 * t;
+        for (int k = 0; k < 3; ++k) {
+            float t0 = __fmul_rn(Q[3 * k], b[0]);
+            float t1 = __fmul_rn(Q[3 * k + 1], b[1]);
+            float t2 = __fmul_rn(Q[3 * k + 2], b[2]);
+            d[k] = __fadd_rn(__fadd_rn(t0, t1), t2);
+            x[k] = wrapf(__fadd_rn(__double2float_rn(R[k]), d[k]), (float)r.L[k], bad);
+        }
+    }
+};
+struct SiteGeomD {
+    double Q[9];
+    __device__ void site(const StepArgs &a, int64_t t, const double R[3], const DevReplica &r, double d[3],
+                         double x[3], int &bad) const
+    {
+        mv(Q, a.tb + 3 * t, d);
+        for (int k = 0; k < 3; ++k) x[k] = wrapd(R[k] + d[k], (double)r.L[k], bad);
+    }
+};
+template <typename Real> struct Geom;
+template <> struct Geom<float> { typedef SiteGeomF type; };
+template <> struct Geom<double> { typedef SiteGeomD type; };
+
+template <typename Real> __device__ __forceinline__ Real site_mass(const StepArgs &a, int64_t t);
+template <> __device__ __forceinline__ float site_mass<float>(const StepArgs &a, int64_t t) { return a.tmf[t]; }
+template <> __device__ __forceinline__ double site_mass<double>(const StepArgs &a, int64_t t) { return a.tm[t]; }
+
+// sum six per-thread values over the CTA into FP64 (out valid in every thread)
+template <typename Real>
+__device__ void block_sum6(Real (&v)[6], double (*scratch)[6], double *out)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) scratch[wid][k] = (double)v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += scratch[w][k];
+            out[k] = s;
+        }
+    __syncthreads();
+}
+
+template <typename Real>
+__device__ __forceinline__ void add_sums(const StepArgs &a, int64_t c, Real m, const Real v[3], const Real xi[3]);
+template <>
+__device__ __forceinline__ void add_sums<float>(const StepArgs &a, int64_t c, float m, const float v[3],
+                                                const float xi[3])
+{
+    unsigned long long *S = reinterpret_cast<unsigned long long *>(a.sums);
+    const int64_t C = a.n_cells;
+    long long w0 = ((long long)__float2ll_rn(__fmul_rn(m, 16777216.0f)) << 16) + 1;
+    float px = __fmul_rn(m, v[0]), py = __fmul_rn(m, v[1]), pz = __fmul_rn(m, v[2]);
+    atomicAdd(S + c, (unsigned long long)w0);
+    atomicAdd(S + C + c, (unsigned long long)q40(px));
+    atomicAdd(S + 2 * C + c, (unsigned long long)q40(py));
+    atomicAdd(S + 3 * C + c, (unsigned long long)q40(pz));
+    if (a.rule == 0) {
+        float e = __fadd_rn(__fadd_rn(__fmul_rn(px, v[0]), __fmul_rn(py, v[1])), __fmul_rn(pz, v[2]));
+        atomicAdd(S + 4 * C + c, (unsigned long long)q40(e));
+    } else {
+        for (int k = 0; k < 3; ++k) atomicAdd(S + (4 + k) * C + c, (unsigned long long)q40(__fmul_rn(m, xi[k])));
+    }
+}
+template <>
+__device__ __forceinline__ void add_sums<double>(const StepArgs &a, int64_t c, double m, const double v[3],
+                                                 const double xi[3])
+{
+    double *S = reinterpret_cast<double *>(a.sums);
+    const int64_t C = a.n_cells;
+    atomicAdd(S + c, 1.0);
+    atomicAdd(S + C + c, m);
+    for (int k = 0; k < 3; ++k) atomicAdd(S + (2 + k) * C + c, m * v[k]);
+    if (a.rule == 0) atomicAdd(S + 5 * C + c, m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+    else for (int k = 0; k < 3; ++k) atomicAdd(S + (5 + k) * C + c, m * xi[k]);
+}
+
+template <typename Real> __device__ __forceinline__ void load_cell(const StepArgs &a, int64_t c, Real p[8]);
+template <> __device__ __forceinline__ void load_cell<float>(const StepArgs &a, int64_t c, float p[8])
+{
+    const float4 *r = reinterpret_cast<const float4 *>(a.params) + 2 * c;
+    float4 x = r[0], y = r[1];
+    p[0] = x.x; p[1] = x.y; p[2] = x.z; p[3] = x.w; p[4] = y.x; p[5] = y.y; p[6] = y.z; p[7] = 0.f;
+}
+template <> __device__ __forceinline__ void load_cell<double>(const StepArgs &a, int64_t c, double p[8])
+{
+    const double2 *r = reinterpret_cast<const double2 *>(a.params) + 4 * c;
+    for (int k = 0; k < 4; ++k) { double2 t = r[k]; p[2 * k] = t.x; p[2 * k + 1] = t.y; }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(128) k_sites_pre(StepArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    Real *vt = reinterpret_cast<Real *>(smem_raw);          // [n_sites][3] thermal draws
+    __shared__ double sQ[9], sV[3], sOm[3], sVt[3], sOmt[3], sred[6];
+    __shared__ double scratch[4][6];
+    __shared__ int sS[3];
+    const DevBody B = a.bodies[blockIdx.x];
+    const DevShape sh = a.shapes[B.shape];
+    const DevReplica r = a.reps[B.rep];
+    const int64_t step = *a.d_step;
+    if (threadIdx.x == 0) {
+        // V = P/M, omega = I^-1 L with I = Q Ihat Q^T (Eq. 5)
+        double Lb[3], wb[3];
+        rotmat(B.q, sQ);
+        for (int k = 0; k < 3; ++k) sV[k] = B.P[k] / sh.M;
+        mtv(sQ, B.Lm, Lb);
+        for (int k = 0; k < 3; ++k) wb[k] = sh.Ihat[k] > 0.0 ? Lb[k] / sh.Ihat[k] : 0.0;
+        mv(sQ, wb, sOm);
+        grid_shift(r, step, sS);
+    }
+    __syncthreads();
+    typename Geom<Real>::type G;
+    for (int k = 0; k < 9; ++k) G.Q[k] = (Real)sQ[k];
+    const Real kT = (Real)a.kT;
+    const int n = sh.n_sites;
+    int bad = 0;
+    Real acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t t = sh.site_begin + j, g = B.site_begin + j;
+        Real d[3], x[3];
+        G.site(a, t, B.R, r, d, x, bad);
+        int c = cell_axis(x[0], sS[0], r.L[0]) +
+                r.L[0] * (cell_axis(x[1], sS[1], r.L[1]) + r.L[1] * cell_axis(x[2], sS[2], r.L[2]));
+        a.site_cell[g] = c;
+        if (!a.naive) {
+            const Real m = site_mass<Real>(a, t);
+            Real nn[3];
+            normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_SITE, 0u), nn);
+            const Real sc = sqrt(kT / m);
+            Real w[3] = {sc * nn[0], sc * nn[1], sc * nn[2]};
+            for (int k = 0; k < 3; ++k) vt[3 * j + k] = w[k];
+            Real p[3] = {m * w[0], m * w[1], m * w[2]};
+            acc[0] += p[0]; acc[1] += p[1]; acc[2] += p[2];
+            acc[3] += d[1] * p[2] - d[2] * p[1];
+            acc[4] += d[2] * p[0] - d[0] * p[2];
+            acc[5] += d[0] * p[1] - d[1] * p[0];
+        }
+    }
+    block_sum6<Real>(acc, scratch, sred);
+    if (threadIdx.x == 0) {
+        if (a.naive) {
+            for (int k = 0; k < 3; ++k) { sVt[k] = 0.0; sOmt[k] = 0.0; }
+        } else {
+            // omega~ = Q Ihat^-1 Q^T L~ (the space-frame inertia of the sites)
+            double Lt[3] = {sred[3], sred[4], sred[5]}, lb[3], wb[3];
+            for (int k = 0; k < 3; ++k) sVt[k] = sred[k] / sh.M;
+            mtv(sQ, Lt, lb);
+            for (int k = 0; k < 3; ++k) wb[k] = sh.Ihat[k] > 0.0 ? lb[k] / sh.Ihat[k] : 0.0;
+            mv(sQ, wb, sOmt);
+        }
+    }
+    __syncthreads();
+    const Real dV[3] = {(Real)(sV[0] - sVt[0]), (Real)(sV[1] - sVt[1]), (Real)(sV[2] - sVt[2])};
+    const Real dW[3] = {(Real)(sOm[0] - sOmt[0]), (Real)(sOm[1] - sOmt[1]), (Real)(sOm[2] - sOmt[2])};
+    Real *SV = reinterpret_cast<Real *>(a.site_v);
+    const int64_t NS = a.n_sites;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t t = sh.site_begin + j, g = B.site_begin + j;
+        Real d[3], x[3];
+        G.site(a, t, B.R, r, d, x, bad);
+        Real v[3];
+        v[0] = dV[0] + (dW[1] * d[2] - dW[2] * d[1]);
+        v[1] = dV[1] + (dW[2] * d[0] - dW[0] * d[2]);
+        v[2] = dV[2] + (dW[0] * d[1] - dW[1] * d[0]);
+        if (!a.naive)
+            for (int k = 0; k < 3; ++k) v[k] += vt[3 * j + k];
+        for (int k = 0; k < 3; ++k) SV[k * NS + g] = v[k];
+        const Real m = site_mass<Real>(a, t);
+        Real xi[3] = {0, 0, 0};
+        if (a.rule == 1) {
+            normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
+            const Real sc = sqrt(kT / m);
+            xi[0] *= sc; xi[1] *= sc; xi[2] *= sc;
+        }
+        add_sums<Real>(a, (int64_t)r.cell_base + a.site_cell[g], m, v, xi);
+    }
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(128) k_sites_post(StepArgs a)
+{
+    __shared__ double sQ[9], sred[6];
+    __shared__ double scratch[4][6];
+    const DevBody B = a.bodies[blockIdx.x];
+    const DevShape sh = a.shapes[B.shape];
+    const DevReplica r = a.reps[B.rep];
+    const int64_t step = *a.d_step;
+    if (threadIdx.x == 0) rotmat(B.q, sQ);
+    __syncthreads();
+    typename Geom<Real>::type G;
+    for (int k = 0; k < 9; ++k) G.Q[k] = (Real)sQ[k];
+    const Real kT = (Real)a.kT, ca = (Real)a.cos_a, sa = (Real)a.sin_a;
+    const Real *SV = reinterpret_cast<const Real *>(a.site_v);
+    const int64_t NS = a.n_sites;
+    int bad = 0;
+    Real acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < sh.n_sites; j += blockDim.x) {
+        const int64_t t = sh.site_begin + j, g = B.site_begin + j;
+        Real d[3], x[3];
+        G.site(a, t, B.R, r, d, x, bad);
+        Real v[3] = {SV[g], SV[NS + g], SV[2 * NS + g]}, vn[3] = {v[0], v[1], v[2]};
+        Real p[8];
+        load_cell<Real>(a, (int64_t)r.cell_base + a.site_cell[g], p);
+        const Real m = site_mass<Real>(a, t);
+        if (p[3] >= Real(0)) {
+            if (a.rule == 0) {
+                Real w[3] = {v[0] - p[0], v[1] - p[1], v[2] - p[2]};
+                Real nd = p[4] * w[0] + p[5] * w[1] + p[6] * w[2];
+                Real cx = p[5] * w[2] - p[6] * w[1], cy = p[6] * w[0] - p[4] * w[2], cz = p[4] * w[1] - p[5] * w[0];
+                Real tt = nd * (Real(1) - ca);
+                vn[0] = p[0] + p[3] * (w[0] * ca + cx * sa + p[4] * tt);
+                vn[1] = p[1] + p[3] * (w[1] * ca + cy * sa + p[5] * tt);
+                vn[2] = p[2] + p[3] * (w[2] * ca + cz * sa + p[6] * tt);
+            } else {
+                Real xi[3];
+                normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
+                const Real sc = sqrt(kT / m);
+                for (int k = 0; k < 3; ++k) vn[k] = p[k] + sc * xi[k] - p[4 + k];
+            }
+        }
+        Real dp[3] = {m * (vn[0] - v[0]), m * (vn[1] - v[1]), m * (vn[2] - v[2])};
+        acc[0] += dp[0]; acc[1] += dp[1]; acc[2] += dp[2];
+        acc[3] += d[1] * dp[2] - d[2] * dp[1];
+        acc[4] += d[2] * dp[0] - d[0] * dp[2];
+        acc[5] += d[0] * dp[1] - d[1] * dp[0];
+    }
+    block_sum6<Real>(acc, scratch, sred);
+    if (threadIdx.x == 0) {
+        // impulse: P += dP, L += dL (Eqs. 3-4)
+        DevBody *o = a.bodies + blockIdx.x;
+        for (int k = 0; k < 3; ++k) {
+            o->P[k] = B.P[k] + sred[k];
+            o->Lm[k] = B.Lm[k] + sred[3 + k];
+        }
+    }
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+cudaError_t configure_body_kernels(int max_sites, int precision)
+{
+    size_t bytes = (size_t)max_sites * 3 * (precision == 1 ? sizeof(float) : sizeof(double));
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (precision == 1)
+        return cudaFuncSetAttribute(k_sites_pre<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaFuncSetAttribute(k_sites_pre<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void launch_sites_pre(const StepArgs &a, int max_sites, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    if (a.precision == 1)
+        k_sites_pre<float><<<a.n_bodies, 128, (size_t)max_sites * 3 * sizeof(float), s>>>(a);
+    else
+        k_sites_pre<double><<<a.n_bodies, 128, (size_t)max_sites * 3 * sizeof(double), s>>>(a);
+}
+
+void launch_sites_post(const StepArgs &a, int, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    if (a.precision == 1) k_sites_post<float><<<a.n_bodies, 128, 0, s>>>(a);
+    else k_sites_post<double><<<a.n_bodies, 128, 0, s>>>(a);
+}
+
+__global__ void k_advance_step(int64_t *step) { *step += 1; }
+
+void launch_advance_step(const StepArgs &a, cudaStream_t s)
+{
+    k_advance_step<<<1, 1, 0, s>>>(const_cast<int64_t *>(a.d_step));
+}
+
+// FP64 body diagnostics: sum P, sum |P|^2/2M, sum L_b.Ihat^-1.L_b/2 (L_b = Q^T L)
+__global__ void k_body_diag(StepArgs a, double *acc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bodies) return;
+    const DevBody b = a.bodies[i];
+    const DevShape sh = a.shapes[b.shape];
+    double Lb[3], Q[9];
+    rotmat(b.q, Q);
+    mtv(Q, b.Lm, Lb);
+    double er = 0.0;
+    for (int k = 0; k < 3; ++k) er += sh.Ihat[k] > 0.0 ? 0.5 * Lb[k] * Lb[k] / sh.Ihat[k] : 0.0;
+    double et = 0.5 * (b.P[0] * b.P[0] + b.P[1] * b.P[1] + b.P[2] * b.P[2]) / sh.M;
+    atomicAdd(acc + 4, b.P[0]);
+    atomicAdd(acc + 5, b.P[1]);
+    atomicAdd(acc + 6, b.P[2]);
+    atomicAdd(acc + 7, et);
+    atomicAdd(acc + 8, er);
+}
+
+void launch_body_diag(const StepArgs &a, double *acc, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    k_body_diag<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a, acc);
+}
+
+}  // namespace mpcd

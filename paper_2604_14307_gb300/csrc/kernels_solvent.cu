@@ -1,0 +1,814 @@
+// Solvent and cell kernels of the MPCD step (Sec. II.A of arXiv 2604.14307).
+//
+// k_solvent   one pass over the solvent that, depending on FLAGS, applies the
+//             collision of the current step (SRD rotation by alpha about the
+//             cell axis with thermostat scale kappa, or the MPCD-AT rule),
+//             streams ballistically with periodic wrap, and bins the streamed
+//             particle into the cell sums of the next collision (random grid
+//             shift, Sec. II.A).  Fused (all three flags) it reads and writes
+//             r and v once per step: 48 B per particle in FP32.
+//             Each thread owns 4 consecutive particles loaded with 128-bit SoA
+//             loads (cache-streaming hints keep the cell arrays in L2); runs
+//             of equal cells are merged in registers before the atomics.
+// k_params    per cell: sums -> centre-of-mass velocity u, SRD axis, thermostat
+//             scale (Huang et al.; Eq. 6 with n = 3(Nc-1)) or AT mean noise;
+//             clears the sums for the next collision.
+// re-sort     counting sort of the solvent by cell (histogram, scan, scatter,
+//             optional per-cell order by tag) for memory locality; it changes
+//             no result.
+#include "mpcd_internal.cuh"
+
+namespace mpcd {
+
+// ------------------------------------------------------------------ helpers
+// (x + 1/2) 2^-32 from all 32 bits, relative error <= 2^-24 (never 0; 1 only
+// when x rounds up to 2^32)
+__device__ __forceinline__ float u01f(uint32_t x)
+{
+    return __fmaf_rn(__uint2float_rn(x), 2.3283064365386962890625e-10f, 1.16415321826934814453125e-10f);
+}
+__device__ __forceinline__ double u01d(uint32_t x)
+{
+    return ((double)x + 0.5) * 2.3283064365386962890625e-10;     // (x + 1/2) 2^-32
+}
+
+// three standard normals from one Philox block (Box-Muller)
+__device__ __forceinline__ void normals3(uint4 w, float n[3])
+{
+    float r1 = sqrtf(-2.0f * logf(u01f(w.x)));
+    float r2 = sqrtf(-2.0f * logf(u01f(w.z)));
+    float s1, c1;
+    sincospif(2.0f * u01f(w.y), &s1, &c1);
+    n[0] = r1 * c1;
+    n[1] = r1 * s1;
+    n[2] = r2 * cospif(2.0f * u01f(w.w));
+}
+__device__ __forceinline__ void normals3(uint4 w, double n[3])
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double r1 = sqrt(-2.0 * log(u01d(w.x)));
+    double r2 = sqrt(-2.0 * log(u01d(w.z)));
+    double s1, c1;
+    sincos(two_pi * u01d(w.y), &s1, &c1);
+    n[0] = r1 * c1;
+    n[1] = r1 * s1;
+    n[2] = r2 * cos(two_pi * u01d(w.w));
+}
+
+// binning rule: X = floor(x 2^20), cell = floor((X - S) / 2^20) mod L
+__device__ __forceinline__ int cell_axis(float x, int S, int L)
+{
+    int c = (__float2int_rd(x * 1048576.0f) - S) >> 20;
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    return ((unsigned)c < (unsigned)L) ? c : 0;   // only a non-finite position gets here; it is flagged
+
+}
+__device__ __forceinline__ int cell_axis(double x, int S, int L)
+{
+    int c = (__double2int_rd(x * 1048576.0) - S) >> 20;
+    c += (c < 0) ? L : 0;
+    c -= (c >= L) ? L : 0;
+    return ((unsigned)c < (unsigned)L) ? c : 0;   // only a non-finite position gets here; it is flagged
+
+}
+
+// streaming x + v dt with periodic wrap, unfused (same rounding as the oracle)
+__device__ __forceinline__ float drift(float x, float v, float dt, float L, int &bad)
+{
+    float y = __fadd_rn(x, __fmul_rn(v, dt));
+    if (y >= L) y = __fsub_rn(y, L);
+    else if (y < 0.0f) { y = __fadd_rn(y, L); if (y >= L) y = 0.0f; }
+    bad |= !(y >= 0.0f && y < L);
+    return y;
+}
+__device__ __forceinline__ double drift(double x, double v, double dt, double L, int &bad)
+{
+    double y = __dadd_rn(x, __dmul_rn(v, dt));
+    if (y >= L) y = __dsub_rn(y, L);
+    else if (y < 0.0) { y = __dadd_rn(y, L); if (y >= L) y = 0.0; }
+    bad |= !(y >= 0.0 && y < L);
+    return y;
+}
+
+__device__ __forceinline__ long long q40(float f)
+{
+    return __float2ll_rn(__fmul_rn(f, 1099511627776.0f));   // f * 2^40, exact scaling
+}
+
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4])
+{
+    float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4])
+{
+    double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&o)[4])
+{
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(o[0], o[1], o[2], o[3]));
+}
+__device__ __forceinline__ void st4(double *p, const double (&o)[4])
+{
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(o[0], o[1]));
+    __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(o[2], o[3]));
+}
+
+// collision parameters of one cell
+template <typename Real> struct CellParams { Real ux, uy, uz, kappa, ax, ay, az; };
+
+__device__ __forceinline__ CellParams<float> load_params(const void *params, int64_t c)
+{
+    const float4 *p = reinterpret_cast<const float4 *>(params) + 2 * c;
+    float4 a = p[0], b = p[1];
+    return {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+}
+__device__ __forceinline__ CellParams<double> load_params_d(const void *params, int64_t c)
+{
+    const double2 *p = reinterpret_cast<const double2 *>(params) + 4 * c;
+    double2 a = p[0], b = p[1], d = p[2], e = p[3];
+    return {a.x, a.y, b.x, b.y, d.x, d.y, e.x};
+}
+template <typename Real> __device__ __forceinline__ CellParams<Real> get_params(const void *pr, int64_t c);
+template <> __device__ __forceinline__ CellParams<float> get_params<float>(const void *pr, int64_t c)
+{
+    return load_params(pr, c);
+}
+template <> __device__ __forceinline__ CellParams<double> get_params<double>(const void *pr, int64_t c)
+{
+    return load_params_d(pr, c);
+}
+
+template <typename Real> struct Consts;
+template <> struct Consts<float> {
+    __device__ static float kT(const StepArgs &a) { return a.kTf; }
+    __device__ static float dt(const StepArgs &a) { return a.dtf; }
+    __device__ static float m(const StepArgs &a) { return a.m_solvent_f; }
+    __device__ static float ca(const StepArgs &a) { return a.cos_af; }
+    __device__ static float sa(const StepArgs &a) { return a.sin_af; }
+};
+template <> struct Consts<double> {
+    __device__ static double kT(const StepArgs &a) { return a.kT; }
+    __device__ static double dt(const StepArgs &a) { return a.dt; }
+    __device__ static double m(const StepArgs &a) { return a.m_solvent; }
+    __device__ static double ca(const StepArgs &a) { return a.cos_a; }
+    __device__ static double sa(const StepArgs &a) { return a.sin_a; }
+};
+
+// SRD: v' = u + kappa R(n, alpha)(v - u)  (Rodrigues)
+template <typename Real>
+__device__ __forceinline__ void srd_rotate(const CellParams<Real> &p, Real ca, Real sa, Real &vx,
+                                           Real &vy, Real &vz)
+{
+    Real wx = vx - p.ux, wy = vy - p.uy, wz = vz - p.uz;
+    Real nd = p.ax * wx + p.ay * wy + p.az * wz;
+    Real cx = p.ay * wz - p.az * wy, cy = p.az * wx - p.ax * wz, cz = p.ax * wy - p.ay * wx;
+    Real t = nd * (Real(1) - ca);
+    vx = p.ux + p.kappa * (wx * ca + cx * sa + p.ax * t);
+    vy = p.uy + p.kappa * (wy * ca + cy * sa + p.ay * t);
+    vz = p.uz + p.kappa * (wz * ca + cz * sa + p.az * t);
+}
+
+// word count of the cell sums
+template <typename Real, int RULE> struct NWords;
+template <> struct NWords<float, 0> { static constexpr int n = 5; };
+template <> struct NWords<float, 1> { static constexpr int n = 7; };
+template <> struct NWords<double, 0> { static constexpr int n = 6; };
+template <> struct NWords<double, 1> { static constexpr int n = 8; };
+template <typename Real> struct SumWord { typedef double type; };
+template <> struct SumWord<float> { typedef long long type; };
+
+// contributions of one particle of mass m and velocity v (and AT noise xi)
+template <int RULE>
+__device__ __forceinline__ void terms(long long w0, float m, float vx, float vy, float vz,
+                                      const float *xi, long long *w)
+{
+    float px = __fmul_rn(m, vx), py = __fmul_rn(m, vy), pz = __fmul_rn(m, vz);
+    w[0] = w0;
+    w[1] = q40(px);
+    w[2] = q40(py);
+    w[3] = q40(pz);
+    if (RULE == 0) {
+        float e = __fadd_rn(__fadd_rn(__fmul_rn(px, vx), __fmul_rn(py, vy)), __fmul_rn(pz, vz));
+        w[4] = q40(e);
+    } else {
+        w[4] = q40(__fmul_rn(m, xi[0]));
+        w[5] = q40(__fmul_rn(m, xi[1]));
+        w[6] = q40(__fmul_rn(m, xi[2]));
+    }
+}
+template <int RULE>
+__device__ __forceinline__ void terms(long long, double m, double vx, double vy, double vz,
+                                      const double *xi, double *w)
+{
+    w[0] = 1.0;
+    w[1] = m;
+    w[2] = m * vx;
+    w[3] = m * vy;
+    w[4] = m * vz;
+    if (RULE == 0) {
+        w[5] = m * (vx * vx + vy * vy + vz * vz);
+    } else {
+        w[5] = m * xi[0];
+        w[6] = m * xi[1];
+        w[7] = m * xi[2];
+    }
+}
+
+__device__ __forceinline__ void red_add(long long *p, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
+
+// --------------------------------------------------------------- the pass
+template <typename Real, int RULE, int FLAGS>
+__global__ void __launch_bounds__(512) k_solvent(StepArgs a)
+{
+    constexpr bool COLLIDE = FLAGS & SOLV_COLLIDE;
+    constexpr bool STREAM = FLAGS & SOLV_STREAM;
+    constexpr bool BIN = FLAGS & SOLV_BIN;
+    constexpr int NW = NWords<Real, RULE>::n;
+    typedef typename SumWord<Real>::type W;
+
+    __shared__ int32_t sS[6];
+    __shared__ int32_t sL[3];
+    __shared__ int32_t sbase;
+    __shared__ int64_t sbeg, send;
+    __shared__ uint32_t skey[2];
+
+    const int64_t step = *a.d_step;
+    const Real dt = Consts<Real>::dt(a), m = Consts<Real>::m(a), kT = Consts<Real>::kT(a);
+    const Real ca = Consts<Real>::ca(a), sa = Consts<Real>::sa(a);
+    const Real sc = sqrt(kT / m);
+    Real *X = reinterpret_cast<Real *>(a.x), *Y = reinterpret_cast<Real *>(a.y);
+    Real *Z = reinterpret_cast<Real *>(a.z), *VX = reinterpret_cast<Real *>(a.vx);
+    Real *VY = reinterpret_cast<Real *>(a.vy), *VZ = reinterpret_cast<Real *>(a.vz);
+    W *sums = reinterpret_cast<W *>(a.sums);
+    const int64_t C = a.n_cells;
+    int bad = 0;
+
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Tile tl = a.tiles[t];
+            DevReplica r = a.reps[tl.rep];
+            sL[0] = r.L[0]; sL[1] = r.L[1]; sL[2] = r.L[2];
+            sbase = r.cell_base;
+            sbeg = tl.begin;
+            send = tl.end;
+            skey[0] = r.key0;
+            skey[1] = r.key1;
+            if (COLLIDE) grid_shift(r, step, &sS[0]);
+            if (BIN) grid_shift(r, step + (COLLIDE ? 1 : 0), &sS[3]);
+        }
+        __syncthreads();
+        const int L0 = sL[0], L1 = sL[1], L2 = sL[2], base = sbase;
+        const Real Lx = (Real)L0, Ly = (Real)L1, Lz = (Real)L2;
+        const int64_t beg = sbeg, end = send;
+        DevReplica rr;
+        rr.key0 = skey[0];
+        rr.key1 = skey[1];
+
+        for (int64_t i = beg + 4 * (int64_t)threadIdx.x; i < end; i += 4 * (int64_t)blockDim.x) {
+            const int nv = (int)min((int64_t)4, end - i);
+            Real x[4], y[4], z[4], vx[4], vy[4], vz[4];
+            ld4(X + i, x); ld4(Y + i, y); ld4(Z + i, z);
+            ld4(VX + i, vx); ld4(VY + i, vy); ld4(VZ + i, vz);
+            uint32_t tg[4] = {0, 0, 0, 0};
+            if (RULE == 1) {
+                uint4 t4 = __ldcs(reinterpret_cast<const uint4 *>(a.tag + i));
+                tg[0] = t4.x; tg[1] = t4.y; tg[2] = t4.z; tg[3] = t4.w;
+            }
+            int run_c = -1;
+            W acc[NW];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= nv) break;
+                if (COLLIDE) {
+                    int c = base + cell_axis(x[j], sS[0], L0) +
+                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    CellParams<Real> p = get_params<Real>(a.params, c);
+                    if (p.kappa >= Real(0)) {
+                        if (RULE == 0) {
+                            srd_rotate<Real>(p, ca, sa, vx[j], vy[j], vz[j]);
+                        } else {
+                            Real n[3];
+                            normals3(draw(rr, step, tg[j], TAG_AT, 0u), n);
+                            vx[j] = p.ux + sc * n[0] - p.ax;
+                            vy[j] = p.uy + sc * n[1] - p.ay;
+                            vz[j] = p.uz + sc * n[2] - p.az;
+                        }
+                    }
+                }
+                if (STREAM) {
+                    x[j] = drift(x[j], vx[j], dt, Lx, bad);
+                    y[j] = drift(y[j], vy[j], dt, Ly, bad);
+                    z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                }
+                if (BIN) {
+                    int c = base + cell_axis(x[j], sS[3], L0) +
+                            L0 * (cell_axis(y[j], sS[4], L1) + L1 * cell_axis(z[j], sS[5], L2));
+                    Real xi[3] = {0, 0, 0};
+                    if (RULE == 1) {
+                        normals3(draw(rr, step + (COLLIDE ? 1 : 0), tg[j], TAG_AT, 0u), xi);
+                        xi[0] *= sc; xi[1] *= sc; xi[2] *= sc;
+                    }
+                    W w[NW];
+                    terms<RULE>(a.w0_solvent, m, vx[j], vy[j], vz[j], xi, w);
+                    if (c == run_c) {
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) acc[k] += w[k];
+                    } else {
+                        if (run_c >= 0) {
+#pragma unroll
+                            for (int k = 0; k < NW; ++k) red_add(sums + k * C + run_c, acc[k]);
+                        }
+                        run_c = c;
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) acc[k] = w[k];
+                    }
+                }
+            }
+            if (BIN && run_c >= 0) {
+#pragma unroll
+                for (int k = 0; k < NW; ++k) red_add(sums + k * C + run_c, acc[k]);
+            }
+            if (STREAM) { st4(X + i, x); st4(Y + i, y); st4(Z + i, z); }
+            if (COLLIDE) { st4(VX + i, vx); st4(VY + i, vy); st4(VZ + i, vz); }
+        }
+    }
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+template <typename Real, int RULE>
+static void dispatch_flags(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s)
+{
+    switch (flags) {
+    case SOLV_STREAM: k_solvent<Real, RULE, SOLV_STREAM><<<cfg.grid, cfg.block, 0, s>>>(a); break;
+    case SOLV_BIN: k_solvent<Real, RULE, SOLV_BIN><<<cfg.grid, cfg.block, 0, s>>>(a); break;
+    case SOLV_COLLIDE: k_solvent<Real, RULE, SOLV_COLLIDE><<<cfg.grid, cfg.block, 0, s>>>(a); break;
+    case SOLV_STREAM | SOLV_BIN:
+        k_solvent<Real, RULE, SOLV_STREAM | SOLV_BIN><<<cfg.grid, cfg.block, 0, s>>>(a);
+        break;
+    case SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN:
+        k_solvent<Real, RULE, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN><<<cfg.grid, cfg.block, 0, s>>>(a);
+        break;
+    default: break;
+    }
+}
+
+void launch_solvent(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s)
+{
+    if (a.n_tiles == 0) return;
+    if (a.precision == 1) {
+        if (a.rule == 0) dispatch_flags<float, 0>(a, flags, cfg, s);
+        else dispatch_flags<float, 1>(a, flags, cfg, s);
+    } else {
+        if (a.rule == 0) dispatch_flags<double, 0>(a, flags, cfg, s);
+        else dispatch_flags<double, 1>(a, flags, cfg, s);
+    }
+}
+
+// ------------------------------------------------------- cell parameters
+// Gamma(n/2, 1) variate for n = 3(Nc - 1): floor(n/2) unit exponentials plus
+// z^2/2 when n is odd (Eq. 6).  FP32 form: four uniforms per logarithm.
+__device__ float gamma_half_dof(const DevReplica &r, int64_t step, uint32_t lc, int n_dof, float)
+{
+    int nE = n_dof / 2;
+    float g = 0.0f;
+#pragma unroll 4
+    for (int j = 0; 4 * j < nE; ++j) {
+        uint4 w = draw(r, step, lc, TAG_THERMO, (uint32_t)j);
+        int k = nE - 4 * j;
+        float prod = u01f(w.x);
+        if (k > 1) prod *= u01f(w.y);
+        if (k > 2) prod *= u01f(w.z);
+        if (k > 3) prod *= u01f(w.w);
+        g -= logf(prod);
+    }
+    if (n_dof & 1) {
+        uint4 w = draw(r, step, lc, TAG_THERMO_ODD, 0u);
+        float z = sqrtf(-2.0f * logf(u01f(w.x))) * cospif(2.0f * u01f(w.y));
+        g += 0.5f * z * z;
+    }
+    return g;
+}
+__device__ double gamma_half_dof(const DevReplica &r, int64_t step, uint32_t lc, int n_dof, double)
+{
+    int nE = n_dof / 2;
+    double g = 0.0;
+    uint4 w = make_uint4(0, 0, 0, 0);
+    for (int i = 0; i < nE; ++i) {
+        if ((i & 3) == 0) w = draw(r, step, lc, TAG_THERMO, (uint32_t)(i >> 2));
+        uint32_t x = (i & 3) == 0 ? w.x : (i & 3) == 1 ? w.y : (i & 3) == 2 ? w.z : w.w;
+        g += -log(u01d(x));
+    }
+    if (n_dof & 1) {
+        w = draw(r, step, lc, TAG_THERMO_ODD, 0u);
+        double z = sqrt(-2.0 * log(u01d(w.x))) * cos(6.283185307179586476925286766559 * u01d(w.y));
+        g += 0.5 * z * z;
+    }
+    return g;
+}
+
+template <typename Real, int RULE>
+__global__ void __launch_bounds__(256) k_params(StepArgs a)
+{
+    constexpr int NW = NWords<Real, RULE>::n;
+    typedef typename SumWord<Real>::type W;
+    const int64_t step = *a.d_step;
+    W *sums = reinterpret_cast<W *>(a.sums);
+    W *dbg = reinterpret_cast<W *>(a.dbg_sums);
+    const int64_t C = a.n_cells;
+    const Real kT = Consts<Real>::kT(a);
+    int err = 0;
+    for (int t = blockIdx.x; t < a.n_ctiles; t += gridDim.x) {
+        const Tile tl = a.ctiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        for (int64_t c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+            W w[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                w[k] = sums[k * C + c];
+                sums[k * C + c] = W(0);
+                if (dbg) dbg[k * C + c] = w[k];
+            }
+            int n;
+            Real M, p[3], s2 = 0, xi[3] = {0, 0, 0};
+            if (sizeof(Real) == 4) {
+                long long w0 = (long long)w[0];
+                n = (int)(w0 & 0xFFFF);
+                M = (Real)(w0 >> 16) * (Real)5.9604644775390625e-8;            // 2^-24
+                const Real s = (Real)9.094947017729282379150390625e-13;        // 2^-40
+                for (int k = 0; k < 3; ++k) p[k] = (Real)(long long)w[1 + k] * s;
+                if (RULE == 0) s2 = (Real)(long long)w[4] * s;
+                else for (int k = 0; k < 3; ++k) xi[k] = (Real)(long long)w[4 + k] * s;
+            } else {
+                n = (int)(double)w[0];
+                M = (Real)(double)w[1];
+                for (int k = 0; k < 3; ++k) p[k] = (Real)(double)w[2 + k];
+                if (RULE == 0) s2 = (Real)(double)w[5];
+                else for (int k = 0; k < 3; ++k) xi[k] = (Real)(double)w[5 + k];
+            }
+            Real rec[8] = {0, 0, 0, Real(-1), 0, 0, 0, 0};
+            if (n >= 2) {
+                Real u[3] = {p[0] / M, p[1] / M, p[2] / M};
+                rec[0] = u[0]; rec[1] = u[1]; rec[2] = u[2];
+                const uint32_t lc = (uint32_t)(c - r.cell_base);
+                if (RULE == 0) {
+                    uint4 wa = draw(r, step, lc, TAG_AXIS, 0u);
+                    Real zz, sp, cp;
+                    if (sizeof(Real) == 4) {
+                        zz = (Real)(2.0f * u01f(wa.x) - 1.0f);
+                        float s_, c_;
+                        sincospif(2.0f * u01f(wa.y), &s_, &c_);
+                        sp = s_; cp = c_;
+                    } else {
+                        zz = (Real)(2.0 * u01d(wa.x) - 1.0);
+                        double s_, c_;
+                        sincos(6.283185307179586476925286766559 * u01d(wa.y), &s_, &c_);
+                        sp = (Real)s_; cp = (Real)c_;
+                    }
+                    Real rho = sqrt(Real(1) - zz * zz);
+                    rec[4] = rho * cp; rec[5] = rho * sp; rec[6] = zz;
+                    Real kappa = Real(1);
+                    if (a.thermostat) {
+                        Real erel = Real(0.5) * (s2 - (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) / M);
+                        if (sizeof(Real) == 4 && erel < s2 * Real(0.015625)) {
+                            // strong cancellation: redo E_rel in FP64 from the exact sums
+                            const double sc = 9.094947017729282379150390625e-13;
+                            double q1 = (double)(long long)w[1] * sc, q2 = (double)(long long)w[2] * sc;
+                            double q3 = (double)(long long)w[3] * sc, e2 = (double)(long long)w[4] * sc;
+                            double Md = (double)((long long)w[0] >> 16) * 5.9604644775390625e-8;
+                            erel = (Real)(0.5 * (e2 - (q1 * q1 + q2 * q2 + q3 * q3) / Md));
+                        }
+                        Real g = gamma_half_dof(r, step, lc, 3 * (n - 1), Real(0));
+                        kappa = erel > Real(0) ? sqrt(kT * g / erel) : Real(1);
+                    }
+                    rec[3] = kappa;
+                } else {
+                    rec[3] = Real(1);
+                    rec[4] = xi[0] / M; rec[5] = xi[1] / M; rec[6] = xi[2] / M;
+                }
+            }
+            if (sizeof(Real) == 4) {
+                float4 *o = reinterpret_cast<float4 *>(a.params) + 2 * c;
+                o[0] = make_float4((float)rec[0], (float)rec[1], (float)rec[2], (float)rec[3]);
+                o[1] = make_float4((float)rec[4], (float)rec[5], (float)rec[6], 0.0f);
+            } else {
+                double2 *o = reinterpret_cast<double2 *>(a.params) + 4 * c;
+                o[0] = make_double2(rec[0], rec[1]);
+                o[1] = make_double2(rec[2], rec[3]);
+                o[2] = make_double2(rec[4], rec[5]);
+                o[3] = make_double2(rec[6], 0.0);
+            }
+        }
+    }
+    if (err) atomicOr(a.d_err, ERR_CELL);
+}
+
+void launch_params(const StepArgs &a, int grid, cudaStream_t s)
+{
+    if (a.n_ctiles == 0) return;
+    grid = grid < a.n_ctiles ? grid : a.n_ctiles;
+    if (a.precision == 1) {
+        if (a.rule == 0) k_params<float, 0><<<grid, 256, 0, s>>>(a);
+        else k_params<float, 1><<<grid, 256, 0, s>>>(a);
+    } else {
+        if (a.rule == 0) k_params<double, 0><<<grid, 256, 0, s>>>(a);
+        else k_params<double, 1><<<grid, 256, 0, s>>>(a);
+    }
+}
+
+// ------------------------------------------------- layout transforms (I/O)
+// host rows (tag order) -> SoA slots; positions outside [0, L) set ERR_POSITION
+template <typename Real>
+__global__ void k_aos_to_soa(StepArgs a, const Real *xa, const Real *va)
+{
+    Real *X[3] = {(Real *)a.x, (Real *)a.y, (Real *)a.z};
+    Real *V[3] = {(Real *)a.vx, (Real *)a.vy, (Real *)a.vz};
+    int bad = 0;
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const Tile tl = a.tiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            int64_t tag = i - r.solv_begin, row = r.row_begin + tag;
+            for (int k = 0; k < 3; ++k) {
+                Real x = xa[3 * row + k];
+                bad |= !(x >= Real(0) && x < (Real)r.L[k]);
+                X[k][i] = x;
+                V[k][i] = va[3 * row + k];
+            }
+            a.tag[i] = (uint32_t)tag;
+        }
+    }
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+template <typename Real>
+__global__ void k_soa_to_aos(StepArgs a, Real *xa, Real *va)
+{
+    const Real *X[3] = {(const Real *)a.x, (const Real *)a.y, (const Real *)a.z};
+    const Real *V[3] = {(const Real *)a.vx, (const Real *)a.vy, (const Real *)a.vz};
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const Tile tl = a.tiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            uint32_t tag = a.tag[i];
+            if (tag == PAD_TAG || (int64_t)tag >= r.n_solvent) continue;
+            int64_t row = r.row_begin + tag;
+            for (int k = 0; k < 3; ++k) {
+                xa[3 * row + k] = X[k][i];
+                va[3 * row + k] = V[k][i];
+            }
+        }
+    }
+}
+
+void launch_aos_to_soa(const StepArgs &a, const void *xaos, const void *vaos, cudaStream_t s)
+{
+    if (a.n_tiles == 0) return;
+    if (a.precision == 1) k_aos_to_soa<float><<<a.n_tiles, 256, 0, s>>>(a, (const float *)xaos, (const float *)vaos);
+    else k_aos_to_soa<double><<<a.n_tiles, 256, 0, s>>>(a, (const double *)xaos, (const double *)vaos);
+}
+
+void launch_soa_to_aos(const StepArgs &a, void *xaos, void *vaos, const int64_t *, cudaStream_t s)
+{
+    if (a.n_tiles == 0) return;
+    if (a.precision == 1) k_soa_to_aos<float><<<a.n_tiles, 256, 0, s>>>(a, (float *)xaos, (float *)vaos);
+    else k_soa_to_aos<double><<<a.n_tiles, 256, 0, s>>>(a, (double *)xaos, (double *)vaos);
+}
+
+// ---------------------------------------------------- FP64 diagnostics
+template <typename Real>
+__global__ void k_solvent_diag(StepArgs a, double *acc)
+{
+    const Real *V[3] = {(const Real *)a.vx, (const Real *)a.vy, (const Real *)a.vz};
+    double s[4] = {0, 0, 0, 0};
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const Tile tl = a.tiles[t];
+        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            double vx = (double)V[0][i], vy = (double)V[1][i], vz = (double)V[2][i];
+            s[0] += vx; s[1] += vy; s[2] += vz;
+            s[3] += vx * vx + vy * vy + vz * vz;
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, v);
+    }
+}
+
+void launch_solvent_diag(const StepArgs &a, double *acc, cudaStream_t s)
+{
+    if (a.n_tiles == 0) return;
+    int grid = a.n_tiles < 1024 ? a.n_tiles : 1024;
+    if (a.precision == 1) k_solvent_diag<float><<<grid, 256, 0, s>>>(a, acc);
+    else k_solvent_diag<double><<<grid, 256, 0, s>>>(a, acc);
+}
+
+// ------------------------------------------------------------- re-sort
+template <typename Real>
+__device__ __forceinline__ int plain_cell(const DevReplica &r, Real x, Real y, Real z)
+{
+    return r.cell_base + cell_axis(x, 0, r.L[0]) +
+           r.L[0] * (cell_axis(y, 0, r.L[1]) + r.L[1] * cell_axis(z, 0, r.L[2]));
+}
+
+template <typename Real>
+__global__ void k_sort_count(StepArgs a, int32_t *counts)
+{
+    const Real *X = (const Real *)a.x, *Y = (const Real *)a.y, *Z = (const Real *)a.z;
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const Tile tl = a.tiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x)
+            atomicAdd(counts + plain_cell(r, X[i], Y[i], Z[i]), 1);
+    }
+}
+
+void launch_sort_count(const StepArgs &a, int32_t *counts, cudaStream_t s)
+{
+    if (a.n_tiles == 0) return;
+    if (a.precision == 1) k_sort_count<float><<<a.n_tiles, 256, 0, s>>>(a, counts);
+    else k_sort_count<double><<<a.n_tiles, 256, 0, s>>>(a, counts);
+}
+
+// exclusive scan: chunks of SCAN_CHUNK elements, one CTA of 1024 threads per chunk
+constexpr int SCAN_THREADS = 1024, SCAN_ITEMS = 8, SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+
+size_t scan_block_sums_size(int64_t n) { return (size_t)((n + SCAN_CHUNK - 1) / SCAN_CHUNK) + 1; }
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *sh, int32_t &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    int32_t before = (wid > 0 ? sh[wid - 1] : 0) + x - v;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t *in, int64_t n, int32_t *bs)
+{
+    __shared__ int32_t sh[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < n) v += in[base + k];
+    int32_t total;
+    block_exclusive_scan(v, sh, total);
+    if (threadIdx.x == 0) bs[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(int32_t *bs, int64_t nb)
+{
+    // exclusive scan of the chunk totals, in passes of SCAN_CHUNK
+    __shared__ int32_t sh[32];
+    int32_t carry = 0;
+    for (int64_t off = 0; off < nb; off += SCAN_CHUNK) {
+        int64_t base = off + (int64_t)threadIdx.x * SCAN_ITEMS;
+        int32_t loc[SCAN_ITEMS];
+        int32_t v = 0;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            loc[k] = (base + k < nb) ? bs[base + k] : 0;
+            v += loc[k];
+        }
+        int32_t total;
+        int32_t ex = block_exclusive_scan(v, sh, total) + carry;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            if (base + k < nb) bs[base + k] = ex;
+            ex += loc[k];
+        }
+        carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const int32_t *in, int32_t *out, int64_t n,
+                                                            const int32_t *bs)
+{
+    __shared__ int32_t sh[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t loc[SCAN_ITEMS];
+    int32_t v = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        loc[k] = (base + k < n) ? in[base + k] : 0;
+        v += loc[k];
+    }
+    int32_t total;
+    int32_t ex = block_exclusive_scan(v, sh, total) + bs[blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = ex;
+        ex += loc[k];
+    }
+}
+
+void launch_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *bs, cudaStream_t s)
+{
+    if (n <= 0) return;
+    int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bs);
+    k_scan_blocks<<<1, SCAN_THREADS, 0, s>>>(bs, nb);
+    k_scan_final<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, bs);
+}
+
+template <typename Real>
+__global__ void k_sort_scatter(StepArgs a, const int32_t *ex, int32_t *cursor, Real *d0, Real *d1, Real *d2,
+                               Real *d3, Real *d4, Real *d5, uint32_t *dtag)
+{
+    const Real *S[6] = {(const Real *)a.x, (const Real *)a.y, (const Real *)a.z,
+                        (const Real *)a.vx, (const Real *)a.vy, (const Real *)a.vz};
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const Tile tl = a.tiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        const int32_t ex0 = ex[r.cell_base];
+        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            int c = plain_cell(r, S[0][i], S[1][i], S[2][i]);
+            int64_t pos = r.solv_begin + (ex[c] - ex0) + atomicAdd(cursor + c, 1);
+            d0[pos] = S[0][i]; d1[pos] = S[1][i]; d2[pos] = S[2][i];
+            d3[pos] = S[3][i]; d4[pos] = S[4][i]; d5[pos] = S[5][i];
+            dtag[pos] = a.tag[i];
+        }
+    }
+}
+
+void launch_sort_scatter(const StepArgs &a, const int32_t *ex, int32_t *cursor, void *const d[6],
+                         uint32_t *dtag, cudaStream_t s)
+{
+    if (a.n_tiles == 0) return;
+    if (a.precision == 1)
+        k_sort_scatter<float><<<a.n_tiles, 256, 0, s>>>(a, ex, cursor, (float *)d[0], (float *)d[1],
+                                                       (float *)d[2], (float *)d[3], (float *)d[4],
+                                                       (float *)d[5], dtag);
+    else
+        k_sort_scatter<double><<<a.n_tiles, 256, 0, s>>>(a, ex, cursor, (double *)d[0], (double *)d[1],
+                                                        (double *)d[2], (double *)d[3], (double *)d[4],
+                                                        (double *)d[5], dtag);
+}
+
+// order every cell's segment by tag (insertion sort; segments hold ~10)
+template <typename Real>
+__global__ void k_sort_canonical(StepArgs a, Real *d0, Real *d1, Real *d2, Real *d3, Real *d4, Real *d5,
+                                 uint32_t *tag, const int32_t *ex)
+{
+    Real *D[6] = {d0, d1, d2, d3, d4, d5};
+    for (int t = blockIdx.x; t < a.n_ctiles; t += gridDim.x) {
+        const Tile tl = a.ctiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        const int32_t ex0 = ex[r.cell_base];
+        const int64_t cend = (int64_t)r.cell_base + (int64_t)r.L[0] * r.L[1] * r.L[2];
+        for (int64_t c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+            int64_t b = r.solv_begin + (ex[c] - ex0);
+            int64_t e = r.solv_begin + ((c + 1 < cend ? ex[c + 1] : ex0 + (int32_t)r.n_solvent) - ex0);
+            for (int64_t i = b + 1; i < e; ++i) {
+                uint32_t key = tag[i];
+                Real v[6];
+                for (int k = 0; k < 6; ++k) v[k] = D[k][i];
+                int64_t j = i - 1;
+                while (j >= b && tag[j] > key) {
+                    tag[j + 1] = tag[j];
+                    for (int k = 0; k < 6; ++k) D[k][j + 1] = D[k][j];
+                    --j;
+                }
+                tag[j + 1] = key;
+                for (int k = 0; k < 6; ++k) D[k][j + 1] = v[k];
+            }
+        }
+    }
+}
+
+void launch_sort_canonical(const StepArgs &a, void *const d[6], uint32_t *tag, const int32_t *ex,
+                           cudaStream_t s)
+{
+    if (a.n_ctiles == 0) return;
+    if (a.precision == 1)
+        k_sort_canonical<float><<<a.n_ctiles, 256, 0, s>>>(a, (float *)d[0], (float *)d[1], (float *)d[2],
+                                                          (float *)d[3], (float *)d[4], (float *)d[5], tag, ex);
+    else
+        k_sort_canonical<double><<<a.n_ctiles, 256, 0, s>>>(a, (double *)d[0], (double *)d[1], (double *)d[2],
+                                                           (double *)d[3], (double *)d[4], (double *)d[5], tag,
+                                                           ex);
+}
+
+}  // namespace mpcd

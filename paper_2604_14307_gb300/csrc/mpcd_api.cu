@@ -1,0 +1,1081 @@
+// C ABI of the MPCD + rigid-body library (include/mpcd.h): context, memory,
+// launch orchestration, software pipelining of whole steps, periodic re-sort,
+// CUDA-graph capture, per-kernel event timing and the autotuner.
+#include "../../include/mpcd.h"
+#include "mpcd_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+using namespace mpcd;
+
+namespace {
+
+struct KStat {
+    int64_t launches = 0;
+    double ms = 0.0;
+    double bytes = 0.0;
+};
+struct Pending {
+    std::string name;
+    cudaEvent_t a, b;
+    double bytes;
+};
+struct GraphEntry {
+    cudaGraphExec_t exec;
+    int cur_end;
+    int64_t since_end;
+};
+
+}  // namespace
+
+struct mpcd_ctx {
+    int device = 0;
+    mpcd_params prm{};
+    mpcd_allocator alloc{};
+    bool use_alloc = false;
+    int status = MPCD_OK;
+    char err[512] = "ok";
+
+    int nrep = 0, nshapes = 0, max_sites = 0;
+    double max_wca_d = 0.0;
+    int64_t Ns = 0, Nslots = 0, B = 0, Nsite = 0, C = 0;
+    int nw = 0, realsz = 0, param_bytes = 0;
+    std::vector<DevReplica> reps;
+    std::vector<Tile> tiles, ctiles;
+    std::vector<DevShape> shapes;
+
+    std::vector<void *> allocations;
+    int64_t dev_bytes = 0;
+    DevReplica *d_reps = nullptr;
+    Tile *d_tiles = nullptr, *d_ctiles = nullptr;
+    int64_t tiles_cap = 0;
+    DevShape *d_shapes = nullptr;
+    DevBody *d_bodies = nullptr;
+    float4 *d_bpos = nullptr;
+    double *d_tb = nullptr, *d_tm = nullptr, *d_tcent = nullptr;
+    float *d_tbf = nullptr, *d_tmf = nullptr;
+    void *sol[2][6] = {};
+    uint32_t *tag[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *sums = nullptr, *params = nullptr, *dbg_sums = nullptr;
+    bool debug = false;
+    void *site_v = nullptr;
+    int32_t *site_cell = nullptr;
+    int64_t *d_step = nullptr;
+    int *d_err = nullptr;
+    double *d_diag = nullptr;
+    int32_t *counts = nullptr, *ex = nullptr, *cursor = nullptr, *scan_bs = nullptr;
+    void *staging = nullptr;
+
+    int64_t step = 0, since_sort = 0, last_key = -1;
+    int num_sms = 0;
+    mpcd_tuning tune{256, 8192, 4, 20};
+
+    bool profiling = false;
+    std::vector<Pending> pending;
+    std::map<std::string, KStat> prof;
+    std::vector<cudaEvent_t> evpool;
+
+    std::map<std::tuple<int64_t, int, int64_t>, GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
+};
+
+namespace {
+
+int fail(mpcd_ctx *c, int st, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(mpcd_ctx *c, int st, const char *fmt, ...)
+{
+    if (c && c->status == MPCD_OK) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+        c->status = st;
+    }
+    return st;
+}
+
+#define CK(ctx, call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? MPCD_ERR_OOM : MPCD_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+    } while (0)
+
+#define CHECK_CTX(ctx)                         \
+    do {                                       \
+        if (!(ctx)) return MPCD_ERR_ARG;       \
+        if ((ctx)->status) return (ctx)->status; \
+    } while (0)
+
+void *dalloc(mpcd_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c->use_alloc) {
+        p = c->alloc.alloc(bytes, c->alloc.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        c->allocations.push_back(p);
+        c->dev_bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+StepArgs make_args(const mpcd_ctx *c)
+{
+    StepArgs a{};
+    const mpcd_params &p = c->prm;
+    a.precision = p.precision;
+    a.rule = p.rule;
+    a.thermostat = p.thermostat;
+    a.naive = p.naive_transfer;
+    a.kT = p.kT;
+    a.dt = p.dt;
+    a.m_solvent = p.m_solvent;
+    double al = p.alpha_deg * 3.14159265358979323846264338327950288 / 180.0;
+    a.cos_a = std::cos(al);
+    a.sin_a = std::sin(al);
+    a.kTf = (float)p.kT;
+    a.dtf = (float)p.dt;
+    a.m_solvent_f = (float)p.m_solvent;
+    a.cos_af = (float)a.cos_a;
+    a.sin_af = (float)a.sin_a;
+    a.w0_solvent = ((long long)std::llrint((double)(a.m_solvent_f * 16777216.0f)) << 16) + 1;
+    a.reps = c->d_reps;
+    a.n_rep = c->nrep;
+    a.tiles = c->d_tiles;
+    a.n_tiles = (int32_t)c->tiles.size();
+    a.ctiles = c->d_ctiles;
+    a.n_ctiles = (int32_t)c->ctiles.size();
+    a.x = c->sol[c->cur][0];
+    a.y = c->sol[c->cur][1];
+    a.z = c->sol[c->cur][2];
+    a.vx = c->sol[c->cur][3];
+    a.vy = c->sol[c->cur][4];
+    a.vz = c->sol[c->cur][5];
+    a.tag = c->tag[c->cur];
+    a.sums = c->sums;
+    a.params = c->params;
+    a.dbg_sums = c->debug ? c->dbg_sums : nullptr;
+    a.n_cells = c->C;
+    a.nw = c->nw;
+    a.bodies = c->d_bodies;
+    a.bpos = c->d_bpos;
+    a.n_bodies = (int32_t)c->B;
+    a.shapes = c->d_shapes;
+    a.tb = c->d_tb;
+    a.tbf = c->d_tbf;
+    a.tm = c->d_tm;
+    a.tmf = c->d_tmf;
+    a.tcent = c->d_tcent;
+    a.max_wca_d = c->max_wca_d;
+    a.site_v = c->site_v;
+    a.site_cell = c->site_cell;
+    a.n_sites = c->Nsite;
+    a.d_step = c->d_step;
+    a.d_err = c->d_err;
+    return a;
+}
+
+void build_tiles(mpcd_ctx *c)
+{
+    c->tiles.clear();
+    const int64_t T = std::max<int64_t>(64, c->tune.tile & ~(int64_t)7);
+    for (int r = 0; r < c->nrep; ++r) {
+        const DevReplica &R = c->reps[r];
+        for (int64_t b = R.solv_begin; b < R.solv_begin + R.n_solvent; b += T)
+            c->tiles.push_back(Tile{r, 0, b, std::min(b + T, R.solv_begin + R.n_solvent)});
+    }
+}
+
+void build_ctiles(mpcd_ctx *c)
+{
+    c->ctiles.clear();
+    const int64_t T = 2048;
+    for (int r = 0; r < c->nrep; ++r) {
+        const DevReplica &R = c->reps[r];
+        int64_t n = (int64_t)R.L[0] * R.L[1] * R.L[2];
+        for (int64_t b = R.cell_base; b < R.cell_base + n; b += T)
+            c->ctiles.push_back(Tile{r, 0, b, std::min(b + T, (int64_t)R.cell_base + n)});
+    }
+}
+
+int upload_tiles(mpcd_ctx *c)
+{
+    if ((int64_t)c->tiles.size() > c->tiles_cap) {
+        c->tiles_cap = (int64_t)c->tiles.size() * 2 + 16;
+        c->d_tiles = (Tile *)dalloc(c, c->tiles_cap * sizeof(Tile));
+        if (!c->d_tiles) return fail(c, MPCD_ERR_OOM, "tile table allocation failed");
+    }
+    if (!c->tiles.empty())
+        CK(c, cudaMemcpy(c->d_tiles, c->tiles.data(), c->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    return MPCD_OK;
+}
+
+// ------------------------------------------------------------- profiling
+template <typename F>
+int timed(mpcd_ctx *c, const char *name, double bytes, cudaStream_t s, F &&launch)
+{
+    if (!c->profiling) {
+        launch();
+        return MPCD_OK;
+    }
+    cudaEvent_t e0, e1;
+    if (c->evpool.size() >= 2) {
+        e0 = c->evpool.back(); c->evpool.pop_back();
+        e1 = c->evpool.back(); c->evpool.pop_back();
+    } else {
+        CK(c, cudaEventCreate(&e0));
+        CK(c, cudaEventCreate(&e1));
+    }
+    CK(c, cudaEventRecord(e0, s));
+    launch();
+    CK(c, cudaEventRecord(e1, s));
+    c->pending.push_back(Pending{name, e0, e1, bytes});
+    return MPCD_OK;
+}
+
+int drain_profile(mpcd_ctx *c)
+{
+    for (auto &p : c->pending) {
+        CK(c, cudaEventSynchronize(p.b));
+        float ms = 0.f;
+        CK(c, cudaEventElapsedTime(&ms, p.a, p.b));
+        KStat &k = c->prof[p.name];
+        k.launches += 1;
+        k.ms += ms;
+        k.bytes = p.bytes;
+        c->evpool.push_back(p.a);
+        c->evpool.push_back(p.b);
+    }
+    c->pending.clear();
+    return MPCD_OK;
+}
+
+// algorithmic bytes of one solvent pass (see the design notes)
+double solvent_bytes(const mpcd_ctx *c, int flags)
+{
+    double n = (double)c->Ns, rs = c->realsz, C = (double)c->C;
+    double b = 0;
+    if (flags & SOLV_STREAM) b += 2 * 3 * rs * n;            // r read + write
+    else if (flags & (SOLV_COLLIDE | SOLV_BIN)) b += 3 * rs * n;  // r read
+    if (flags & SOLV_COLLIDE) b += 2 * 3 * rs * n + C * c->param_bytes;   // v read+write, params
+    else if (flags & SOLV_BIN) b += 3 * rs * n;              // v read
+    if (c->prm.rule == MPCD_AT) b += 4 * n;                    // tags
+    if (flags & SOLV_BIN) b += C * c->nw * 8.0;              // sums written once
+    return b;
+}
+
+// ----------------------------------------------------------- step pieces
+int k_stream(mpcd_ctx *c, cudaStream_t s)
+{
+    StepArgs a = make_args(c);
+    LaunchCfg cfg{c->tune.block, std::max(1, std::min((int)c->tiles.size(), c->num_sms * c->tune.ctas_per_sm))};
+    int e = timed(c, "solvent_stream", solvent_bytes(c, SOLV_STREAM), s, [&] { launch_solvent(a, SOLV_STREAM, cfg, s); });
+    if (e) return e;
+    e = timed(c, "body_md", 0, s, [&] { launch_body_md(a, s); });
+    if (e) return e;
+    return timed(c, "body_force", 0, s, [&] { launch_body_force(a, 1, s); });
+}
+
+int k_bodies(mpcd_ctx *c, cudaStream_t s)
+{
+    StepArgs a = make_args(c);
+    int e = timed(c, "body_md", 0, s, [&] { launch_body_md(a, s); });
+    if (e) return e;
+    return timed(c, "body_force", 0, s, [&] { launch_body_force(a, 1, s); });
+}
+
+int k_pre(mpcd_ctx *c, cudaStream_t s)
+{
+    StepArgs a = make_args(c);
+    double bytes = (double)c->Nsite * (3.0 * c->realsz + 4.0);
+    return timed(c, "sites_pre", bytes, s, [&] { launch_sites_pre(a, c->max_sites, s); });
+}
+
+int k_params(mpcd_ctx *c, cudaStream_t s)
+{
+    StepArgs a = make_args(c);
+    double bytes = (double)c->C * (2.0 * c->nw * 8.0 + c->param_bytes);
+    return timed(c, "cell_params", bytes, s, [&] { launch_params(a, c->num_sms * 8, s); });
+}
+
+int k_post(mpcd_ctx *c, cudaStream_t s)
+{
+    StepArgs a = make_args(c);
+    double bytes = (double)c->Nsite * (3.0 * c->realsz + 4.0);
+    return timed(c, "sites_post", bytes, s, [&] { launch_sites_post(a, c->max_sites, s); });
+}
+
+int k_solvent(mpcd_ctx *c, int flags, cudaStream_t s)
+{
+    StepArgs a = make_args(c);
+    LaunchCfg cfg{c->tune.block, std::max(1, std::min((int)c->tiles.size(), c->num_sms * c->tune.ctas_per_sm))};
+    const char *name = flags == (SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN) ? "solvent_fused"
+                       : flags == SOLV_COLLIDE                          ? "solvent_collide"
+                       : flags == SOLV_BIN                              ? "solvent_bin"
+                       : flags == (SOLV_STREAM | SOLV_BIN)              ? "solvent_stream_bin"
+                                                                        : "solvent_stream";
+    return timed(c, name, solvent_bytes(c, flags), s, [&] { launch_solvent(a, flags, cfg, s); });
+}
+
+int k_advance(mpcd_ctx *c, cudaStream_t s)
+{
+    StepArgs a = make_args(c);
+    launch_advance_step(a, s);
+    c->last_key = c->step;
+    c->step += 1;
+    return MPCD_OK;
+}
+
+int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
+{
+    if (c->Ns == 0) return MPCD_OK;
+    StepArgs a = make_args(c);
+    const int nxt = c->cur ^ 1;
+    double bytes = (double)c->Ns * (2.0 * (6.0 * c->realsz + 4.0) + 3.0 * c->realsz);
+    int e = timed(c, "sort", bytes, s, [&] {
+        cudaMemsetAsync(c->counts, 0, c->C * sizeof(int32_t), s);
+        cudaMemsetAsync(c->cursor, 0, c->C * sizeof(int32_t), s);
+        cudaMemsetAsync(c->tag[nxt], 0xFF, c->Nslots * sizeof(uint32_t), s);
+        launch_sort_count(a, c->counts, s);
+        launch_scan(c->counts, c->ex, c->C, c->scan_bs, s);
+        void *dst[6] = {c->sol[nxt][0], c->sol[nxt][1], c->sol[nxt][2],
+                        c->sol[nxt][3], c->sol[nxt][4], c->sol[nxt][5]};
+        launch_sort_scatter(a, c->ex, c->cursor, dst, c->tag[nxt], s);
+        if (canonical) launch_sort_canonical(a, dst, c->tag[nxt], c->ex, s);
+    });
+    if (e) return e;
+    c->cur = nxt;
+    c->since_sort = 0;
+    return MPCD_OK;
+}
+
+// whole steps, software-pipelined: the solvent pass of step k collides (k),
+// streams and bins for step k+1
+int run_steps(mpcd_ctx *c, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return MPCD_OK;
+    int e = k_solvent(c, SOLV_STREAM | SOLV_BIN, s);
+    for (int64_t k = 0; k < n && !e; ++k) {
+        if ((e = k_bodies(c, s))) break;
+        if ((e = k_pre(c, s))) break;
+        if ((e = k_params(c, s))) break;
+        if ((e = k_post(c, s))) break;
+        const bool last = (k == n - 1);
+        if ((e = k_solvent(c, last ? SOLV_COLLIDE : (SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN), s))) break;
+        if (!last && c->prm.sort_period >= 0 && ++c->since_sort >= c->tune.sort_period)
+            if ((e = do_sort(c, 0, s))) break;
+        if ((e = k_advance(c, s))) break;
+    }
+    if (!e && !c->profiling) {
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) return fail(c, MPCD_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(ce));
+    }
+    return e;
+}
+
+int check_device_error(mpcd_ctx *c, cudaStream_t s)
+{
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    if (h & ERR_POSITION)
+        return fail(c, MPCD_ERR_STATE, "a particle or body left the periodic box in one step (|v dt| >= L)");
+    if (h) return fail(c, MPCD_ERR_STATE, "device error word 0x%x", h);
+    return MPCD_OK;
+}
+
+void clear_graphs(mpcd_ctx *c)
+{
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.second.exec);
+    c->graphs.clear();
+}
+
+}  // namespace
+
+// ======================================================================== ABI
+extern "C" {
+
+int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_desc *shapes,
+                int32_t n_replicas, const mpcd_replica_desc *replicas, const mpcd_allocator *allocator,
+                int32_t device, mpcd_ctx **out)
+{
+    if (!out || !params || n_shapes < 0 || n_replicas <= 0 || !replicas || (n_shapes > 0 && !shapes))
+        return MPCD_ERR_ARG;
+    *out = nullptr;
+    const mpcd_params &p = *params;
+    if (!(p.kT > 0) || !(p.dt > 0) || !(p.m_solvent > 0) || !std::isfinite(p.alpha_deg) ||
+        (p.rule != MPCD_SRD && p.rule != MPCD_AT) || (p.precision != MPCD_P32 && p.precision != MPCD_P64) ||
+        p.reserved != 0)
+        return MPCD_ERR_ARG;
+    if (allocator && (!allocator->alloc || !allocator->free)) return MPCD_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return MPCD_ERR_CUDA;
+    }
+    mpcd_ctx *c = new mpcd_ctx();
+    c->device = device;
+    c->prm = p;
+    if (allocator) {
+        c->alloc = *allocator;
+        c->use_alloc = true;
+    }
+    c->nrep = n_replicas;
+    c->nshapes = n_shapes;
+    c->realsz = p.precision == MPCD_P32 ? 4 : 8;
+    c->nw = p.precision == MPCD_P32 ? (p.rule == MPCD_SRD ? 5 : 7) : (p.rule == MPCD_SRD ? 6 : 8);
+    c->param_bytes = p.precision == MPCD_P32 ? 32 : 64;
+    if (p.sort_period > 0) c->tune.sort_period = p.sort_period;
+
+    // shapes
+    std::vector<double> tb, tm, tcent;
+    for (int s = 0; s < n_shapes; ++s) {
+        const mpcd_shape_desc &d = shapes[s];
+        if (d.n_sites <= 0 || !d.b || !d.m || d.n_centres < 0 || (d.n_centres > 0 && !d.centres) ||
+            !(d.wca_d > 1.0 || d.n_centres == 0)) {
+            delete c;
+            return MPCD_ERR_ARG;
+        }
+        DevShape S{};
+        S.site_begin = (int64_t)tm.size();
+        S.cent_begin = (int64_t)tcent.size() / 3;
+        S.n_sites = d.n_sites;
+        S.n_cent = d.n_centres;
+        S.wca_d = d.wca_d;
+        double M = 0, I[3] = {0, 0, 0}, com[3] = {0, 0, 0}, off = 0;
+        for (int j = 0; j < d.n_sites; ++j) {
+            const double *b = d.b + 3 * j;
+            if (!(d.m[j] > 0) || !std::isfinite(b[0] + b[1] + b[2])) {
+                delete c;
+                return MPCD_ERR_ARG;
+            }
+            double r2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+            M += d.m[j];
+            for (int k = 0; k < 3; ++k) {
+                I[k] += d.m[j] * (r2 - b[k] * b[k]);
+                com[k] += d.m[j] * b[k];
+            }
+            off = std::max({off, std::fabs(d.m[j] * b[0] * b[1]), std::fabs(d.m[j] * b[0] * b[2]),
+                            std::fabs(d.m[j] * b[1] * b[2])});
+            for (int k = 0; k < 3; ++k) tb.push_back(b[k]);
+            tm.push_back(d.m[j]);
+        }
+        // the template must be centred and principal (Eqs. 3-5 with R = site COM)
+        double Ix = 0, Iy = 0, Iz = 0;
+        for (int j = 0; j < d.n_sites; ++j) {
+            const double *b = d.b + 3 * j;
+            Ix += d.m[j] * b[0] * b[1];
+            Iy += d.m[j] * b[0] * b[2];
+            Iz += d.m[j] * b[1] * b[2];
+        }
+        double Imax = std::max({I[0], I[1], I[2], 1e-300});
+        if (std::fabs(com[0]) + std::fabs(com[1]) + std::fabs(com[2]) > 1e-8 * M * std::sqrt(Imax / M) + 1e-12 ||
+            std::fabs(Ix) + std::fabs(Iy) + std::fabs(Iz) > 1e-8 * Imax) {
+            delete c;
+            return MPCD_ERR_ARG;
+        }
+        (void)off;
+        S.M = M;
+        for (int k = 0; k < 3; ++k) S.Ihat[k] = I[k];
+        double bound = 0;
+        for (int j = 0; j < d.n_centres; ++j) {
+            const double *x = d.centres + 3 * j;
+            bound = std::max(bound, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+            for (int k = 0; k < 3; ++k) tcent.push_back(x[k]);
+        }
+        S.bound = bound;
+        c->max_sites = std::max(c->max_sites, d.n_sites);
+        c->max_wca_d = std::max(c->max_wca_d, d.wca_d);
+        c->shapes.push_back(S);
+    }
+
+    // replicas, slots, cells, bodies
+    std::vector<int32_t> body_shape;
+    int64_t slot = 0, cells = 0, bodies = 0, sites = 0, rows = 0;
+    for (int r = 0; r < n_replicas; ++r) {
+        const mpcd_replica_desc &d = replicas[r];
+        if (d.L[0] < 3 || d.L[1] < 3 || d.L[2] < 3 || d.L[0] > 4096 || d.L[1] > 4096 || d.L[2] > 4096 ||
+            d.n_solvent < 0 || d.n_bodies < 0 || (d.n_bodies > 0 && !d.body_shape)) {
+            delete c;
+            return MPCD_ERR_ARG;
+        }
+        DevReplica R{};
+        for (int k = 0; k < 3; ++k) R.L[k] = d.L[k];
+        R.cell_base = (int32_t)cells;
+        R.solv_begin = slot;
+        R.n_solvent = d.n_solvent;
+        R.body_begin = bodies;
+        R.body_end = bodies + d.n_bodies;
+        R.site_begin = sites;
+        R.row_begin = rows;
+        R.key0 = (uint32_t)p.seed;
+        R.key1 = (uint32_t)(p.seed >> 32) ^ (uint32_t)r;
+        for (int b = 0; b < d.n_bodies; ++b) {
+            int s = d.body_shape[b];
+            if (s < 0 || s >= n_shapes) {
+                delete c;
+                return MPCD_ERR_ARG;
+            }
+            body_shape.push_back(s);
+            sites += c->shapes[s].n_sites;
+            // the minimum image must be unique for every centre pair
+            double reach = 2 * c->shapes[s].bound + c->shapes[s].wca_d + 1.2;
+            if (d.n_bodies > 1 && (reach > 0.5 * d.L[0] || reach > 0.5 * d.L[1] || reach > 0.5 * d.L[2])) {
+                delete c;
+                return MPCD_ERR_ARG;
+            }
+        }
+        cells += (int64_t)d.L[0] * d.L[1] * d.L[2];
+        slot += (d.n_solvent + 7) & ~(int64_t)7;
+        bodies += d.n_bodies;
+        rows += d.n_solvent;
+        c->reps.push_back(R);
+    }
+    if (cells >= ((int64_t)1 << 31) || slot >= ((int64_t)1 << 31) || sites >= ((int64_t)1 << 31)) {
+        delete c;
+        return MPCD_ERR_ARG;
+    }
+    c->Ns = rows;
+    c->Nslots = slot + 8;
+    c->C = cells;
+    c->B = bodies;
+    c->Nsite = sites;
+
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return MPCD_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (configure_body_kernels(c->max_sites, p.precision) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return MPCD_ERR_ARG;
+    }
+
+    // device memory
+    auto A = [&](size_t bytes) { return dalloc(c, bytes); };
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        for (int k = 0; k < 6; ++k) ok &= (c->sol[b][k] = A(c->Nslots * c->realsz)) != nullptr;
+        ok &= (c->tag[b] = (uint32_t *)A(c->Nslots * sizeof(uint32_t))) != nullptr;
+    }
+    ok &= (c->sums = A((size_t)c->C * c->nw * 8)) != nullptr;
+    ok &= (c->params = A((size_t)c->C * c->param_bytes)) != nullptr;
+    ok &= (c->d_reps = (DevReplica *)A(c->reps.size() * sizeof(DevReplica))) != nullptr;
+    ok &= (c->d_shapes = (DevShape *)A(std::max<size_t>(1, c->shapes.size()) * sizeof(DevShape))) != nullptr;
+    ok &= (c->d_bodies = (DevBody *)A(std::max<int64_t>(1, c->B) * sizeof(DevBody))) != nullptr;
+    ok &= (c->d_bpos = (float4 *)A(std::max<int64_t>(1, c->B) * sizeof(float4))) != nullptr;
+    ok &= (c->d_tb = (double *)A(std::max<size_t>(1, tb.size()) * 8)) != nullptr;
+    ok &= (c->d_tbf = (float *)A(std::max<size_t>(1, tb.size()) * 4)) != nullptr;
+    ok &= (c->d_tm = (double *)A(std::max<size_t>(1, tm.size()) * 8)) != nullptr;
+    ok &= (c->d_tmf = (float *)A(std::max<size_t>(1, tm.size()) * 4)) != nullptr;
+    ok &= (c->d_tcent = (double *)A(std::max<size_t>(1, tcent.size()) * 8)) != nullptr;
+    ok &= (c->site_v = A(std::max<int64_t>(1, c->Nsite) * 3 * c->realsz)) != nullptr;
+    ok &= (c->site_cell = (int32_t *)A(std::max<int64_t>(1, c->Nsite) * 4)) != nullptr;
+    ok &= (c->d_step = (int64_t *)A(8)) != nullptr;
+    ok &= (c->d_err = (int *)A(8)) != nullptr;
+    ok &= (c->d_diag = (double *)A(16 * 8)) != nullptr;
+    ok &= (c->counts = (int32_t *)A(c->C * 4)) != nullptr;
+    ok &= (c->ex = (int32_t *)A(c->C * 4)) != nullptr;
+    ok &= (c->cursor = (int32_t *)A(c->C * 4)) != nullptr;
+    ok &= (c->scan_bs = (int32_t *)A(scan_block_sums_size(c->C) * 4)) != nullptr;
+    ok &= (c->staging = A(std::max<int64_t>(1, c->Ns) * 6 * c->realsz)) != nullptr;
+    if (!ok) {
+        mpcd_destroy(c);
+        return MPCD_ERR_OOM;
+    }
+    std::vector<float> tbf(tb.begin(), tb.end()), tmf(tm.begin(), tm.end());
+    std::vector<DevBody> hb(std::max<int64_t>(1, c->B));
+    {
+        int64_t site = 0, bi = 0;
+        for (int r = 0; r < n_replicas; ++r)
+            for (int b = 0; b < replicas[r].n_bodies; ++b, ++bi) {
+                DevBody &B = hb[bi];
+                std::memset(&B, 0, sizeof B);
+                B.q[0] = 1.0;
+                B.shape = body_shape[bi];
+                B.rep = r;
+                B.site_begin = site;
+                site += c->shapes[B.shape].n_sites;
+            }
+    }
+    int st = MPCD_OK;
+    auto H2D = [&](void *d, const void *h, size_t n) {
+        if (n && cudaMemcpy(d, h, n, cudaMemcpyHostToDevice) != cudaSuccess) st = MPCD_ERR_CUDA;
+    };
+    H2D(c->d_reps, c->reps.data(), c->reps.size() * sizeof(DevReplica));
+    H2D(c->d_shapes, c->shapes.data(), c->shapes.size() * sizeof(DevShape));
+    H2D(c->d_bodies, hb.data(), c->B * sizeof(DevBody));
+    H2D(c->d_tb, tb.data(), tb.size() * 8);
+    H2D(c->d_tbf, tbf.data(), tbf.size() * 4);
+    H2D(c->d_tm, tm.data(), tm.size() * 8);
+    H2D(c->d_tmf, tmf.data(), tmf.size() * 4);
+    H2D(c->d_tcent, tcent.data(), tcent.size() * 8);
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < 6; ++k)
+            if (cudaMemset(c->sol[b][k], 0, c->Nslots * c->realsz) != cudaSuccess) st = MPCD_ERR_CUDA;
+        if (cudaMemset(c->tag[b], 0xFF, c->Nslots * 4) != cudaSuccess) st = MPCD_ERR_CUDA;
+    }
+    if (cudaMemset(c->sums, 0, (size_t)c->C * c->nw * 8) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (cudaMemset(c->params, 0, (size_t)c->C * c->param_bytes) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (cudaMemset(c->d_step, 0, 8) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (cudaMemset(c->d_err, 0, 8) != cudaSuccess) st = MPCD_ERR_CUDA;
+    build_tiles(c);
+    build_ctiles(c);
+    if (!st) st = upload_tiles(c);
+    if (!st) {
+        c->d_ctiles = (Tile *)dalloc(c, std::max<size_t>(1, c->ctiles.size()) * sizeof(Tile));
+        if (!c->d_ctiles) st = MPCD_ERR_OOM;
+        else H2D(c->d_ctiles, c->ctiles.data(), c->ctiles.size() * sizeof(Tile));
+    }
+    if (!st && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (st) {
+        cudaGetLastError();
+        mpcd_destroy(c);
+        return st;
+    }
+    *out = c;
+    return MPCD_OK;
+}
+
+int mpcd_destroy(mpcd_ctx *c)
+{
+    if (!c) return MPCD_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    clear_graphs(c);
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->evpool) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (void *p : c->allocations) {
+        if (c->use_alloc) c->alloc.free(p, c->alloc.user);
+        else cudaFree(p);
+    }
+    cudaGetLastError();
+    delete c;
+    return MPCD_OK;
+}
+
+int mpcd_sizes(const mpcd_ctx *c, mpcd_sizes_t *o)
+{
+    if (!c || !o) return MPCD_ERR_ARG;
+    o->n_solvent = c->Ns;
+    o->n_bodies = c->B;
+    o->n_sites = c->Nsite;
+    o->n_cells = c->C;
+    o->n_replicas = c->nrep;
+    o->n_shapes = c->nshapes;
+    o->device_bytes = c->dev_bytes;
+    o->sum_words = c->nw;
+    o->param_bytes = c->param_bytes;
+    return MPCD_OK;
+}
+
+const char *mpcd_last_error(const mpcd_ctx *c) { return c ? c->err : "null context"; }
+
+int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
+{
+    CHECK_CTX(c);
+    if (!h || (c->Ns > 0 && (!h->x || !h->v)) || (c->B > 0 && (!h->R || !h->q || !h->P || !h->Lm)) || h->step < 0)
+        return MPCD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(c, cudaSetDevice(c->device));
+    // bodies: conjugate momentum p = 2 q (x) (0, Q^T L)
+    std::vector<DevBody> hb(std::max<int64_t>(1, c->B));
+    if (c->B) CK(c, cudaMemcpy(hb.data(), c->d_bodies, c->B * sizeof(DevBody), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < c->B; ++i) {
+        DevBody &b = hb[i];
+        const DevReplica &R = c->reps[b.rep];
+        double nq = 0;
+        for (int k = 0; k < 4; ++k) nq += h->q[4 * i + k] * h->q[4 * i + k];
+        if (!(std::fabs(nq - 1.0) < 1e-6)) return MPCD_ERR_ARG;
+        for (int k = 0; k < 3; ++k) {
+            double x = h->R[3 * i + k];
+            if (!(x >= 0.0 && x < R.L[k])) return MPCD_ERR_ARG;
+            b.R[k] = x;
+            b.P[k] = h->P[3 * i + k];
+            b.F[k] = b.T[k] = 0.0;
+        }
+        for (int k = 0; k < 4; ++k) b.q[k] = h->q[4 * i + k];
+        for (int k = 0; k < 3; ++k) b.Lm[k] = h->Lm[3 * i + k];
+    }
+    const size_t n3 = (size_t)c->Ns * 3;
+    clear_graphs(c);
+    char *stg = (char *)c->staging;
+    if (c->Ns) {
+        CK(c, cudaMemcpyAsync(stg, h->x, n3 * c->realsz, cudaMemcpyHostToDevice, s));
+        CK(c, cudaMemcpyAsync(stg + n3 * c->realsz, h->v, n3 * c->realsz, cudaMemcpyHostToDevice, s));
+    }
+    c->cur = 0;
+    for (int k = 0; k < 6; ++k) CK(c, cudaMemsetAsync(c->sol[0][k], 0, c->Nslots * c->realsz, s));
+    CK(c, cudaMemsetAsync(c->tag[0], 0xFF, c->Nslots * 4, s));
+    StepArgs a = make_args(c);
+    launch_aos_to_soa(a, stg, stg + n3 * c->realsz, s);
+    if (c->B) CK(c, cudaMemcpyAsync(c->d_bodies, hb.data(), c->B * sizeof(DevBody), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemsetAsync(c->sums, 0, (size_t)c->C * c->nw * 8, s));
+    int64_t stp = h->step;
+    CK(c, cudaMemcpyAsync(c->d_step, &stp, 8, cudaMemcpyHostToDevice, s));
+    launch_body_force(a, 0, s);
+    CK(c, cudaGetLastError());
+    // the upload kernel flags positions outside [0, L): reject the state
+    int flag = 0;
+    CK(c, cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    if (flag) {
+        CK(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        CK(c, cudaMemset(c->tag[0], 0xFF, c->Nslots * 4));
+        return MPCD_ERR_ARG;
+    }
+    c->step = h->step;
+    c->since_sort = 0;
+    c->last_key = -1;
+    // start from cell-sorted storage (memory locality; no effect on results)
+    if (c->prm.sort_period >= 0) {
+        int e = do_sort(c, 0, s);
+        if (e) return e;
+        CK(c, cudaGetLastError());
+    }
+    return MPCD_OK;
+}
+
+int mpcd_get_state(mpcd_ctx *c, mpcd_host_state *h, void *stream)
+{
+    CHECK_CTX(c);
+    if (!h || (c->Ns > 0 && (!h->x || !h->v)) || (c->B > 0 && (!h->R || !h->q || !h->P || !h->Lm)))
+        return MPCD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(c, cudaSetDevice(c->device));
+    const size_t n3 = (size_t)c->Ns * 3;
+    char *stg = (char *)c->staging;
+    StepArgs a = make_args(c);
+    launch_soa_to_aos(a, stg, stg + n3 * c->realsz, nullptr, s);
+    CK(c, cudaGetLastError());
+    if (c->Ns) {
+        CK(c, cudaMemcpyAsync(h->x, stg, n3 * c->realsz, cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(h->v, stg + n3 * c->realsz, n3 * c->realsz, cudaMemcpyDeviceToHost, s));
+    }
+    std::vector<DevBody> hb(std::max<int64_t>(1, c->B));
+    if (c->B) CK(c, cudaMemcpyAsync(hb.data(), c->d_bodies, c->B * sizeof(DevBody), cudaMemcpyDeviceToHost, s));
+    int e = check_device_error(c, s);
+    if (e) return e;
+    for (int64_t i = 0; i < c->B; ++i) {
+        const DevBody &b = hb[i];
+        for (int k = 0; k < 3; ++k) {
+            h->R[3 * i + k] = b.R[k];
+            h->P[3 * i + k] = b.P[k];
+            h->Lm[3 * i + k] = b.Lm[k];
+        }
+        for (int k = 0; k < 4; ++k) h->q[4 * i + k] = b.q[k];
+    }
+    h->step = c->step;
+    return MPCD_OK;
+}
+
+int mpcd_stream(mpcd_ctx *c, void *stream)
+{
+    CHECK_CTX(c);
+    CK(c, cudaSetDevice(c->device));
+    int e = k_stream(c, (cudaStream_t)stream);
+    if (!e) CK(c, cudaGetLastError());
+    return e;
+}
+
+int mpcd_couple(mpcd_ctx *c, int32_t phase, void *stream)
+{
+    CHECK_CTX(c);
+    if (phase != MPCD_PRE && phase != MPCD_POST) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int e = phase == MPCD_PRE ? k_pre(c, s) : k_post(c, s);
+    if (!e && phase == MPCD_POST) e = k_advance(c, s);
+    if (!e) CK(c, cudaGetLastError());
+    return e;
+}
+
+int mpcd_collide(mpcd_ctx *c, void *stream)
+{
+    CHECK_CTX(c);
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int e = k_solvent(c, SOLV_BIN, s);
+    if (!e) e = k_params(c, s);
+    if (!e) e = k_solvent(c, SOLV_COLLIDE, s);
+    if (!e) CK(c, cudaGetLastError());
+    c->last_key = c->step;
+    return e;
+}
+
+int mpcd_step(mpcd_ctx *c, int64_t nsteps, void *stream)
+{
+    CHECK_CTX(c);
+    if (nsteps < 0) return MPCD_ERR_ARG;
+    if (nsteps == 0) return MPCD_OK;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->profiling || nsteps < 2) return run_steps(c, nsteps, s);
+    auto key = std::make_tuple(nsteps, c->cur, c->since_sort);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        const int cur0 = c->cur;
+        const int64_t since0 = c->since_sort, step0 = c->step, key0 = c->last_key;
+        CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int e = run_steps(c, nsteps, c->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+        if (e) {
+            if (g) cudaGraphDestroy(g);
+            return e;
+        }
+        if (ce != cudaSuccess) return fail(c, MPCD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+        GraphEntry ge{};
+        ce = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(c, MPCD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        ge.cur_end = c->cur;
+        ge.since_end = c->since_sort;
+        c->cur = cur0;
+        c->since_sort = since0;
+        c->step = step0;
+        c->last_key = key0;
+        it = c->graphs.emplace(key, ge).first;
+    }
+    CK(c, cudaGraphLaunch(it->second.exec, s));
+    c->cur = it->second.cur_end;
+    c->since_sort = it->second.since_end;
+    c->last_key = c->step + nsteps - 1;
+    c->step += nsteps;
+    return MPCD_OK;
+}
+
+int mpcd_sort(mpcd_ctx *c, int32_t canonical, void *stream)
+{
+    CHECK_CTX(c);
+    CK(c, cudaSetDevice(c->device));
+    int e = do_sort(c, canonical, (cudaStream_t)stream);
+    if (!e) CK(c, cudaGetLastError());
+    return e;
+}
+
+int mpcd_diagnostics(mpcd_ctx *c, mpcd_diag *o, void *stream)
+{
+    CHECK_CTX(c);
+    if (!o) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(c, cudaMemsetAsync(c->d_diag, 0, 16 * 8, s));
+    StepArgs a = make_args(c);
+    launch_solvent_diag(a, c->d_diag, s);
+    launch_body_diag(a, c->d_diag, s);
+    CK(c, cudaGetLastError());
+    double h[16];
+    CK(c, cudaMemcpyAsync(h, c->d_diag, 16 * 8, cudaMemcpyDeviceToHost, s));
+    int e = check_device_error(c, s);
+    if (e) return e;
+    const double m = c->prm.m_solvent;
+    for (int k = 0; k < 3; ++k) {
+        o->p_solvent[k] = m * h[k];
+        o->p_bodies[k] = h[4 + k];
+    }
+    o->ke_solvent = 0.5 * m * h[3];
+    o->ke_trans = h[7];
+    o->ke_rot = h[8];
+    o->step = c->step;
+    return MPCD_OK;
+}
+
+int mpcd_set_debug(mpcd_ctx *c, int32_t on)
+{
+    CHECK_CTX(c);
+    CK(c, cudaSetDevice(c->device));
+    if (on && !c->dbg_sums) {
+        c->dbg_sums = dalloc(c, (size_t)c->C * c->nw * 8);
+        if (!c->dbg_sums) return fail(c, MPCD_ERR_OOM, "debug buffer allocation failed");
+        CK(c, cudaMemset(c->dbg_sums, 0, (size_t)c->C * c->nw * 8));
+    }
+    c->debug = on != 0;
+    clear_graphs(c);
+    return MPCD_OK;
+}
+
+int mpcd_debug_cells(mpcd_ctx *c, void *sums, void *params, int32_t *site_cell, void *site_v, int32_t *shift,
+                     void *stream)
+{
+    CHECK_CTX(c);
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sums) {
+        if (!c->dbg_sums) return MPCD_ERR_ARG;
+        CK(c, cudaMemcpyAsync(sums, c->dbg_sums, (size_t)c->C * c->nw * 8, cudaMemcpyDeviceToHost, s));
+    }
+    if (params) CK(c, cudaMemcpyAsync(params, c->params, (size_t)c->C * c->param_bytes, cudaMemcpyDeviceToHost, s));
+    if (site_cell && c->Nsite)
+        CK(c, cudaMemcpyAsync(site_cell, c->site_cell, c->Nsite * 4, cudaMemcpyDeviceToHost, s));
+    if (site_v && c->Nsite)
+        CK(c, cudaMemcpyAsync(site_v, c->site_v, c->Nsite * 3 * c->realsz, cudaMemcpyDeviceToHost, s));
+    if (shift) {
+        int64_t key = c->last_key >= 0 ? c->last_key : c->step;
+        for (int r = 0; r < c->nrep; ++r) grid_shift(c->reps[r], key, shift + 3 * r);
+    }
+    CK(c, cudaStreamSynchronize(s));
+    return MPCD_OK;
+}
+
+int mpcd_set_profiling(mpcd_ctx *c, int32_t on)
+{
+    CHECK_CTX(c);
+    c->profiling = on != 0;
+    return MPCD_OK;
+}
+
+int mpcd_reset_profile(mpcd_ctx *c)
+{
+    CHECK_CTX(c);
+    int e = drain_profile(c);
+    c->prof.clear();
+    return e;
+}
+
+int mpcd_get_profile(mpcd_ctx *c, mpcd_kernel_time *o, int32_t max)
+{
+    CHECK_CTX(c);
+    int e = drain_profile(c);
+    if (e) return e;
+    int n = 0;
+    for (auto &kv : c->prof) {
+        if (o && n < max) {
+            std::memset(o[n].name, 0, sizeof o[n].name);
+            std::strncpy(o[n].name, kv.first.c_str(), sizeof o[n].name - 1);
+            o[n].launches = kv.second.launches;
+            o[n].total_ms = kv.second.ms;
+            o[n].bytes_per_launch = kv.second.bytes;
+        }
+        ++n;
+    }
+    return n;
+}
+
+int mpcd_get_tuning(const mpcd_ctx *c, mpcd_tuning *o)
+{
+    if (!c || !o) return MPCD_ERR_ARG;
+    *o = c->tune;
+    return MPCD_OK;
+}
+
+int mpcd_set_tuning(mpcd_ctx *c, const mpcd_tuning *t)
+{
+    CHECK_CTX(c);
+    if (!t) return MPCD_ERR_ARG;
+    if (t->block > 0) {
+        if (t->block % 32 || t->block > 512) return MPCD_ERR_ARG;
+        c->tune.block = t->block;
+    }
+    if (t->tile > 0) {
+        if (t->tile < 64) return MPCD_ERR_ARG;
+        c->tune.tile = t->tile;
+    }
+    if (t->ctas_per_sm > 0) c->tune.ctas_per_sm = std::min(t->ctas_per_sm, 32);
+    if (t->sort_period > 0) c->tune.sort_period = t->sort_period;
+    CK(c, cudaSetDevice(c->device));
+    build_tiles(c);
+    int e = upload_tiles(c);
+    clear_graphs(c);
+    return e;
+}
+
+int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
+{
+    CHECK_CTX(c);
+    if (steps_per_trial <= 0) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // snapshot the state (both solvent buffers are restored through `cur`)
+    const size_t sb = c->Nslots * c->realsz;
+    std::vector<void *> save;
+    for (int k = 0; k < 6; ++k) {
+        void *p = dalloc(c, sb);
+        if (!p) return fail(c, MPCD_ERR_OOM, "autotune snapshot");
+        CK(c, cudaMemcpyAsync(p, c->sol[c->cur][k], sb, cudaMemcpyDeviceToDevice, s));
+        save.push_back(p);
+    }
+    void *stag = dalloc(c, c->Nslots * 4), *sbody = dalloc(c, std::max<int64_t>(1, c->B) * sizeof(DevBody));
+    if (!stag || !sbody) return fail(c, MPCD_ERR_OOM, "autotune snapshot");
+    CK(c, cudaMemcpyAsync(stag, c->tag[c->cur], c->Nslots * 4, cudaMemcpyDeviceToDevice, s));
+    CK(c, cudaMemcpyAsync(sbody, c->d_bodies, std::max<int64_t>(1, c->B) * sizeof(DevBody), cudaMemcpyDeviceToDevice, s));
+    const int64_t step0 = c->step, since0 = c->since_sort, key0 = c->last_key;
+    const int cur0 = c->cur;
+    auto restore = [&]() -> int {
+        c->cur = cur0;
+        for (int k = 0; k < 6; ++k) CK(c, cudaMemcpyAsync(c->sol[cur0][k], save[k], sb, cudaMemcpyDeviceToDevice, s));
+        CK(c, cudaMemcpyAsync(c->tag[cur0], stag, c->Nslots * 4, cudaMemcpyDeviceToDevice, s));
+        CK(c, cudaMemcpyAsync(c->d_bodies, sbody, std::max<int64_t>(1, c->B) * sizeof(DevBody), cudaMemcpyDeviceToDevice, s));
+        CK(c, cudaMemcpyAsync(c->d_step, &step0, 8, cudaMemcpyHostToDevice, s));
+        CK(c, cudaStreamSynchronize(s));
+        c->step = step0;
+        c->since_sort = since0;
+        c->last_key = key0;
+        return MPCD_OK;
+    };
+    mpcd_tuning best = c->tune;
+    float best_ms = 1e30f;
+    const int blocks[] = {128, 256, 512};
+    const int tiles_[] = {2048, 8192, 32768};
+    const int ctas[] = {2, 4, 8};
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    const bool prof = c->profiling;
+    c->profiling = false;
+    int st = MPCD_OK;
+    for (int bl : blocks)
+        for (int tl : tiles_)
+            for (int ct : ctas) {
+                if (bl * ct > 2048) continue;
+                mpcd_tuning t{bl, tl, ct, c->tune.sort_period};
+                c->tune = t;
+                build_tiles(c);
+                if ((st = upload_tiles(c))) goto out;
+                if ((st = run_steps(c, 1, s))) goto out;   // warm-up
+                CK(c, cudaEventRecord(e0, s));
+                if ((st = run_steps(c, steps_per_trial, s))) goto out;
+                CK(c, cudaEventRecord(e1, s));
+                CK(c, cudaEventSynchronize(e1));
+                float ms;
+                CK(c, cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+                if ((st = restore())) goto out;
+            }
+out:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->profiling = prof;
+    if (st) return st;
+    c->tune = best;
+    build_tiles(c);
+    clear_graphs(c);
+    return upload_tiles(c);
+}
+
+}  // extern "C"

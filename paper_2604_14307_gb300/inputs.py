@@ -432,6 +432,57 @@ def initial_state(system: System, seed: Optional[int] = None) -> State:
     return State(x=x, v=v, R=R, q=q, P=P, Lm=Lm, step=0)
 
 
+def rsa_spheres(rng: np.random.Generator, L: Sequence[int], n: int, d: float,
+                gap: float = 0.2, batch: int = 65536, max_proposals: int = 50_000_000):
+    """Random sequential addition of up to n equal spheres (centre distance
+    >= d + gap), vectorised: proposals are screened in batches against a grid
+    of the spheres already placed, and the survivors are then added one at a
+    time with a check against the ones added before them in the same batch.
+    Every accepted sphere has been tested against all earlier ones, as in
+    sequential RSA.  Returns centres (k, 3), k <= n."""
+    L = np.asarray(L, dtype=np.float64)
+    dmin = d + gap
+    cs = dmin / math.sqrt(3.0) * 0.999              # at most one centre per grid cell
+    ng = np.maximum((L // cs).astype(int), 1)
+    csz = L / ng
+    reach = int(math.ceil(dmin / csz.min()))
+    grid = -np.ones(tuple(ng), dtype=np.int64)
+    R = np.zeros((n, 3))
+    k, proposals = 0, 0
+    offs = np.array([(a, b, c) for a in range(-reach, reach + 1) for b in range(-reach, reach + 1)
+                     for c in range(-reach, reach + 1)])
+    while k < n and proposals < max_proposals:
+        P = rng.random((batch, 3)) * L
+        proposals += batch
+        cell = np.minimum((P / csz).astype(int), ng - 1)
+        ok = np.ones(batch, dtype=bool)
+        for o in np.array_split(offs, 5):
+            nb = (cell[:, None, :] + o[None, :, :]) % ng
+            idx = grid[nb[..., 0], nb[..., 1], nb[..., 2]]
+            has = idx >= 0
+            dv = P[:, None, :] - R[np.maximum(idx, 0)]
+            dv -= L * np.round(dv / L)
+            close_ = has & ((dv * dv).sum(-1) < dmin * dmin)
+            ok &= ~close_.any(1)
+        for i in np.flatnonzero(ok):
+            if k >= n:
+                break
+            nb = (cell[i] + offs) % ng
+            idx = grid[nb[:, 0], nb[:, 1], nb[:, 2]]
+            idx = idx[idx >= 0]
+            if idx.size:
+                dv = P[i] - R[idx]
+                dv -= L * np.round(dv / L)
+                if ((dv * dv).sum(-1) < dmin * dmin).any():
+                    continue
+            if grid[tuple(cell[i])] >= 0:
+                continue
+            R[k] = P[i]
+            grid[tuple(cell[i])] = k
+            k += 1
+    return R[:k]
+
+
 def build_system(params: Params, shapes: List[Shape], Ls: Sequence[Sequence[int]],
                  density: float, bodies_per_rep: Sequence[Sequence[int]],
                  name: str, placement_seed: int = 12345,
@@ -445,6 +496,11 @@ def build_system(params: Params, shapes: List[Shape], Ls: Sequence[Sequence[int]
         if R_q is not None:
             R, q = R_q[i]
             placed = list(ids)
+        elif ids and len(set(ids)) == 1 and len(shapes[ids[0]].centres) == 1 \
+                and np.allclose(shapes[ids[0]].centres, 0.0):
+            R = rsa_spheres(rng, L, len(ids), shapes[ids[0]].wca_d)
+            q = random_quaternions(rng, len(R))
+            placed = [ids[0]] * len(R)
         else:
             R, q, placed = rsa_place(rng, L, shapes, ids)
         reps.append(Replica(L=L, n_solvent=n_s, body_shapes=list(placed)))

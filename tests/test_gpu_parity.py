@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (stated once, used everywhere):
+  * integer work - cell indices, counts, masses in the fixed-point count|mass
+    word, streamed positions - must be bit-exact;
+  * floating point: |gpu - oracle| <= tol * (|oracle| + scale) with
+    tol = 1e-12 for the FP64 form and 1e-5 for the FP32 form, scale the
+    thermal value of the quantity (sqrt(kT/m) for velocities, sqrt(M kT) for
+    body momenta, sqrt(I kT) for angular momenta).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_14307_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {I.P64: 1e-12, I.P32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14307_gb300 import binding, build_lib
+    build_lib.build()
+    return binding
+
+
+def close(a, b, tol, scale):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    err = np.abs(a - b) / (np.abs(b) + scale)
+    return err.max() if err.size else 0.0
+
+
+def body_scales(system):
+    Ms = np.array([system.shapes[s].m.sum() for s in system.body_shape_array()])
+    Is = np.array([I.shape_inertia_diag(system.shapes[s]).max() for s in system.body_shape_array()])
+    return np.sqrt(Ms)[:, None], np.sqrt(Is)[:, None]
+
+
+def site_mask_cells(osys, tr):
+    """cells that contain at least one site"""
+    m = np.zeros(osys.n_cells, dtype=bool)
+    if osys.n_sites:
+        for r in range(len(osys.L)):
+            b0, b1 = osys.body_off[r], osys.body_off[r + 1]
+            g0, g1 = osys.site_base[b0], osys.site_base[b1]
+            m[osys.cell_base[r] + tr["cell_site"][g0:g1]] = True
+    return m
+
+
+def one_step(B, system, check_sums=True):
+    prec = system.params.precision
+    tol = TOL[prec]
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_debug(True)
+    sim.set_state(st)
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st)
+
+    # a1 + a9: streaming is bit-exact; bodies agree to rounding
+    sim.stream()
+    O.stream(osys, ost)
+    g = sim.get_state()
+    assert np.array_equal(g.x, ost.x)
+    sM, sI = body_scales(system)
+    if osys.n_bodies:
+        assert close(g.R, ost.R, tol, 1.0) < 1e-14
+        assert close(g.q, ost.q, tol, 1.0) < 1e-13
+        assert close(g.P, ost.P, tol, sM) < tol
+        assert close(g.Lm, ost.Lm, tol, sI) < tol
+
+    # a2-a8
+    sim.couple(B.MPCD_PRE)
+    sim.collide()
+    d = sim.debug_cells()
+    sim.couple(B.MPCD_POST)
+    tr = O.collide(osys, ost)
+    ost.step += 1
+
+    assert np.array_equal(d["shift"], tr["shift"])
+    if osys.n_sites:
+        assert np.array_equal(d["site_cell"], tr["cell_site"])
+        ms = np.concatenate([osys.m[osys.site_off[s]:osys.site_off[s + 1]]
+                             for s in osys.body_shape[:osys.n_bodies]])
+        assert close(d["site_v"], tr["site_v"], tol, np.sqrt(1.0 / ms)[:, None]) < tol
+    n = tr["sums"][0]
+    if check_sums:
+        if prec == I.P32:
+            w = d["sums"]
+            # count | mass word: integer, bit-exact everywhere
+            assert np.array_equal(w[0], tr["fixed"][0])
+            # momentum (and energy / AT noise) words: bit-exact where only solvent
+            # enters (identical float inputs); within tolerance where sites enter
+            sm = site_mask_cells(osys, tr)
+            nw = w.shape[0]
+            if system.params.rule == I.SRD:
+                assert np.array_equal(w[1:, ~sm], tr["fixed"][1:, ~sm])
+            else:
+                assert np.array_equal(w[1:4, ~sm], tr["fixed"][1:4, ~sm])
+            M = tr["sums"][1]
+            for k in range(1, nw):
+                diff = np.abs(w[k] - tr["fixed"][k]) * 2.0**-40
+                assert np.all(diff <= tol * (M * 4.0 + 1.0))
+        else:
+            w = d["sums"]
+            assert np.array_equal(w[0], n)
+            assert close(w[1], tr["sums"][1], tol, 1.0) < tol
+            for k in range(2, 5):
+                assert close(w[k], tr["sums"][k], tol, np.sqrt(np.maximum(tr["sums"][1], 1.0))) < tol
+    # cell parameters of every cell that collides
+    sel = n >= 2
+    p = d["params"].astype(np.float64)
+    assert np.all(p[~sel, 3] < 0)
+    assert close(p[sel, 0:3], tr["cell_u"][sel], tol, 1.0) < tol
+    if system.params.rule == I.SRD:
+        assert close(p[sel, 3], tr["cell_kappa"][sel], tol, 1.0) < 5 * tol
+        assert close(p[sel, 4:7], tr["cell_axis"][sel], tol, 1.0) < tol
+    else:
+        assert close(p[sel, 4:7], tr["cell_xibar"][sel], tol, 1.0) < tol
+
+    g = sim.get_state()
+    assert np.array_equal(g.x, ost.x)
+    assert close(g.v, ost.v, tol, 1.0) < tol
+    if osys.n_bodies:
+        assert close(g.P, ost.P, tol, sM) < tol
+        assert close(g.Lm, ost.Lm, tol, sI) < tol
+    assert g.step == 1
+    sim.close()
+    return g, ost
+
+
+@pytest.mark.parametrize("prec", [I.P64, I.P32])
+def test_one_step_single_sphere_L10(B, prec):
+    one_step(B, I.single_sphere_L10(prec))
+
+
+@pytest.mark.parametrize("prec", [I.P64, I.P32])
+@pytest.mark.parametrize("rule,thermo", [(I.SRD, 1), (I.AT, 0)])
+def test_one_step_small_suspension(B, prec, rule, thermo):
+    system = I.suspension(16, 5.0, 0.15, 2.0, 2, 5.0, rule, thermo, prec, seed=3, name="small")
+    assert system.n_bodies >= 3
+    one_step(B, system)
+
+
+@pytest.mark.parametrize("prec", [I.P64, I.P32])
+def test_one_step_suspension_L50(B, prec):
+    """L=50, density 5, 221 radius-3 642-site spheres, MPCD-AT."""
+    one_step(B, I.suspension_L50(prec))
+
+
+def test_one_step_ragged_replicas(B):
+    """Several uneven replicas, one with no colloid and one tiny box."""
+    prm = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=9)
+    shapes = [I.sphere_shape(2.0, 2, 5.0), I.dumbbell_shape(2.0, 2.0, 2, 5.0)]
+    rng = np.random.default_rng(0)
+    Ls = [(12, 12, 12), (3, 3, 3), (9, 14, 11), (20, 20, 20)]
+    ids = [[0, 1], [], [0], [1, 0, 1]]
+    system = I.build_system(prm, shapes, Ls, 3.3, ids, "ragged", placement_seed=5)
+    system.replicas[1].n_solvent = 7          # ragged tail, not a multiple of 4
+    system._placements[1] = (np.zeros((0, 3)), np.zeros((0, 4)))
+    one_step(B, system)
+
+
+def test_pipelined_steps_equal_unfused_bitwise(B):
+    """mpcd_step(n) (fused solvent pass, CUDA graph, re-sorts) reproduces the
+    unfused stream/couple/collide/couple sequence bit for bit (FP32 form)."""
+    for rule in (I.SRD, I.AT):
+        system = I.suspension(16, 5.0, 0.15, 2.0, 2, 5.0, rule, 1, I.P32, seed=4, name="pipe")
+        st = I.initial_state(system)
+        a = B.Simulation(system, sort_period=3)
+        a.set_state(st)
+        a.step(7)
+        a.step(1)
+        ga = a.get_state()
+        b = B.Simulation(system, sort_period=-1)
+        b.set_state(st)
+        for _ in range(8):
+            b.stream()
+            b.couple(B.MPCD_PRE)
+            b.collide()
+            b.couple(B.MPCD_POST)
+        gb = b.get_state()
+        for k in ("x", "v", "R", "q", "P", "Lm"):
+            assert np.array_equal(getattr(ga, k), getattr(gb, k)), (rule, k)
+        assert ga.step == gb.step == 8
+        a.close()
+        b.close()
+
+
+def test_restart_and_input_order_are_bitwise_reproducible(B):
+    system = I.suspension(16, 5.0, 0.15, 2.0, 2, 5.0, I.SRD, 1, I.P32, seed=6, name="restart")
+    st = I.initial_state(system)
+    s1 = B.Simulation(system)
+    s1.set_state(st)
+    s1.step(12)
+    ref = s1.get_state()
+    s1.set_state(st)
+    s1.step(5)
+    mid = s1.get_state()
+    s2 = B.Simulation(system)
+    s2.set_state(mid)
+    s2.step(7)
+    out = s2.get_state()
+    for k in ("x", "v", "R", "q", "P", "Lm"):
+        assert np.array_equal(getattr(out, k), getattr(ref, k)), k
+    # permuted solvent input order: SRD draws are per cell, so the physics is
+    # unchanged and the (permuted-back) result is bit-identical
+    perm = np.random.default_rng(1).permutation(system.n_solvent)
+    stp = st.copy()
+    stp.x, stp.v = st.x[perm], st.v[perm]
+    s3 = B.Simulation(system)
+    s3.set_state(stp)
+    s3.step(12)
+    o3 = s3.get_state()
+    inv = np.argsort(perm)
+    assert np.array_equal(o3.x[inv], ref.x) and np.array_equal(o3.v[inv], ref.v)
+    for s in (s1, s2, s3):
+        s.close()
+
+
+def test_multi_step_fp64_tracks_oracle(B):
+    system = I.suspension(16, 5.0, 0.15, 2.0, 2, 5.0, I.SRD, 1, I.P64, seed=8, name="track")
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.step(10)
+    g = sim.get_state()
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st)
+    O.step(osys, ost, 10)
+    assert np.array_equal(np.floor(g.x * 2**20), np.floor(ost.x * 2**20))
+    assert close(g.v, ost.v, 0, 1.0) < 1e-10
+    sM, sI = body_scales(system)
+    assert close(g.P, ost.P, 0, sM) < 1e-10
+    assert close(g.Lm, ost.Lm, 0, sI) < 1e-10
+    sim.close()
+
+
+def test_conservation_and_canonical_sort(B):
+    system = I.suspension(20, 5.0, 0.2, 2.0, 2, 5.0, I.SRD, 1, I.P32, seed=10, name="cons")
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    d0 = sim.diagnostics()
+    sim.step(20)
+    d1 = sim.diagnostics()
+    p0 = d0["p_solvent"] + d0["p_bodies"]
+    p1 = d1["p_solvent"] + d1["p_bodies"]
+    # FP32 rounding of each updated velocity: random walk ~ sqrt(N steps) ulp
+    assert np.all(np.abs(p1 - p0) < 1e-3 * np.sqrt(system.n_solvent))
+    before = sim.get_state()
+    sim.sort(canonical=True)
+    after = sim.get_state()
+    for k in ("x", "v", "R", "q", "P", "Lm"):
+        assert np.array_equal(getattr(before, k), getattr(after, k))
+    sim.close()
+
+
+def test_invalid_arguments_are_rejected(B):
+    system = I.single_sphere_L10(I.P32)
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    bad = st.copy()
+    bad.x[5, 1] = 10.0        # == L: outside [0, L)
+    with pytest.raises(B.MPCDError) as e:
+        sim.set_state(bad)
+    assert e.value.status == B.MPCD_ERR_ARG
+    sim.set_state(st)         # the context is still usable
+    sim.step(2)
+    with pytest.raises(B.MPCDError):
+        sim.step(-1)
+    sim.close()

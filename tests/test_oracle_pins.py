@@ -139,6 +139,28 @@ def test_fixed_point_sums_are_exact_integer_sums():
     assert np.allclose(tr["fixed"][1:4] * 2.0**-40, tr["sums"][2:5], atol=1e-9)
 
 
+def test_fixed_point_words_of_the_at_rule():
+    """AT form: words are count|mass, m v (3) and m xi (3) - no energy word."""
+    s, st = tiny_system(L=4, density=6.0, precision=I.P32, site_mass=5.0, rule=I.AT)
+    osys, ost, pre, tr = run_collision(s, st)
+    cell, m, v0, _ = members(osys, pre, tr, ost)
+    ref = quantised_sums_numpy(cell, m, v0, 64)
+    assert np.array_equal(tr["fixed"][:4], ref[:4])
+    ns = osys.n_solvent
+    ids = np.concatenate([np.arange(ns), ns + np.arange(osys.n_sites)])
+    xi = O.normals(osys, 0, pre_step(st), ids, O.TAG_AT) * np.sqrt(1.0 / m)[:, None]
+    pf = m.astype(np.float32)[:, None] * xi.astype(np.float32)
+    w = np.rint(pf * np.float32(2.0**40)).astype(np.int64)
+    for a in range(3):
+        out = np.zeros(64, dtype=np.int64)
+        np.add.at(out, cell, w[:, a])
+        assert np.array_equal(tr["fixed"][4 + a], out)
+
+
+def pre_step(st):
+    return st.step
+
+
 # --------------------------------------------------------------- collision ---
 @pytest.mark.parametrize("rule,thermostat", [(I.SRD, 0), (I.SRD, 1), (I.AT, 0)])
 def test_collision_conserves_cell_mass_and_momentum(rule, thermostat):
