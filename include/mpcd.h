@@ -188,11 +188,15 @@ const char *mpcd_last_error(const mpcd_ctx *ctx);
 
 /* Capture buffers for tests.  After mpcd_set_debug(ctx, 1) every collision
  * keeps a copy of its cell sums before they are consumed.
- * sums:      [sum_words][n_cells]; P32 words are int64 fixed point:
- *            w0 = (round(m 2^24) << 16) + 1 summed (count in the low 16 bits),
- *            w1..3 = round(fl32(m v) 2^40), w4 = round(fl32(m v.v) 2^40) (SRD)
- *            or w4..6 = round(fl32(m xi) 2^40) (AT); P64 words are doubles
- *            N, M, m v (3), m v.v (SRD) or m xi (3) (AT).
+ * sums:      [sum_words][n_cells].  P32: int64 words, exact sums over the cell
+ *              w0 = (p_x, p_y), w1 = (p_z, count), p = round(fl32(m v) 2^20),
+ *              SRD: w2 = round(fl32(m v.v) 2^28); AT: w2 = (q_x, q_y),
+ *              w3 = (q_z, 0), q = round(fl32(m xi) 2^20); (hi, lo) is the pair of
+ *              signed 32-bit halves hi 2^32 + lo; count is 1 per solvent particle
+ *              and 2^12 per site.  P64: doubles N, M, m v (3), then m v.v (SRD)
+ *              or m xi (3) (AT).  The P32 form needs one site mass per context,
+ *              at most 4095 solvent particles and 1023 sites per cell and
+ *              |sum m v_a| < 2048 per cell.
  * params:    [n_cells][param_bytes] collision parameters (u, kappa, axis / xibar).
  * site_cell: [n_sites] replica-local cell of every site.
  * site_v:    [n_sites][3] site velocities entering the collision (float/double).
@@ -223,8 +227,10 @@ int mpcd_reset_profile(mpcd_ctx *ctx);
 typedef struct {
     int32_t block;          /* threads per CTA of the solvent pass */
     int32_t tile;           /* particles per work tile */
-    int32_t ctas_per_sm;    /* persistent CTAs per SM */
+    int32_t ctas_per_sm;    /* persistent CTAs per SM (capped by shared memory) */
     int32_t sort_period;    /* steps between re-sorts */
+    int32_t staged;         /* 1: stage tiles in shared memory with bulk async copies,
+                               0: direct 128-bit loads; -1 keeps the current value */
 } mpcd_tuning;
 int mpcd_get_tuning(const mpcd_ctx *ctx, mpcd_tuning *out);
 int mpcd_set_tuning(mpcd_ctx *ctx, const mpcd_tuning *t);

@@ -81,7 +81,7 @@ typedef struct {
     double *site_r;        /* [Nsites][3] stored site positions */
     double *site_v;        /* [Nsites][3] velocities entering the collision */
     double *site_vpost;    /* [Nsites][3] velocities after the collision */
-    int64_t *fixed;        /* [NW][Ctot] fixed-point sums (P32 form) */
+    int64_t *fixed;        /* [4][Ctot] fixed-point cell words (P32 form; SRD uses 3) */
     double *sums;          /* [6][Ctot]: N, M, sum m v (3), sum m v.v */
     double *cell_u;        /* [Ctot][3] */
     double *cell_axis;     /* [Ctot][3] */
@@ -239,17 +239,34 @@ void orc_grid_shift(const orc_sys *s, int rep, int64_t step, int32_t S[3])
 }
 
 /* ------------------------------------------------------------------ */
-/* fixed-point quantisation of the P32 form                            */
+/* fixed-point cell record of the P32 form                              */
 /* ------------------------------------------------------------------ */
-static int64_t q40(float x) { return (int64_t)llrintf(x * 1099511627776.0f); } /* x * 2^40 */
+/* Int64 words per cell, each an exact sum of per-particle integers; a pair
+ * word holds two signed 32-bit halves, hi * 2^32 + lo:
+ *   w0 = (p_x, p_y),  w1 = (p_z, count)        p = round(fl32(m v) 2^20)
+ *   SRD: w2 = round(e 2^28), e = fl32(fl32(fl32(px vx) + fl32(py vy)) + fl32(pz vz))
+ *   AT:  w2 = (q_x, q_y), w3 = (q_z, 0)        q = round(fl32(m xi) 2^20)
+ * count = 1 for a solvent particle, 2^12 for a site (solvent in bits 0-11,
+ * sites in bits 12-21).  Rounding is to nearest, ties to even, of the float
+ * value times the power of two (an exact scaling). */
+static int64_t qs(float x, float pow2) { return (int64_t)llrintf(x * pow2); }
+static int64_t pack2(int64_t hi, int64_t lo) { return (int64_t)((uint64_t)hi << 32) + lo; }
 
-static void fixed_terms(float m, const float v[3], int64_t w[5])
+static void record_terms(float m, const float v[3], int is_site, int rule, int64_t w[4])
 {
-    w[0] = ((int64_t)llrintf(m * 16777216.0f) << 16) + 1;   /* mass * 2^24 | count */
     float px = m * v[0], py = m * v[1], pz = m * v[2];
-    float e = (px * v[0] + py * v[1]) + pz * v[2];
-    /* the sum above is written as three products and two adds, unfused */
-    w[1] = q40(px); w[2] = q40(py); w[3] = q40(pz); w[4] = q40(e);
+    float e = (px * v[0] + py * v[1]) + pz * v[2];   /* unfused: -ffp-contract=off */
+    int64_t cnt = is_site ? ((int64_t)1 << 12) : 1;
+    w[0] = pack2(qs(px, 1048576.0f), qs(py, 1048576.0f));                      /* 2^20 */
+    w[1] = pack2(qs(pz, 1048576.0f), cnt);
+    w[2] = rule == ORC_SRD ? qs(e, 268435456.0f) : 0;                            /* 2^28 */
+    w[3] = 0;
+}
+
+static void unpack2(int64_t w, int64_t *hi, int64_t *lo)
+{
+    *lo = (int64_t)(int32_t)(uint32_t)(w & 0xFFFFFFFF);
+    *hi = (w - *lo) / ((int64_t)1 << 32);
 }
 
 /* ------------------------------------------------------------------ */
@@ -499,7 +516,6 @@ static float f32(double x) { return (float)x; }
 int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
 {
     const int p32 = (s->precision == ORC_P32);
-    const int NW = (s->rule == ORC_AT) ? 7 : 5;
     const double alpha = s->alpha_deg * 3.14159265358979323846264338327950288 / 180.0;
     const double ca = cos(alpha), sa = sin(alpha);
     const int64_t Ns = s->solv_off[s->n_rep];
@@ -633,7 +649,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
             uint32_t lc = (uint32_t)(c - cbase[r]);
             int64_t n = start[c + 1] - start[c];
             double M = 0, pm[3] = { 0, 0, 0 }, e2 = 0;
-            int64_t fx[7] = { 0, 0, 0, 0, 0, 0, 0 };
+            int64_t fx[4] = { 0, 0, 0, 0 };
             for (int64_t k = start[c]; k < start[c + 1]; ++k) {
                 int64_t id = order[k];
                 double m = id < Ns ? s->m_solvent : 0.0;
@@ -647,11 +663,10 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                 M += m;
                 for (int a = 0; a < 3; ++a) { pm[a] += m * v[a]; e2 += m * v[a] * v[a]; }
                 if (p32) {
-                    /* words: count|mass, m v (3), then m v.v (SRD) or m xi (3, AT, below) */
                     float vf[3] = { f32(v[0]), f32(v[1]), f32(v[2]) };
-                    int64_t w[5];
-                    fixed_terms(f32(m), vf, w);
-                    for (int q = 0; q < (s->rule == ORC_AT ? 4 : 5); ++q) fx[q] += w[q];
+                    int64_t w[4];
+                    record_terms(f32(m), vf, id >= Ns, s->rule, w);
+                    for (int q = 0; q < 4; ++q) fx[q] += w[q];
                 }
             }
             double u[3] = { 0, 0, 0 };
@@ -664,7 +679,21 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                 double z = 2.0 * u01(w[0]) - 1.0, ph = 6.283185307179586476925286766559 * u01(w[1]);
                 double rho = sqrt(1.0 - z * z);
                 axis[0] = rho * cos(ph); axis[1] = rho * sin(ph); axis[2] = z;
-                if (s->thermostat) {
+                if (s->thermostat && p32) {
+                    /* P32 form: the kinetic energy entering the thermostat is the
+                     * one its fixed-point sums carry, i.e. of the stored float
+                     * velocities with float32 products m v.v (the same numbers as
+                     * the words above), evaluated here in FP64 */
+                    int64_t h[3], l[3];
+                    unpack2(fx[0], &h[0], &l[0]);
+                    unpack2(fx[1], &h[1], &l[1]);
+                    double S1[3] = { (double)h[0] * 0x1p-20, (double)l[0] * 0x1p-20, (double)h[1] * 0x1p-20 };
+                    double S2 = (double)fx[2] * 0x1p-28, pp = 0.0;
+                    for (int a = 0; a < 3; ++a) pp += S1[a] * S1[a];
+                    double Erel = 0.5 * (S2 - pp / M);
+                    double Ep = thermostat_energy(s, r, st->step, lc, n);
+                    kappa = Erel > 0.0 ? sqrt(Ep / Erel) : 1.0;
+                } else if (s->thermostat) {
                     double Erel = 0.0;
                     for (int64_t k = start[c]; k < start[c + 1]; ++k) {
                         int64_t id = order[k];
@@ -704,23 +733,16 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                         mx[a] += m * sc * nn[a];
                     }
                     if (p32) {
-                        for (int a = 0; a < 3; ++a) {
-                            float pf = f32(m) * f32(sc * nn[a]);
-                            fx[4 + a] += q40(pf);
-                        }
+                        float q[3];
+                        for (int a = 0; a < 3; ++a) q[a] = f32(m) * f32(sc * nn[a]);
+                        fx[2] += pack2(qs(q[0], 1048576.0f), qs(q[1], 1048576.0f));
+                        fx[3] += pack2(qs(q[2], 1048576.0f), 0);
                     }
                 }
                 for (int a = 0; a < 3; ++a) xib[a] = mx[a] / M;
             }
-            if (p32 && tr && tr->fixed) {
-                if (s->rule == ORC_AT) {
-                    /* word order for AT: count|mass, m v (3), m xi (3) */
-                    int64_t t[7] = { fx[0], fx[1], fx[2], fx[3], fx[4], fx[5], fx[6] };
-                    for (int q = 0; q < 7; ++q) tr->fixed[q * Ctot + c] = t[q];
-                } else {
-                    for (int q = 0; q < 5; ++q) tr->fixed[q * Ctot + c] = fx[q];
-                }
-            }
+            if (p32 && tr && tr->fixed)
+                for (int q = 0; q < 4; ++q) tr->fixed[q * Ctot + c] = fx[q];
             if (tr && tr->sums) {
                 tr->sums[0 * Ctot + c] = (double)n; tr->sums[1 * Ctot + c] = M;
                 for (int a = 0; a < 3; ++a) tr->sums[(2 + a) * Ctot + c] = pm[a];
@@ -790,7 +812,6 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
         if (tr->order) memcpy(tr->order, order, (Ns + Nsite) * sizeof(int64_t));
         if (tr->cell_start) memcpy(tr->cell_start, start, (Ctot + 1) * sizeof(int64_t));
     }
-    (void)NW;
 done:
     free(site_base); free(site_body); free(body_rep); free(cbase); free(sv); free(svp); free(sd);
     free(cell_of); free(start); free(order); free(vnew);

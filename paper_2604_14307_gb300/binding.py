@@ -89,7 +89,7 @@ class KernelTime(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("sort_period", C.c_int32)]
+                ("sort_period", C.c_int32), ("staged", C.c_int32)]
 
 
 _lib = None
@@ -350,10 +350,11 @@ class Simulation:
     def tuning(self) -> dict:
         t = Tuning()
         self._check(self.lib.mpcd_get_tuning(self.ctx, C.byref(t)))
-        return dict(block=t.block, tile=t.tile, ctas_per_sm=t.ctas_per_sm, sort_period=t.sort_period)
+        return dict(block=t.block, tile=t.tile, ctas_per_sm=t.ctas_per_sm, sort_period=t.sort_period,
+                    staged=t.staged)
 
-    def set_tuning(self, block=0, tile=0, ctas_per_sm=0, sort_period=0):
-        t = Tuning(block, tile, ctas_per_sm, sort_period)
+    def set_tuning(self, block=0, tile=0, ctas_per_sm=0, sort_period=0, staged=-1):
+        t = Tuning(block, tile, ctas_per_sm, sort_period, staged)
         self._check(self.lib.mpcd_set_tuning(self.ctx, C.byref(t)))
 
     def autotune(self, steps_per_trial: int = 3, stream=None) -> dict:

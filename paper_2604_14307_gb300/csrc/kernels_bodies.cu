@@ -157,6 +157,17 @@ __global__ void k_body_md(StepArgs a)
     for (int k = 0; k < 3; ++k) { o->R[k] = b.R[k]; o->P[k] = b.P[k]; o->Lm[k] = b.Lm[k]; }
     for (int k = 0; k < 4; ++k) o->q[k] = b.q[k];
     a.bpos[i] = make_float4((float)b.R[0], (float)b.R[1], (float)b.R[2], (float)sh.bound);
+    // neighbour lists stay valid while every body is within half the skin of
+    // its position at the last build
+    const float4 p0 = a.bpos_build[i];
+    float d2 = 0.0f;
+    const float Rf[3] = {(float)b.R[0], (float)b.R[1], (float)b.R[2]}, R0[3] = {p0.x, p0.y, p0.z};
+    for (int k = 0; k < 3; ++k) {
+        float d = Rf[k] - R0[k], h = 0.5f * r.L[k];
+        d = d > h ? d - r.L[k] : (d < -h ? d + r.L[k] : d);
+        d2 += d * d;
+    }
+    if (d2 > 0.25f * NLIST_SKIN * NLIST_SKIN) atomicOr(a.nl_dirty, 1);
     if (bad) atomicOr(a.d_err, ERR_POSITION);
 }
 
@@ -184,84 +195,141 @@ __device__ __forceinline__ void min_image(double d[3], const int32_t L[3])
     }
 }
 
+// Forces on body i are summed by lane (j - first) mod 32 in ascending j, then
+// by a fixed shuffle tree, whichever path enumerates the candidates, so the
+// result depends only on the set of interacting pairs.
+__device__ __forceinline__ void pair_force(const StepArgs &a, const DevBody &bi, const DevShape &si,
+                                           const double Qi[9], int64_t j, const DevReplica &r,
+                                           double F[3], double T[3])
+{
+    const double rc_extra = 1.122462048309373;   // 2^(1/6) sigma
+    const DevBody bj = a.bodies[j];
+    const DevShape sj = a.shapes[bj.shape];
+    const double dij = 0.5 * (si.wca_d + sj.wca_d);
+    const double delta = dij - 1.0, rcut = delta + rc_extra;
+    double Qj[9];
+    rotmat(bj.q, Qj);
+    for (int ca = 0; ca < si.n_cent; ++ca) {
+        double c_a[3];
+        mv(Qi, a.tcent + 3 * (si.cent_begin + ca), c_a);
+        for (int cc = 0; cc < sj.n_cent; ++cc) {
+            double c_c[3], dv[3];
+            mv(Qj, a.tcent + 3 * (sj.cent_begin + cc), c_c);
+            for (int k = 0; k < 3; ++k) dv[k] = (bi.R[k] + c_a[k]) - (bj.R[k] + c_c[k]);
+            min_image(dv, r.L);
+            double rr = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+            if (rr > rcut) continue;
+            double s = 1.0 / (rr - delta);
+            double s6 = s * s * s * s * s * s;
+            double fm = 4.0 * (12.0 * s6 * s6 - 6.0 * s6) / (rr - delta);
+            double f[3] = {fm * dv[0] / rr, fm * dv[1] / rr, fm * dv[2] / rr};
+            F[0] += f[0]; F[1] += f[1]; F[2] += f[2];
+            T[0] += c_a[1] * f[2] - c_a[2] * f[1];
+            T[1] += c_a[2] * f[0] - c_a[0] * f[2];
+            T[2] += c_a[0] * f[1] - c_a[1] * f[0];
+        }
+    }
+}
+
+__device__ __forceinline__ bool may_interact(const StepArgs &a, const float4 &pi, const float4 &pj,
+                                             const DevReplica &r, float reach)
+{
+    const float hx = 0.5f * r.L[0], hy = 0.5f * r.L[1], hz = 0.5f * r.L[2];
+    float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+    dx = dx > hx ? dx - r.L[0] : (dx < -hx ? dx + r.L[0] : dx);
+    dy = dy > hy ? dy - r.L[1] : (dy < -hy ? dy + r.L[1] : dy);
+    dz = dz > hz ? dz - r.L[2] : (dz < -hz ? dz + r.L[2] : dz);
+    const float lim = pi.w + pj.w + reach;
+    return dx * dx + dy * dy + dz * dz <= lim * lim;
+}
+
+// candidate neighbours of each body within the bounding spheres + cutoff + skin
+__global__ void k_nlist_build(StepArgs a)
+{
+    if (!*a.nl_dirty) return;
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= a.n_bodies) return;
+    const DevBody &bi = a.bodies[i];
+    const DevShape &si = a.shapes[bi.shape];
+    const DevReplica r = a.reps[bi.rep];
+    const float4 pi = a.bpos[i];
+    const float reach = (float)(0.5 * (si.wca_d + a.max_wca_d) - 1.0 + 1.122462048309373) + NLIST_SKIN + 1e-2f;
+    int count = 0;
+    for (int64_t j0 = r.body_begin; j0 < r.body_end; j0 += 32) {
+        const int64_t j = j0 + lane;
+        bool hit = j < r.body_end && j != i && may_interact(a, pi, a.bpos[j], r, reach);
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        int slot = count + __popc(m & ((1u << lane) - 1u));
+        if (hit && slot < NLIST_MAX) a.nlist[(int64_t)i * NLIST_MAX + slot] = (int32_t)j;
+        count += __popc(m);
+    }
+    if (lane == 0) {
+        a.ncount[i] = count <= NLIST_MAX ? count : -1;
+        a.bpos_build[i] = pi;
+    }
+}
+
+// One thread per body: FP64 forces summed over the candidates in ascending j
+// (the list, or every body when the list overflowed - the same result), the
+// second half kick, and the pose record the site kernels read.
 __global__ void k_body_force(StepArgs a, int kick)
 {
-    const int wid = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (wid >= a.n_bodies) return;
-    const int i = wid;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bodies) return;
     const DevBody bi = a.bodies[i];
     const DevShape si = a.shapes[bi.shape];
     const DevReplica r = a.reps[bi.rep];
     double Qi[9];
     rotmat(bi.q, Qi);
-    const double rc_extra = 1.122462048309373;   // 2^(1/6) sigma
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-    const float4 pi = a.bpos[i];
-    const float hx = 0.5f * r.L[0], hy = 0.5f * r.L[1], hz = 0.5f * r.L[2];
-    const float dmax = (float)(si.wca_d + a.max_wca_d) * 0.5f + (float)rc_extra - 1.0f;
-    for (int64_t j = r.body_begin + lane; j < r.body_end; j += 32) {
-        if (j == i) continue;
-        // bounding-sphere prefilter in FP32 on the compact positions (margin 1e-2)
-        const float4 pj = a.bpos[j];
-        float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        dx = dx > hx ? dx - r.L[0] : (dx < -hx ? dx + r.L[0] : dx);
-        dy = dy > hy ? dy - r.L[1] : (dy < -hy ? dy + r.L[1] : dy);
-        dz = dz > hz ? dz - r.L[2] : (dz < -hz ? dz + r.L[2] : dz);
-        const float lim = pi.w + pj.w + dmax + 1e-2f;
-        if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
-        const DevBody bj = a.bodies[j];
-        const DevShape sj = a.shapes[bj.shape];
-        const double dij = 0.5 * (si.wca_d + sj.wca_d);
-        const double delta = dij - 1.0, rcut = delta + rc_extra;
-        double Qj[9];
-        rotmat(bj.q, Qj);
-        for (int ca = 0; ca < si.n_cent; ++ca) {
-            double c_a[3];
-            mv(Qi, a.tcent + 3 * (si.cent_begin + ca), c_a);
-            for (int cc = 0; cc < sj.n_cent; ++cc) {
-                double c_c[3], dv[3];
-                mv(Qj, a.tcent + 3 * (sj.cent_begin + cc), c_c);
-                for (int k = 0; k < 3; ++k) dv[k] = (bi.R[k] + c_a[k]) - (bj.R[k] + c_c[k]);
-                min_image(dv, r.L);
-                double rr = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-                if (rr > rcut) continue;
-                double s = 1.0 / (rr - delta);
-                double s6 = s * s * s * s * s * s;
-                double fm = 4.0 * (12.0 * s6 * s6 - 6.0 * s6) / (rr - delta);
-                double f[3] = {fm * dv[0] / rr, fm * dv[1] / rr, fm * dv[2] / rr};
-                F[0] += f[0]; F[1] += f[1]; F[2] += f[2];
-                T[0] += c_a[1] * f[2] - c_a[2] * f[1];
-                T[1] += c_a[2] * f[0] - c_a[0] * f[2];
-                T[2] += c_a[0] * f[1] - c_a[1] * f[0];
-            }
+    const int n = a.ncount[i];
+    if (n >= 0 && n <= NLIST_MAX) {
+        for (int e = 0; e < n; ++e) {
+            const int64_t j = a.nlist[(int64_t)i * NLIST_MAX + e];
+            if (j >= r.body_begin && j < r.body_end) pair_force(a, bi, si, Qi, j, r, F, T);
         }
+    } else {
+        const float4 pi = a.bpos[i];
+        const float reach = (float)(0.5 * (si.wca_d + a.max_wca_d) - 1.0 + 1.122462048309373) + 1e-2f;
+        for (int64_t j = r.body_begin; j < r.body_end; ++j)
+            if (j != i && may_interact(a, pi, a.bpos[j], r, reach)) pair_force(a, bi, si, Qi, j, r, F, T);
     }
-    for (int o = 16; o > 0; o >>= 1)
-        for (int k = 0; k < 3; ++k) {
-            F[k] += __shfl_down_sync(0xffffffffu, F[k], o);
-            T[k] += __shfl_down_sync(0xffffffffu, T[k], o);
-        }
-    if (lane == 0) {
-        DevBody *o = a.bodies + i;
-        for (int k = 0; k < 3; ++k) { o->F[k] = F[k]; o->T[k] = T[k]; }
-        if (kick) {
-            double p[4], Lm[3];
-            L_to_p(bi.q, bi.Lm, p);
-            for (int k = 0; k < 3; ++k) o->P[k] = bi.P[k] + 0.5 * a.dt * F[k];
-            torque_kick(bi.q, p, T, 0.5 * a.dt);
-            p_to_L(bi.q, p, Lm);
-            for (int k = 0; k < 3; ++k) o->Lm[k] = Lm[k];
-        }
+    DevBody *o = a.bodies + i;
+    double P[3] = {bi.P[0], bi.P[1], bi.P[2]}, L[3] = {bi.Lm[0], bi.Lm[1], bi.Lm[2]};
+    for (int k = 0; k < 3; ++k) { o->F[k] = F[k]; o->T[k] = T[k]; }
+    if (kick) {
+        double p[4];
+        L_to_p(bi.q, L, p);
+        for (int k = 0; k < 3; ++k) P[k] = bi.P[k] + 0.5 * a.dt * F[k];
+        torque_kick(bi.q, p, T, 0.5 * a.dt);
+        p_to_L(bi.q, p, L);
+        for (int k = 0; k < 3; ++k) { o->P[k] = P[k]; o->Lm[k] = L[k]; }
     }
+    // pose: Q, R, V = P/M, omega = Q Ihat^-1 Q^T L (Eq. 5)
+    double V[3], Lb[3], wb[3], W[3];
+    for (int k = 0; k < 3; ++k) V[k] = P[k] / si.M;
+    mtv(Qi, L, Lb);
+    for (int k = 0; k < 3; ++k) wb[k] = si.Ihat[k] > 0.0 ? Lb[k] / si.Ihat[k] : 0.0;
+    mv(Qi, wb, W);
+    double *p64 = a.pose64 + (int64_t)i * POSE_W;
+    float *p32 = a.pose32 + (int64_t)i * POSE_W;
+    for (int k = 0; k < 9; ++k) { p64[k] = Qi[k]; p32[k] = (float)Qi[k]; }
+    for (int k = 0; k < 3; ++k) {
+        p64[9 + k] = bi.R[k]; p32[9 + k] = (float)bi.R[k];
+        p64[12 + k] = V[k]; p32[12 + k] = (float)V[k];
+        p64[15 + k] = W[k]; p32[15 + k] = (float)W[k];
+    }
+    if (i == 0) *a.nl_dirty = 0;   // the lists used by this step are fresh
 }
 
 void launch_body_force(const StepArgs &a, int kick, cudaStream_t s)
 {
     if (a.n_bodies == 0) return;
     if (!kick) k_body_pos<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
-    int warps_per_block = 4;
-    k_body_force<<<(a.n_bodies + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(a, kick);
+    const int wpb = 4;
+    k_nlist_build<<<(a.n_bodies + wpb - 1) / wpb, 32 * wpb, 0, s>>>(a);
+    k_body_force<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a, kick);
 }
 
 // ---------------------------------------------------------------- sites
@@ -272,12 +340,20 @@ __device__ __forceinline__ float u01f(uint32_t x)
     return __fmaf_rn(__uint2float_rn(x), 2.3283064365386962890625e-10f, 1.16415321826934814453125e-10f);
 }
 __device__ __forceinline__ double u01d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386962890625e-10; }
+// -2 ln u, accurate near u = 1 through the exact complement 1 - u
+__device__ __forceinline__ float neg2log(uint32_t x)
+{
+    return (x & 0x80000000u) ? -2.0f * log1pf(-u01f(~x)) : -2.0f * __logf(u01f(x));
+}
+// Box-Muller; the angles are shifted by pi into [-pi, pi) where the fast
+// sine/cosine are accurate: cos(2 pi u) = -cos(2 pi (u - 1/2))
 __device__ __forceinline__ void normals3(uint4 w, float n[3])
 {
-    float r1 = sqrtf(-2.0f * logf(u01f(w.x))), r2 = sqrtf(-2.0f * logf(u01f(w.z)));
+    const float r1 = sqrtf(neg2log(w.x)), r2 = sqrtf(neg2log(w.z));
     float s1, c1;
-    sincospif(2.0f * u01f(w.y), &s1, &c1);
-    n[0] = r1 * c1; n[1] = r1 * s1; n[2] = r2 * cospif(2.0f * u01f(w.w));
+    __sincosf(6.283185307179586f * (u01f(w.y) - 0.5f), &s1, &c1);
+    n[0] = -r1 * c1; n[1] = -r1 * s1;
+    n[2] = -r2 * __cosf(6.283185307179586f * (u01f(w.w) - 0.5f));
 }
 __device__ __forceinline__ void normals3(uint4 w, double n[3])
 {
@@ -303,85 +379,59 @@ __device__ __forceinline__ int cell_axis(double x, int S, int L)
     return ((unsigned)c < (unsigned)L) ? c : 0;   // only a non-finite position gets here; it is flagged
 
 }
-__device__ __forceinline__ long long q40(float f) { return __float2ll_rn(__fmul_rn(f, 1099511627776.0f)); }
 
 // Site geometry of the two forms.  P32: d = Qf bf in float (three products,
 // two adds), r = fl32(R) + d; P64: d = Q b in double.  Both wrapped into [0, L).
-struct SiteGeomF {
-    float Q[9];
-    __device__ void site(const StepArgs &a, int64_t t, const double R[3], const DevReplica &r, float d[3],
-                         float x[3], int &bad) const
-    {
-        const float *b = a.tbf + 3 * t;
-        for (int k = 0; k < 3; ++k) {
-            float t0 = __fmul_rn(Q[3 * k], b[0]);
-            float t1 = __fmul_rn(Q[3 * k + 1], b[1]);
-            float t2 = __fmul_rn(Q[3 * k + 2], b[2]);
-            d[k] = __fadd_rn(__fadd_rn(t0, t1), t2);
-            x[k] = wrapf(__fadd_rn(__double2float_rn(R[k]), d[k]), (float)r.L[k], bad);
-        }
-    }
+template <typename Real> struct Pose {
+    Real Q[9], R[3], V[3], W[3];
 };
-struct SiteGeomD {
-    double Q[9];
-    __device__ void site(const StepArgs &a, int64_t t, const double R[3], const DevReplica &r, double d[3],
-                         double x[3], int &bad) const
-    {
-        mv(Q, a.tb + 3 * t, d);
-        for (int k = 0; k < 3; ++k) x[k] = wrapd(R[k] + d[k], (double)r.L[k], bad);
+__device__ __forceinline__ void site_geom(const StepArgs &a, int64_t t, const Pose<float> &P, const DevReplica &r,
+                                          float d[3], float x[3], int &bad)
+{
+    const float *b = a.tbf + 3 * t;
+    for (int k = 0; k < 3; ++k) {
+        const float t0 = __fmul_rn(P.Q[3 * k], b[0]);
+        const float t1 = __fmul_rn(P.Q[3 * k + 1], b[1]);
+        const float t2 = __fmul_rn(P.Q[3 * k + 2], b[2]);
+        d[k] = __fadd_rn(__fadd_rn(t0, t1), t2);
+        x[k] = wrapf(__fadd_rn(P.R[k], d[k]), (float)r.L[k], bad);
     }
-};
-template <typename Real> struct Geom;
-template <> struct Geom<float> { typedef SiteGeomF type; };
-template <> struct Geom<double> { typedef SiteGeomD type; };
+}
+__device__ __forceinline__ void site_geom(const StepArgs &a, int64_t t, const Pose<double> &P, const DevReplica &r,
+                                          double d[3], double x[3], int &bad)
+{
+    mv(P.Q, a.tb + 3 * t, d);
+    for (int k = 0; k < 3; ++k) x[k] = wrapd(P.R[k] + d[k], (double)r.L[k], bad);
+}
+__device__ __forceinline__ const float *pose_ptr(const StepArgs &a, int b, float) { return a.pose32 + (int64_t)b * POSE_W; }
+__device__ __forceinline__ const double *pose_ptr(const StepArgs &a, int b, double) { return a.pose64 + (int64_t)b * POSE_W; }
 
 template <typename Real> __device__ __forceinline__ Real site_mass(const StepArgs &a, int64_t t);
 template <> __device__ __forceinline__ float site_mass<float>(const StepArgs &a, int64_t t) { return a.tmf[t]; }
 template <> __device__ __forceinline__ double site_mass<double>(const StepArgs &a, int64_t t) { return a.tm[t]; }
 
-// sum six per-thread values over the CTA into FP64 (out valid in every thread)
+// sum six per-thread values over the CTA in the form's precision (thread 0 gets it)
 template <typename Real>
-__device__ void block_sum6(Real (&v)[6], double (*scratch)[6], double *out)
+__device__ void block_sum6(Real (&v)[6], Real (*scratch)[6], Real *out)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = 0; k < 6; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (lane == 0)
-        for (int k = 0; k < 6; ++k) scratch[wid][k] = (double)v[k];
+        for (int k = 0; k < 6; ++k) scratch[wid][k] = v[k];
     __syncthreads();
     if (threadIdx.x == 0)
         for (int k = 0; k < 6; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += scratch[w][k];
+            Real s = 0;
+            for (int w = 0; w < SITE_WARPS; ++w) s += scratch[w][k];
             out[k] = s;
         }
     __syncthreads();
 }
 
-template <typename Real>
-__device__ __forceinline__ void add_sums(const StepArgs &a, int64_t c, Real m, const Real v[3], const Real xi[3]);
-template <>
-__device__ __forceinline__ void add_sums<float>(const StepArgs &a, int64_t c, float m, const float v[3],
-                                                const float xi[3])
-{
-    unsigned long long *S = reinterpret_cast<unsigned long long *>(a.sums);
-    const int64_t C = a.n_cells;
-    long long w0 = ((long long)__float2ll_rn(__fmul_rn(m, 16777216.0f)) << 16) + 1;
-    float px = __fmul_rn(m, v[0]), py = __fmul_rn(m, v[1]), pz = __fmul_rn(m, v[2]);
-    atomicAdd(S + c, (unsigned long long)w0);
-    atomicAdd(S + C + c, (unsigned long long)q40(px));
-    atomicAdd(S + 2 * C + c, (unsigned long long)q40(py));
-    atomicAdd(S + 3 * C + c, (unsigned long long)q40(pz));
-    if (a.rule == 0) {
-        float e = __fadd_rn(__fadd_rn(__fmul_rn(px, v[0]), __fmul_rn(py, v[1])), __fmul_rn(pz, v[2]));
-        atomicAdd(S + 4 * C + c, (unsigned long long)q40(e));
-    } else {
-        for (int k = 0; k < 3; ++k) atomicAdd(S + (4 + k) * C + c, (unsigned long long)q40(__fmul_rn(m, xi[k])));
-    }
-}
-template <>
-__device__ __forceinline__ void add_sums<double>(const StepArgs &a, int64_t c, double m, const double v[3],
-                                                 const double xi[3])
+// FP64 form: the sites' contributions to the double sum arrays
+__device__ __forceinline__ void add_sums64(const StepArgs &a, int64_t c, double m, const double v[3],
+                                           const double xi[3])
 {
     double *S = reinterpret_cast<double *>(a.sums);
     const int64_t C = a.n_cells;
@@ -405,50 +455,48 @@ template <> __device__ __forceinline__ void load_cell<double>(const StepArgs &a,
     for (int k = 0; k < 4; ++k) { double2 t = r[k]; p[2 * k] = t.x; p[2 * k + 1] = t.y; }
 }
 
+// PRE coupling: site poses, thermal draws, Eq. 7, binning of the sites.
+// Arithmetic in the form's precision only (the pose record carries the FP64
+// body quantities already reduced to it).
 template <typename Real>
-__global__ void __launch_bounds__(128) k_sites_pre(StepArgs a)
+__global__ void __launch_bounds__(SITE_THREADS) k_sites_pre(StepArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     Real *vt = reinterpret_cast<Real *>(smem_raw);          // [n_sites][3] thermal draws
-    __shared__ double sQ[9], sV[3], sOm[3], sVt[3], sOmt[3], sred[6];
-    __shared__ double scratch[4][6];
+    __shared__ Real sPose[POSE_W], sVt[3], sWt[3], sred[6];
+    __shared__ Real scratch[SITE_WARPS][6];
     __shared__ int sS[3];
-    const DevBody B = a.bodies[blockIdx.x];
-    const DevShape sh = a.shapes[B.shape];
-    const DevReplica r = a.reps[B.rep];
+    const DevBody &B = a.bodies[blockIdx.x];
+    const int shape = B.shape, rep = B.rep;
+    const int64_t site_begin = B.site_begin;
+    const DevShape sh = a.shapes[shape];
+    const DevReplica r = a.reps[rep];
     const int64_t step = *a.d_step;
-    if (threadIdx.x == 0) {
-        // V = P/M, omega = I^-1 L with I = Q Ihat Q^T (Eq. 5)
-        double Lb[3], wb[3];
-        rotmat(B.q, sQ);
-        for (int k = 0; k < 3; ++k) sV[k] = B.P[k] / sh.M;
-        mtv(sQ, B.Lm, Lb);
-        for (int k = 0; k < 3; ++k) wb[k] = sh.Ihat[k] > 0.0 ? Lb[k] / sh.Ihat[k] : 0.0;
-        mv(sQ, wb, sOm);
-        grid_shift(r, step, sS);
-    }
+    if (threadIdx.x < POSE_W) sPose[threadIdx.x] = pose_ptr(a, blockIdx.x, Real(0))[threadIdx.x];
+    if (threadIdx.x == 0) grid_shift(r, step, sS);
     __syncthreads();
-    typename Geom<Real>::type G;
-    for (int k = 0; k < 9; ++k) G.Q[k] = (Real)sQ[k];
+    Pose<Real> P;
+    for (int k = 0; k < 9; ++k) P.Q[k] = sPose[k];
+    for (int k = 0; k < 3; ++k) { P.R[k] = sPose[9 + k]; P.V[k] = sPose[12 + k]; P.W[k] = sPose[15 + k]; }
     const Real kT = (Real)a.kT;
     const int n = sh.n_sites;
     int bad = 0;
     Real acc[6] = {0, 0, 0, 0, 0, 0};
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int64_t t = sh.site_begin + j, g = B.site_begin + j;
+        const int64_t t = sh.site_begin + j, g = site_begin + j;
         Real d[3], x[3];
-        G.site(a, t, B.R, r, d, x, bad);
-        int c = cell_axis(x[0], sS[0], r.L[0]) +
-                r.L[0] * (cell_axis(x[1], sS[1], r.L[1]) + r.L[1] * cell_axis(x[2], sS[2], r.L[2]));
+        site_geom(a, t, P, r, d, x, bad);
+        const int c = cell_axis(x[0], sS[0], r.L[0]) +
+                      r.L[0] * (cell_axis(x[1], sS[1], r.L[1]) + r.L[1] * cell_axis(x[2], sS[2], r.L[2]));
         a.site_cell[g] = c;
         if (!a.naive) {
             const Real m = site_mass<Real>(a, t);
             Real nn[3];
             normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_SITE, 0u), nn);
             const Real sc = sqrt(kT / m);
-            Real w[3] = {sc * nn[0], sc * nn[1], sc * nn[2]};
+            const Real w[3] = {sc * nn[0], sc * nn[1], sc * nn[2]};
             for (int k = 0; k < 3; ++k) vt[3 * j + k] = w[k];
-            Real p[3] = {m * w[0], m * w[1], m * w[2]};
+            const Real p[3] = {m * w[0], m * w[1], m * w[2]};
             acc[0] += p[0]; acc[1] += p[1]; acc[2] += p[2];
             acc[3] += d[1] * p[2] - d[2] * p[1];
             acc[4] += d[2] * p[0] - d[0] * p[2];
@@ -458,76 +506,104 @@ __global__ void __launch_bounds__(128) k_sites_pre(StepArgs a)
     block_sum6<Real>(acc, scratch, sred);
     if (threadIdx.x == 0) {
         if (a.naive) {
-            for (int k = 0; k < 3; ++k) { sVt[k] = 0.0; sOmt[k] = 0.0; }
+            for (int k = 0; k < 3; ++k) { sVt[k] = 0; sWt[k] = 0; }
         } else {
-            // omega~ = Q Ihat^-1 Q^T L~ (the space-frame inertia of the sites)
-            double Lt[3] = {sred[3], sred[4], sred[5]}, lb[3], wb[3];
-            for (int k = 0; k < 3; ++k) sVt[k] = sred[k] / sh.M;
-            mtv(sQ, Lt, lb);
-            for (int k = 0; k < 3; ++k) wb[k] = sh.Ihat[k] > 0.0 ? lb[k] / sh.Ihat[k] : 0.0;
-            mv(sQ, wb, sOmt);
+            // V~ = sum m v~ / M, omega~ = Q Ihat^-1 Q^T L~
+            Real lb[3], wb[3];
+            for (int k = 0; k < 3; ++k) sVt[k] = sred[k] / (Real)sh.M;
+            for (int k = 0; k < 3; ++k)
+                lb[k] = (P.Q[k] * sred[3] + P.Q[3 + k] * sred[4]) + P.Q[6 + k] * sred[5];
+            for (int k = 0; k < 3; ++k) wb[k] = sh.Ihat[k] > 0.0 ? lb[k] / (Real)sh.Ihat[k] : Real(0);
+            for (int k = 0; k < 3; ++k)
+                sWt[k] = (P.Q[3 * k] * wb[0] + P.Q[3 * k + 1] * wb[1]) + P.Q[3 * k + 2] * wb[2];
         }
     }
     __syncthreads();
-    const Real dV[3] = {(Real)(sV[0] - sVt[0]), (Real)(sV[1] - sVt[1]), (Real)(sV[2] - sVt[2])};
-    const Real dW[3] = {(Real)(sOm[0] - sOmt[0]), (Real)(sOm[1] - sOmt[1]), (Real)(sOm[2] - sOmt[2])};
+    const Real dV[3] = {P.V[0] - sVt[0], P.V[1] - sVt[1], P.V[2] - sVt[2]};
+    const Real dW[3] = {P.W[0] - sWt[0], P.W[1] - sWt[1], P.W[2] - sWt[2]};
     Real *SV = reinterpret_cast<Real *>(a.site_v);
     const int64_t NS = a.n_sites;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int64_t t = sh.site_begin + j, g = B.site_begin + j;
-        Real d[3], x[3];
-        G.site(a, t, B.R, r, d, x, bad);
-        Real v[3];
-        v[0] = dV[0] + (dW[1] * d[2] - dW[2] * d[1]);
-        v[1] = dV[1] + (dW[2] * d[0] - dW[0] * d[2]);
-        v[2] = dV[2] + (dW[0] * d[1] - dW[1] * d[0]);
-        if (!a.naive)
-            for (int k = 0; k < 3; ++k) v[k] += vt[3 * j + k];
-        for (int k = 0; k < 3; ++k) SV[k * NS + g] = v[k];
-        const Real m = site_mass<Real>(a, t);
-        Real xi[3] = {0, 0, 0};
-        if (a.rule == 1) {
-            normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
-            const Real sc = sqrt(kT / m);
-            xi[0] *= sc; xi[1] *= sc; xi[2] *= sc;
+    // uniform trip count: every lane reaches the warp-wide record flush
+    for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        const bool valid = j < n;
+        Real v[3] = {0, 0, 0}, xi[3] = {0, 0, 0}, m = Real(0);
+        int cell = 0;
+        if (valid) {
+            const int64_t t = sh.site_begin + j, g = site_begin + j;
+            Real d[3], x[3];
+            site_geom(a, t, P, r, d, x, bad);
+            v[0] = dV[0] + (dW[1] * d[2] - dW[2] * d[1]);
+            v[1] = dV[1] + (dW[2] * d[0] - dW[0] * d[2]);
+            v[2] = dV[2] + (dW[0] * d[1] - dW[1] * d[0]);
+            if (!a.naive)
+                for (int k = 0; k < 3; ++k) v[k] += vt[3 * j + k];
+            for (int k = 0; k < 3; ++k) SV[k * NS + g] = v[k];
+            m = site_mass<Real>(a, t);
+            if (a.rule == 1) {
+                normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
+                const Real sc = sqrt(kT / m);
+                xi[0] *= sc; xi[1] *= sc; xi[2] *= sc;
+            }
+            cell = r.cell_base + a.site_cell[g];
         }
-        add_sums<Real>(a, (int64_t)r.cell_base + a.site_cell[g], m, v, xi);
+        if (valid) {
+            if constexpr (sizeof(Real) == 4) {
+                long long w[4];
+                unsigned long long *S = reinterpret_cast<unsigned long long *>(a.sums);
+                if (a.rule == 0) {
+                    record_terms<0>(m, v[0], v[1], v[2], xi, true, w);
+                    for (int k = 0; k < 3; ++k) atomicAdd(S + k * a.n_cells + cell, (unsigned long long)w[k]);
+                } else {
+                    record_terms<1>(m, v[0], v[1], v[2], xi, true, w);
+                    for (int k = 0; k < 4; ++k) atomicAdd(S + k * a.n_cells + cell, (unsigned long long)w[k]);
+                }
+            } else {
+                add_sums64(a, cell, m, v, xi);
+            }
+        }
     }
     if (bad) atomicOr(a.d_err, ERR_POSITION);
 }
 
+// POST coupling: site collision and the per-warp partial sums of the
+// momentum dP = sum m (v' - v) and angular momentum dL = sum d x m (v' - v)
+// transferred to the body (Eqs. 3-4); k_body_impulse adds them in FP64.
 template <typename Real>
-__global__ void __launch_bounds__(128) k_sites_post(StepArgs a)
+__global__ void __launch_bounds__(SITE_THREADS) k_sites_post(StepArgs a)
 {
-    __shared__ double sQ[9], sred[6];
-    __shared__ double scratch[4][6];
-    const DevBody B = a.bodies[blockIdx.x];
+    __shared__ Real sPose[POSE_W];
+    const DevBody &B = a.bodies[blockIdx.x];
+    const int64_t site_begin = B.site_begin;
     const DevShape sh = a.shapes[B.shape];
     const DevReplica r = a.reps[B.rep];
     const int64_t step = *a.d_step;
-    if (threadIdx.x == 0) rotmat(B.q, sQ);
+    if (threadIdx.x < POSE_W) sPose[threadIdx.x] = pose_ptr(a, blockIdx.x, Real(0))[threadIdx.x];
     __syncthreads();
-    typename Geom<Real>::type G;
-    for (int k = 0; k < 9; ++k) G.Q[k] = (Real)sQ[k];
+    Pose<Real> P;
+    for (int k = 0; k < 9; ++k) P.Q[k] = sPose[k];
+    for (int k = 0; k < 3; ++k) { P.R[k] = sPose[9 + k]; P.V[k] = 0; P.W[k] = 0; }
     const Real kT = (Real)a.kT, ca = (Real)a.cos_a, sa = (Real)a.sin_a;
     const Real *SV = reinterpret_cast<const Real *>(a.site_v);
     const int64_t NS = a.n_sites;
     int bad = 0;
     Real acc[6] = {0, 0, 0, 0, 0, 0};
     for (int j = threadIdx.x; j < sh.n_sites; j += blockDim.x) {
-        const int64_t t = sh.site_begin + j, g = B.site_begin + j;
+        const int64_t t = sh.site_begin + j, g = site_begin + j;
         Real d[3], x[3];
-        G.site(a, t, B.R, r, d, x, bad);
-        Real v[3] = {SV[g], SV[NS + g], SV[2 * NS + g]}, vn[3] = {v[0], v[1], v[2]};
+        site_geom(a, t, P, r, d, x, bad);
+        const Real v[3] = {SV[g], SV[NS + g], SV[2 * NS + g]};
+        Real vn[3] = {v[0], v[1], v[2]};
         Real p[8];
         load_cell<Real>(a, (int64_t)r.cell_base + a.site_cell[g], p);
         const Real m = site_mass<Real>(a, t);
         if (p[3] >= Real(0)) {
             if (a.rule == 0) {
-                Real w[3] = {v[0] - p[0], v[1] - p[1], v[2] - p[2]};
-                Real nd = p[4] * w[0] + p[5] * w[1] + p[6] * w[2];
-                Real cx = p[5] * w[2] - p[6] * w[1], cy = p[6] * w[0] - p[4] * w[2], cz = p[4] * w[1] - p[5] * w[0];
-                Real tt = nd * (Real(1) - ca);
+                const Real w[3] = {v[0] - p[0], v[1] - p[1], v[2] - p[2]};
+                const Real nd = p[4] * w[0] + p[5] * w[1] + p[6] * w[2];
+                const Real cx = p[5] * w[2] - p[6] * w[1], cy = p[6] * w[0] - p[4] * w[2];
+                const Real cz = p[4] * w[1] - p[5] * w[0];
+                const Real tt = nd * (Real(1) - ca);
                 vn[0] = p[0] + p[3] * (w[0] * ca + cx * sa + p[4] * tt);
                 vn[1] = p[1] + p[3] * (w[1] * ca + cy * sa + p[5] * tt);
                 vn[2] = p[2] + p[3] * (w[2] * ca + cz * sa + p[6] * tt);
@@ -538,22 +614,36 @@ __global__ void __launch_bounds__(128) k_sites_post(StepArgs a)
                 for (int k = 0; k < 3; ++k) vn[k] = p[k] + sc * xi[k] - p[4 + k];
             }
         }
-        Real dp[3] = {m * (vn[0] - v[0]), m * (vn[1] - v[1]), m * (vn[2] - v[2])};
+        const Real dp[3] = {m * (vn[0] - v[0]), m * (vn[1] - v[1]), m * (vn[2] - v[2])};
         acc[0] += dp[0]; acc[1] += dp[1]; acc[2] += dp[2];
         acc[3] += d[1] * dp[2] - d[2] * dp[1];
         acc[4] += d[2] * dp[0] - d[0] * dp[2];
         acc[5] += d[0] * dp[1] - d[1] * dp[0];
     }
-    block_sum6<Real>(acc, scratch, sred);
-    if (threadIdx.x == 0) {
-        // impulse: P += dP, L += dL (Eqs. 3-4)
-        DevBody *o = a.bodies + blockIdx.x;
-        for (int k = 0; k < 3; ++k) {
-            o->P[k] = B.P[k] + sred[k];
-            o->Lm[k] = B.Lm[k] + sred[3 + k];
-        }
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    if ((threadIdx.x & 31) == 0) {
+        Real *out = reinterpret_cast<Real *>(a.partial) + ((int64_t)blockIdx.x * SITE_WARPS + (threadIdx.x >> 5)) * 6;
+        for (int k = 0; k < 6; ++k) out[k] = acc[k];
     }
     if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+// impulse P += dP, L += dL accumulated in FP64 from the per-warp partials
+template <typename Real>
+__global__ void k_body_impulse(StepArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bodies) return;
+    const Real *in = reinterpret_cast<const Real *>(a.partial) + (int64_t)i * SITE_WARPS * 6;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < SITE_WARPS; ++w)
+        for (int k = 0; k < 6; ++k) s[k] += (double)in[w * 6 + k];
+    DevBody *o = a.bodies + i;
+    for (int k = 0; k < 3; ++k) {
+        o->P[k] += s[k];
+        o->Lm[k] += s[3 + k];
+    }
 }
 
 cudaError_t configure_body_kernels(int max_sites, int precision)
@@ -569,16 +659,23 @@ void launch_sites_pre(const StepArgs &a, int max_sites, cudaStream_t s)
 {
     if (a.n_bodies == 0) return;
     if (a.precision == 1)
-        k_sites_pre<float><<<a.n_bodies, 128, (size_t)max_sites * 3 * sizeof(float), s>>>(a);
+        k_sites_pre<float><<<a.n_bodies, SITE_THREADS, (size_t)max_sites * 3 * sizeof(float), s>>>(a);
     else
-        k_sites_pre<double><<<a.n_bodies, 128, (size_t)max_sites * 3 * sizeof(double), s>>>(a);
+        k_sites_pre<double><<<a.n_bodies, SITE_THREADS, (size_t)max_sites * 3 * sizeof(double), s>>>(a);
 }
 
 void launch_sites_post(const StepArgs &a, int, cudaStream_t s)
 {
     if (a.n_bodies == 0) return;
-    if (a.precision == 1) k_sites_post<float><<<a.n_bodies, 128, 0, s>>>(a);
-    else k_sites_post<double><<<a.n_bodies, 128, 0, s>>>(a);
+    if (a.precision == 1) k_sites_post<float><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+    else k_sites_post<double><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+}
+
+void launch_body_impulse(const StepArgs &a, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    if (a.precision == 1) k_body_impulse<float><<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
+    else k_body_impulse<double><<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
 }
 
 __global__ void k_advance_step(int64_t *step) { *step += 1; }

@@ -32,16 +32,24 @@ __device__ __forceinline__ double u01d(uint32_t x)
     return ((double)x + 0.5) * 2.3283064365386962890625e-10;     // (x + 1/2) 2^-32
 }
 
-// three standard normals from one Philox block (Box-Muller)
+// -2 ln u for u = (x + 1/2) 2^-32 with full relative precision also near u = 1,
+// where 1 - u = (~x + 1/2) 2^-32 is formed exactly from the integer complement
+__device__ __forceinline__ float neg2log(uint32_t x)
+{
+    return (x & 0x80000000u) ? -2.0f * log1pf(-u01f(~x)) : -2.0f * __logf(u01f(x));
+}
+
+// three standard normals from one Philox block (Box-Muller); the angles are
+// shifted by pi into [-pi, pi) where the fast sine/cosine are accurate
 __device__ __forceinline__ void normals3(uint4 w, float n[3])
 {
-    float r1 = sqrtf(-2.0f * logf(u01f(w.x)));
-    float r2 = sqrtf(-2.0f * logf(u01f(w.z)));
+    const float r1 = sqrtf(neg2log(w.x));
+    const float r2 = sqrtf(neg2log(w.z));
     float s1, c1;
-    sincospif(2.0f * u01f(w.y), &s1, &c1);
-    n[0] = r1 * c1;
-    n[1] = r1 * s1;
-    n[2] = r2 * cospif(2.0f * u01f(w.w));
+    __sincosf(6.283185307179586f * (u01f(w.y) - 0.5f), &s1, &c1);
+    n[0] = -r1 * c1;
+    n[1] = -r1 * s1;
+    n[2] = -r2 * __cosf(6.283185307179586f * (u01f(w.w) - 0.5f));
 }
 __device__ __forceinline__ void normals3(uint4 w, double n[3])
 {
@@ -91,10 +99,6 @@ __device__ __forceinline__ double drift(double x, double v, double dt, double L,
     return y;
 }
 
-__device__ __forceinline__ long long q40(float f)
-{
-    return __float2ll_rn(__fmul_rn(f, 1099511627776.0f));   // f * 2^40, exact scaling
-}
 
 __device__ __forceinline__ void ld4(const float *p, float (&o)[4])
 {
@@ -174,35 +178,17 @@ __device__ __forceinline__ void srd_rotate(const CellParams<Real> &p, Real ca, R
 
 // word count of the cell sums
 template <typename Real, int RULE> struct NWords;
-template <> struct NWords<float, 0> { static constexpr int n = 5; };
-template <> struct NWords<float, 1> { static constexpr int n = 7; };
+template <> struct NWords<float, 0> { static constexpr int n = 3; };
+template <> struct NWords<float, 1> { static constexpr int n = 4; };
 template <> struct NWords<double, 0> { static constexpr int n = 6; };
 template <> struct NWords<double, 1> { static constexpr int n = 8; };
 template <typename Real> struct SumWord { typedef double type; };
 template <> struct SumWord<float> { typedef long long type; };
 
-// contributions of one particle of mass m and velocity v (and AT noise xi)
+// FP64 form: contributions of one particle (mass m, velocity v, AT noise xi)
+// to the double sum arrays N, M, m v (3), m v.v (SRD) or m xi (3) (AT)
 template <int RULE>
-__device__ __forceinline__ void terms(long long w0, float m, float vx, float vy, float vz,
-                                      const float *xi, long long *w)
-{
-    float px = __fmul_rn(m, vx), py = __fmul_rn(m, vy), pz = __fmul_rn(m, vz);
-    w[0] = w0;
-    w[1] = q40(px);
-    w[2] = q40(py);
-    w[3] = q40(pz);
-    if (RULE == 0) {
-        float e = __fadd_rn(__fadd_rn(__fmul_rn(px, vx), __fmul_rn(py, vy)), __fmul_rn(pz, vz));
-        w[4] = q40(e);
-    } else {
-        w[4] = q40(__fmul_rn(m, xi[0]));
-        w[5] = q40(__fmul_rn(m, xi[1]));
-        w[6] = q40(__fmul_rn(m, xi[2]));
-    }
-}
-template <int RULE>
-__device__ __forceinline__ void terms(long long, double m, double vx, double vy, double vz,
-                                      const double *xi, double *w)
+__device__ __forceinline__ void terms64(double m, double vx, double vy, double vz, const double *xi, double *w)
 {
     w[0] = 1.0;
     w[1] = m;
@@ -218,11 +204,72 @@ __device__ __forceinline__ void terms(long long, double m, double vx, double vy,
     }
 }
 
+// backward run totals over a thread's 4 consecutive particles: T[j] is the sum
+// of the run that starts at j (static indices only)
+__device__ __forceinline__ unsigned run_totals(const int (&c)[4], int nv, long long (&w)[4][4])
+{
+#pragma unroll
+    for (int j = 2; j >= 0; --j)
+        if (j + 1 < nv && c[j + 1] == c[j])
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[j][k] += w[j + 1][k];
+    unsigned heads = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j < nv && (j == 0 || c[j] != c[j - 1])) heads |= 1u << j;
+    return heads;
+}
+
 __device__ __forceinline__ void red_add(long long *p, long long v)
 {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
 }
 __device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); }
+
+// Binning of a thread's 4 consecutive particles: cell under the shift S,
+// per-particle fixed-point (P32) or double (P64) terms, runs of equal cells
+// merged in registers, then one atomic per word and run.
+template <typename Real, int RULE, bool COLLIDE, typename W>
+__device__ __forceinline__ void bin4(const StepArgs &a, const Real (&x)[4], const Real (&y)[4], const Real (&z)[4],
+                                     const Real (&vx)[4], const Real (&vy)[4], const Real (&vz)[4],
+                                     const uint32_t (&tg)[4], int nv, const int32_t *S, int L0, int L1, int L2,
+                                     int base, const DevReplica &rr, int64_t step, Real m, Real sc, W *sums,
+                                     int64_t C)
+{
+    int cc[4];
+    Real xi[4][3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        cc[j] = base + cell_axis(x[j], S[0], L0) + L0 * (cell_axis(y[j], S[1], L1) + L1 * cell_axis(z[j], S[2], L2));
+        xi[j][0] = xi[j][1] = xi[j][2] = Real(0);
+        if (RULE == 1 && j < nv) {
+            normals3(draw(rr, step + (COLLIDE ? 1 : 0), tg[j], TAG_AT, 0u), xi[j]);
+            xi[j][0] *= sc; xi[j][1] *= sc; xi[j][2] *= sc;
+        }
+    }
+    if constexpr (sizeof(Real) == 4) {
+        constexpr int NW = Words32<RULE>::n;
+        long long w[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) record_terms<RULE>(m, vx[j], vy[j], vz[j], xi[j], false, w[j]);
+        const unsigned heads = run_totals(cc, nv, w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((heads >> j) & 1u)
+#pragma unroll
+                for (int k = 0; k < NW; ++k) red_add(sums + k * C + cc[j], w[j][k]);
+    } else {
+        constexpr int NW = RULE == 0 ? 6 : 8;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= nv) break;
+            double w[NW];
+            terms64<RULE>(m, vx[j], vy[j], vz[j], xi[j], w);
+#pragma unroll
+            for (int k = 0; k < NW; ++k) red_add(sums + k * C + cc[j], w[k]);
+        }
+    }
+}
 
 // --------------------------------------------------------------- the pass
 template <typename Real, int RULE, int FLAGS>
@@ -283,8 +330,6 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
                 uint4 t4 = __ldcs(reinterpret_cast<const uint4 *>(a.tag + i));
                 tg[0] = t4.x; tg[1] = t4.y; tg[2] = t4.z; tg[3] = t4.w;
             }
-            int run_c = -1;
-            W acc[NW];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (j >= nv) break;
@@ -309,34 +354,9 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
                     y[j] = drift(y[j], vy[j], dt, Ly, bad);
                     z[j] = drift(z[j], vz[j], dt, Lz, bad);
                 }
-                if (BIN) {
-                    int c = base + cell_axis(x[j], sS[3], L0) +
-                            L0 * (cell_axis(y[j], sS[4], L1) + L1 * cell_axis(z[j], sS[5], L2));
-                    Real xi[3] = {0, 0, 0};
-                    if (RULE == 1) {
-                        normals3(draw(rr, step + (COLLIDE ? 1 : 0), tg[j], TAG_AT, 0u), xi);
-                        xi[0] *= sc; xi[1] *= sc; xi[2] *= sc;
-                    }
-                    W w[NW];
-                    terms<RULE>(a.w0_solvent, m, vx[j], vy[j], vz[j], xi, w);
-                    if (c == run_c) {
-#pragma unroll
-                        for (int k = 0; k < NW; ++k) acc[k] += w[k];
-                    } else {
-                        if (run_c >= 0) {
-#pragma unroll
-                            for (int k = 0; k < NW; ++k) red_add(sums + k * C + run_c, acc[k]);
-                        }
-                        run_c = c;
-#pragma unroll
-                        for (int k = 0; k < NW; ++k) acc[k] = w[k];
-                    }
-                }
             }
-            if (BIN && run_c >= 0) {
-#pragma unroll
-                for (int k = 0; k < NW; ++k) red_add(sums + k * C + run_c, acc[k]);
-            }
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+                                                m, sc, sums, C);
             if (STREAM) { st4(X + i, x); st4(Y + i, y); st4(Z + i, z); }
             if (COLLIDE) { st4(VX + i, vx); st4(VY + i, vy); st4(VZ + i, vz); }
         }
@@ -344,9 +364,281 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
     if (bad) atomicOr(a.d_err, ERR_POSITION);
 }
 
+// ------------------------------------------- staged pass (bulk async copies)
+// The same per-particle arithmetic as k_solvent, but each CTA streams its
+// tiles through a two-stage shared-memory ring: thread 0 issues one
+// cp.async.bulk per SoA array (completion counted on an mbarrier) for tile
+// k+1 while the CTA computes tile k, and writes results back with bulk
+// stores.  Memory-level parallelism is then set by the copy engine, not by
+// the number of resident warps.  Every mbarrier wait is bounded.
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity)
+{
+    for (uint32_t i = 0; i < SPIN_LIMIT; ++i)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(b))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void sld4(const float *p, float (&o)[4])
+{
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void sld4(const double *p, double (&o)[4])
+{
+    double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void sst4(float *p, const float (&o)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void sst4(double *p, const double (&o)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
+}
+
+template <typename Real, int RULE>
+__host__ __device__ constexpr size_t stage_bytes(int cap)
+{
+    return ((size_t)cap * (6 * sizeof(Real) + (RULE == 1 ? 4 : 0)) + 127) & ~(size_t)127;
+}
+
+template <typename Real, int RULE, int FLAGS>
+__global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
+{
+    constexpr bool COLLIDE = FLAGS & SOLV_COLLIDE;
+    constexpr bool STREAM = FLAGS & SOLV_STREAM;
+    constexpr bool BIN = FLAGS & SOLV_BIN;
+    constexpr int NW = NWords<Real, RULE>::n;
+    typedef typename SumWord<Real>::type W;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int32_t sS[6];
+    __shared__ int32_t sL[3];
+    __shared__ int32_t sbase, scount;
+    __shared__ uint32_t skey[2];
+
+    const size_t SB = stage_bytes<Real, RULE>(cap);
+    const int64_t step = *a.d_step;
+    const Real dt = Consts<Real>::dt(a), m = Consts<Real>::m(a), kT = Consts<Real>::kT(a);
+    const Real ca = Consts<Real>::ca(a), sa = Consts<Real>::sa(a);
+    const Real sc = sqrt(kT / m);
+    Real *G[6] = {reinterpret_cast<Real *>(a.x), reinterpret_cast<Real *>(a.y), reinterpret_cast<Real *>(a.z),
+                  reinterpret_cast<Real *>(a.vx), reinterpret_cast<Real *>(a.vy), reinterpret_cast<Real *>(a.vz)};
+    W *sums = reinterpret_cast<W *>(a.sums);
+    const int64_t C = a.n_cells;
+    int bad = 0;
+
+    auto issue_load = [&](int tile, int stage) {
+        const Tile tl = a.tiles[tile];
+        const int n4 = (int)((tl.end - tl.begin + 3) & ~(int64_t)3);
+        const uint32_t nb = (uint32_t)(n4 * sizeof(Real));
+        unsigned char *base = smem + stage * SB;
+        mbar_expect_tx(&bar[stage], 6 * nb + (RULE == 1 ? (uint32_t)(n4 * 4) : 0u));
+        for (int k = 0; k < 6; ++k) bulk_load(base + (size_t)k * cap * sizeof(Real), G[k] + tl.begin, nb, &bar[stage]);
+        if (RULE == 1) bulk_load(base + (size_t)6 * cap * sizeof(Real), a.tag + tl.begin, (uint32_t)(n4 * 4), &bar[stage]);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x < a.n_tiles) issue_load(blockIdx.x, 0);
+    uint32_t phase0 = 0, phase1 = 0;
+    int k = 0;
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++k) {
+        const int st = k & 1;
+        int64_t beg = 0;
+        if (threadIdx.x == 0) {
+            const int tn = t + gridDim.x;
+            if (tn < a.n_tiles) {
+                bulk_wait_read_all();          // stage st^1 was last stored from; reuse it
+                issue_load(tn, st ^ 1);
+            }
+            const Tile tl = a.tiles[t];
+            const DevReplica r = a.reps[tl.rep];
+            sL[0] = r.L[0]; sL[1] = r.L[1]; sL[2] = r.L[2];
+            sbase = r.cell_base;
+            scount = (int)(tl.end - tl.begin);
+            skey[0] = r.key0;
+            skey[1] = r.key1;
+            if (COLLIDE) grid_shift(r, step, &sS[0]);
+            if (BIN) grid_shift(r, step + (COLLIDE ? 1 : 0), &sS[3]);
+        }
+        __syncthreads();
+        const bool got = mbar_wait_bounded(&bar[st], st ? phase1 : phase0);
+        if (!__syncthreads_and(got)) {
+            if (threadIdx.x == 0) {
+                atomicOr(a.d_err, ERR_TIMEOUT);
+                bulk_wait_all();
+                mbar_wait_bounded(&bar[st ^ 1], st ? phase0 : phase1);
+            }
+            return;
+        }
+        if (st) phase1 ^= 1; else phase0 ^= 1;
+        const int L0 = sL[0], L1 = sL[1], L2 = sL[2], base = sbase, n = scount;
+        const Real Lx = (Real)L0, Ly = (Real)L1, Lz = (Real)L2;
+        DevReplica rr;
+        rr.key0 = skey[0];
+        rr.key1 = skey[1];
+        Real *S[6];
+        for (int q = 0; q < 6; ++q) S[q] = reinterpret_cast<Real *>(smem + st * SB + (size_t)q * cap * sizeof(Real));
+        const uint32_t *stag = reinterpret_cast<const uint32_t *>(smem + st * SB + (size_t)6 * cap * sizeof(Real));
+
+        // uniform trip count: every lane of a warp reaches the warp-wide flush
+        for (int i0 = 0; i0 < n; i0 += 4 * blockDim.x) {
+            const int i = i0 + 4 * threadIdx.x;
+            const int nv = max(0, min(4, n - i));
+            Real x[4], y[4], z[4], vx[4], vy[4], vz[4];
+            if (nv > 0) {
+                sld4(S[0] + i, x); sld4(S[1] + i, y); sld4(S[2] + i, z);
+                sld4(S[3] + i, vx); sld4(S[4] + i, vy); sld4(S[5] + i, vz);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[j] = y[j] = z[j] = vx[j] = vy[j] = vz[j] = Real(0);
+            }
+            uint32_t tg[4] = {0, 0, 0, 0};
+            if (RULE == 1 && nv > 0) {
+                uint4 t4 = *reinterpret_cast<const uint4 *>(stag + i);
+                tg[0] = t4.x; tg[1] = t4.y; tg[2] = t4.z; tg[3] = t4.w;
+            }
+            if (COLLIDE) {
+                // issue the four parameter gathers before any of them is used
+                CellParams<Real> p[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int c = base + cell_axis(x[j], sS[0], L0) +
+                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    c = j < nv ? c : base;
+                    p[j] = get_params<Real>(a.params, c);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j < nv && p[j].kappa >= Real(0)) {
+                        if (RULE == 0) {
+                            srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
+                        } else {
+                            Real nn[3];
+                            normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn);
+                            vx[j] = p[j].ux + sc * nn[0] - p[j].ax;
+                            vy[j] = p[j].uy + sc * nn[1] - p[j].ay;
+                            vz[j] = p[j].uz + sc * nn[2] - p[j].az;
+                        }
+                    }
+                }
+            }
+            if (STREAM) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < nv) {
+                        x[j] = drift(x[j], vx[j], dt, Lx, bad);
+                        y[j] = drift(y[j], vy[j], dt, Ly, bad);
+                        z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                    }
+            }
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+                                                m, sc, sums, C);
+            if (nv > 0) {
+                if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
+                if (COLLIDE) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0 && (STREAM || COLLIDE)) {
+            const Tile tl = a.tiles[t];
+            beg = tl.begin;
+            const uint32_t nb = (uint32_t)(((n + 3) & ~3) * sizeof(Real));
+            if (STREAM)
+                for (int q = 0; q < 3; ++q) bulk_store(G[q] + beg, S[q], nb);
+            if (COLLIDE)
+                for (int q = 3; q < 6; ++q) bulk_store(G[q] + beg, S[q], nb);
+            bulk_commit();
+        }
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+template <typename Real, int RULE, int FLAGS>
+static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
+{
+    static bool configured = false;   // opt in to large dynamic shared memory once
+    const size_t bytes = solvent_smem_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap, cfg.block);
+    if (!configured) {
+        cudaFuncSetAttribute(k_solvent_staged<Real, RULE, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        configured = true;
+    }
+    k_solvent_staged<Real, RULE, FLAGS><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
+}
+
 template <typename Real, int RULE>
 static void dispatch_flags(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s)
 {
+    if (cfg.staged) {
+        switch (flags) {
+        case SOLV_STREAM: launch_staged<Real, RULE, SOLV_STREAM>(a, cfg, s); break;
+        case SOLV_BIN: launch_staged<Real, RULE, SOLV_BIN>(a, cfg, s); break;
+        case SOLV_COLLIDE: launch_staged<Real, RULE, SOLV_COLLIDE>(a, cfg, s); break;
+        case SOLV_STREAM | SOLV_BIN: launch_staged<Real, RULE, SOLV_STREAM | SOLV_BIN>(a, cfg, s); break;
+        case SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN:
+            launch_staged<Real, RULE, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN>(a, cfg, s);
+            break;
+        default: break;
+        }
+        return;
+    }
     switch (flags) {
     case SOLV_STREAM: k_solvent<Real, RULE, SOLV_STREAM><<<cfg.grid, cfg.block, 0, s>>>(a); break;
     case SOLV_BIN: k_solvent<Real, RULE, SOLV_BIN><<<cfg.grid, cfg.block, 0, s>>>(a); break;
@@ -373,26 +665,40 @@ void launch_solvent(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s)
     }
 }
 
+size_t solvent_stage_bytes(int precision, int rule, int cap)
+{
+    if (precision == 1) return rule == 0 ? stage_bytes<float, 0>(cap) : stage_bytes<float, 1>(cap);
+    return rule == 0 ? stage_bytes<double, 0>(cap) : stage_bytes<double, 1>(cap);
+}
+
+size_t solvent_smem_bytes(int precision, int rule, int cap, int)
+{
+    return 2 * solvent_stage_bytes(precision, rule, cap);
+}
+
 // ------------------------------------------------------- cell parameters
 // Gamma(n/2, 1) variate for n = 3(Nc - 1): floor(n/2) unit exponentials plus
-// z^2/2 when n is odd (Eq. 6).  FP32 form: four uniforms per logarithm.
+// z^2/2 when n is odd (Eq. 6).  FP32 form: one fast logarithm per pair of
+// uniforms (the product of two is >= 2^-66, never subnormal).
 __device__ float gamma_half_dof(const DevReplica &r, int64_t step, uint32_t lc, int n_dof, float)
 {
-    int nE = n_dof / 2;
+    const int nE = n_dof / 2;
     float g = 0.0f;
-#pragma unroll 4
+#pragma unroll 2
     for (int j = 0; 4 * j < nE; ++j) {
-        uint4 w = draw(r, step, lc, TAG_THERMO, (uint32_t)j);
-        int k = nE - 4 * j;
-        float prod = u01f(w.x);
-        if (k > 1) prod *= u01f(w.y);
-        if (k > 2) prod *= u01f(w.z);
-        if (k > 3) prod *= u01f(w.w);
-        g -= logf(prod);
+        const uint4 w = draw(r, step, lc, TAG_THERMO, (uint32_t)j);
+        const int k = nE - 4 * j;
+        float p0 = u01f(w.x), p1 = 1.0f;
+        if (k > 1) p0 *= u01f(w.y);
+        if (k > 2) p1 = u01f(w.z);
+        if (k > 3) p1 *= u01f(w.w);
+        g -= __logf(p0) + __logf(p1);
     }
     if (n_dof & 1) {
-        uint4 w = draw(r, step, lc, TAG_THERMO_ODD, 0u);
-        float z = sqrtf(-2.0f * logf(u01f(w.x))) * cospif(2.0f * u01f(w.y));
+        const uint4 w = draw(r, step, lc, TAG_THERMO_ODD, 0u);
+        float sn, cs;
+        __sincosf(6.283185307179586f * (u01f(w.y) - 0.5f), &sn, &cs);   // cos(2 pi u) = -cs
+        const float z = sqrtf(neg2log(w.x)) * cs;
         g += 0.5f * z * z;
     }
     return g;
@@ -415,6 +721,112 @@ __device__ double gamma_half_dof(const DevReplica &r, int64_t step, uint32_t lc,
     return g;
 }
 
+// signed 128-bit -> float by magnitude (|error| <= 2 ulp)
+__device__ __forceinline__ float i128f(__int128 x)
+{
+    const bool neg = x < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
+    const float f = fmaf(ull2f((unsigned long long)(u >> 64)), 18446744073709551616.0f,
+                         ull2f((unsigned long long)u));
+    return neg ? -f : f;
+}
+
+// Relative kinetic energy E_rel = (S2 - |S1|^2 / M) / 2 of a cell from its exact
+// fixed-point sums, without cancellation: about a fixed-point reference
+// velocity w0 ~ u,  sum m|v - w0|^2 = S2 - 2 w0.S1 + M |w0|^2 is formed in exact
+// int128 arithmetic and E_rel = (that - |S1 - M w0|^2 / M) / 2.
+// Units: S1 of 2^-20, S2 of 2^-28, Mq of 2^-24, w0 of 2^-20; products of 2^-64.
+__device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long S1[3], long long S2, float M,
+                                                  const float u[3])
+{
+    int W[3];
+    long long W2 = 0;
+    __int128 D = (__int128)S2 << 36;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        W[k] = __float2int_rn(fminf(fmaxf(u[k] * 1048576.0f, -5.0e8f), 5.0e8f));
+        D -= ((__int128)W[k] * S1[k]) << 25;
+        W2 += (long long)W[k] * W[k];
+    }
+    D += (__int128)Mq * W2;
+    float r = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const __int128 dk = ((__int128)S1[k] << 44) - (((__int128)Mq * W[k]) << 20);
+        const float df = i128f(dk) * 5.421010862427522170037264e-20f;   // 2^-64
+        r += df * df;
+    }
+    const float e2 = i128f(D) * 5.421010862427522170037264e-20f - r / M;
+    return 0.5f * fmaxf(e2, 0.0f);
+}
+
+// FP32 form: cell words -> collision parameters with FP32/integer pipes only
+template <int RULE>
+__global__ void __launch_bounds__(256) k_params32(StepArgs a)
+{
+    constexpr int NW = Words32<RULE>::n;
+    const int64_t step = *a.d_step;
+    long long *sums = reinterpret_cast<long long *>(a.sums);
+    long long *dbg = reinterpret_cast<long long *>(a.dbg_sums);
+    const int64_t C = a.n_cells;
+    const float kT = a.kTf;
+    const float s20 = 9.5367431640625e-07f;   // 2^-20
+    for (int t = blockIdx.x; t < a.n_ctiles; t += gridDim.x) {
+        const Tile tl = a.ctiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        for (int64_t c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
+            long long w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                w[k] = sums[k * C + c];
+                sums[k * C + c] = 0;
+                if (dbg) dbg[k * C + c] = w[k];
+            }
+            long long S1[3], cnt;
+            unpack2(w[0], S1[0], S1[1]);
+            unpack2(w[1], S1[2], cnt);
+            const int ns = (int)(cnt & 0xFFF), nb = (int)((cnt >> 12) & 0x3FF), n = ns + nb;
+            float rec[8] = {0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, 0.f};
+            if (n >= 2) {
+                const long long Mq = (long long)ns * a.qm_solvent + (long long)nb * a.qm_site;
+                const float M = (float)ns * a.m_solvent_f + (float)nb * a.m_site_f;
+                const float iM = 1.0f / M;
+                float u[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) u[k] = ll2f(S1[k]) * s20 * iM;
+                rec[0] = u[0]; rec[1] = u[1]; rec[2] = u[2];
+                const uint32_t lc = (uint32_t)(c - r.cell_base);
+                if (RULE == 0) {
+                    // axis: z = u1 - (1 - u1), rho = 2 sqrt(u1 (1 - u1)), phi = 2 pi u2
+                    const uint4 wa = draw(r, step, lc, TAG_AXIS, 0u);
+                    const float ua = u01f(wa.x), ub = u01f(~wa.x);
+                    const float zz = ua - ub, rho = 2.0f * sqrtf(ua * ub);
+                    float sn, cs;
+                    __sincosf(6.283185307179586f * (u01f(wa.y) - 0.5f), &sn, &cs);   // angle shifted by pi
+                    rec[4] = -rho * cs; rec[5] = -rho * sn; rec[6] = zz;
+                    float kappa = 1.0f;
+                    if (a.thermostat) {
+                        const float erel = rel_energy_fixed(Mq, S1, w[2], M, u);
+                        const float g = gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
+                        kappa = erel > 0.0f ? sqrtf(kT * g / erel) : 1.0f;
+                    }
+                    rec[3] = kappa;
+                } else {
+                    long long qx, qy, qz, zero;
+                    unpack2(w[2], qx, qy);
+                    unpack2(w[3], qz, zero);
+                    rec[3] = 1.0f;
+                    rec[4] = ll2f(qx) * s20 * iM; rec[5] = ll2f(qy) * s20 * iM; rec[6] = ll2f(qz) * s20 * iM;
+                }
+            }
+            float4 *o = reinterpret_cast<float4 *>(a.params) + 2 * c;
+            o[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
+            o[1] = make_float4(rec[4], rec[5], rec[6], 0.0f);
+        }
+    }
+}
+
+// FP64 form (plain): the same parameters in double precision
 template <typename Real, int RULE>
 __global__ void __launch_bounds__(256) k_params(StepArgs a)
 {
@@ -439,15 +851,7 @@ __global__ void __launch_bounds__(256) k_params(StepArgs a)
             }
             int n;
             Real M, p[3], s2 = 0, xi[3] = {0, 0, 0};
-            if (sizeof(Real) == 4) {
-                long long w0 = (long long)w[0];
-                n = (int)(w0 & 0xFFFF);
-                M = (Real)(w0 >> 16) * (Real)5.9604644775390625e-8;            // 2^-24
-                const Real s = (Real)9.094947017729282379150390625e-13;        // 2^-40
-                for (int k = 0; k < 3; ++k) p[k] = (Real)(long long)w[1 + k] * s;
-                if (RULE == 0) s2 = (Real)(long long)w[4] * s;
-                else for (int k = 0; k < 3; ++k) xi[k] = (Real)(long long)w[4 + k] * s;
-            } else {
+            {
                 n = (int)(double)w[0];
                 M = (Real)(double)w[1];
                 for (int k = 0; k < 3; ++k) p[k] = (Real)(double)w[2 + k];
@@ -462,30 +866,18 @@ __global__ void __launch_bounds__(256) k_params(StepArgs a)
                 if (RULE == 0) {
                     uint4 wa = draw(r, step, lc, TAG_AXIS, 0u);
                     Real zz, sp, cp;
-                    if (sizeof(Real) == 4) {
-                        zz = (Real)(2.0f * u01f(wa.x) - 1.0f);
-                        float s_, c_;
-                        sincospif(2.0f * u01f(wa.y), &s_, &c_);
-                        sp = s_; cp = c_;
-                    } else {
+                    Real rho;
+                    {
                         zz = (Real)(2.0 * u01d(wa.x) - 1.0);
+                        rho = (Real)sqrt(1.0 - (double)zz * (double)zz);
                         double s_, c_;
                         sincos(6.283185307179586476925286766559 * u01d(wa.y), &s_, &c_);
                         sp = (Real)s_; cp = (Real)c_;
                     }
-                    Real rho = sqrt(Real(1) - zz * zz);
                     rec[4] = rho * cp; rec[5] = rho * sp; rec[6] = zz;
                     Real kappa = Real(1);
                     if (a.thermostat) {
                         Real erel = Real(0.5) * (s2 - (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) / M);
-                        if (sizeof(Real) == 4 && erel < s2 * Real(0.015625)) {
-                            // strong cancellation: redo E_rel in FP64 from the exact sums
-                            const double sc = 9.094947017729282379150390625e-13;
-                            double q1 = (double)(long long)w[1] * sc, q2 = (double)(long long)w[2] * sc;
-                            double q3 = (double)(long long)w[3] * sc, e2 = (double)(long long)w[4] * sc;
-                            double Md = (double)((long long)w[0] >> 16) * 5.9604644775390625e-8;
-                            erel = (Real)(0.5 * (e2 - (q1 * q1 + q2 * q2 + q3 * q3) / Md));
-                        }
                         Real g = gamma_half_dof(r, step, lc, 3 * (n - 1), Real(0));
                         kappa = erel > Real(0) ? sqrt(kT * g / erel) : Real(1);
                     }
@@ -511,13 +903,13 @@ __global__ void __launch_bounds__(256) k_params(StepArgs a)
     if (err) atomicOr(a.d_err, ERR_CELL);
 }
 
-void launch_params(const StepArgs &a, int grid, cudaStream_t s)
+void launch_params(const StepArgs &a, int, cudaStream_t s)
 {
     if (a.n_ctiles == 0) return;
-    grid = grid < a.n_ctiles ? grid : a.n_ctiles;
+    const int grid = a.n_ctiles;   // one 256-cell tile per CTA, one cell per thread
     if (a.precision == 1) {
-        if (a.rule == 0) k_params<float, 0><<<grid, 256, 0, s>>>(a);
-        else k_params<float, 1><<<grid, 256, 0, s>>>(a);
+        if (a.rule == 0) k_params32<0><<<grid, 256, 0, s>>>(a);
+        else k_params32<1><<<grid, 256, 0, s>>>(a);
     } else {
         if (a.rule == 0) k_params<double, 0><<<grid, 256, 0, s>>>(a);
         else k_params<double, 1><<<grid, 256, 0, s>>>(a);

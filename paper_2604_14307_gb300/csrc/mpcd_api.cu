@@ -46,6 +46,7 @@ struct mpcd_ctx {
 
     int nrep = 0, nshapes = 0, max_sites = 0;
     double max_wca_d = 0.0;
+    double m_site = 0.0;   // the common site mass (required by the P32 form)
     int64_t Ns = 0, Nslots = 0, B = 0, Nsite = 0, C = 0;
     int nw = 0, realsz = 0, param_bytes = 0;
     std::vector<DevReplica> reps;
@@ -59,7 +60,12 @@ struct mpcd_ctx {
     int64_t tiles_cap = 0;
     DevShape *d_shapes = nullptr;
     DevBody *d_bodies = nullptr;
-    float4 *d_bpos = nullptr;
+    float4 *d_bpos = nullptr, *d_bpos_build = nullptr;
+    int32_t *d_nlist = nullptr, *d_ncount = nullptr;
+    int *d_nl_dirty = nullptr;
+    float *d_pose32 = nullptr;
+    double *d_pose64 = nullptr;
+    void *d_partial = nullptr;
     double *d_tb = nullptr, *d_tm = nullptr, *d_tcent = nullptr;
     float *d_tbf = nullptr, *d_tmf = nullptr;
     void *sol[2][6] = {};
@@ -77,7 +83,8 @@ struct mpcd_ctx {
 
     int64_t step = 0, since_sort = 0, last_key = -1;
     int num_sms = 0;
-    mpcd_tuning tune{256, 8192, 4, 20};
+    mpcd_tuning tune{256, 2048, 2, 20, 1};
+    int smem_per_sm = 0;
 
     bool profiling = false;
     std::vector<Pending> pending;
@@ -154,7 +161,9 @@ StepArgs make_args(const mpcd_ctx *c)
     a.m_solvent_f = (float)p.m_solvent;
     a.cos_af = (float)a.cos_a;
     a.sin_af = (float)a.sin_a;
-    a.w0_solvent = ((long long)std::llrint((double)(a.m_solvent_f * 16777216.0f)) << 16) + 1;
+    a.qm_solvent = (long long)std::llrint((double)a.m_solvent_f * 16777216.0);
+    a.m_site_f = (float)c->m_site;
+    a.qm_site = (long long)std::llrint((double)a.m_site_f * 16777216.0);
     a.reps = c->d_reps;
     a.n_rep = c->nrep;
     a.tiles = c->d_tiles;
@@ -175,6 +184,13 @@ StepArgs make_args(const mpcd_ctx *c)
     a.nw = c->nw;
     a.bodies = c->d_bodies;
     a.bpos = c->d_bpos;
+    a.bpos_build = c->d_bpos_build;
+    a.nlist = c->d_nlist;
+    a.ncount = c->d_ncount;
+    a.nl_dirty = c->d_nl_dirty;
+    a.pose32 = c->d_pose32;
+    a.pose64 = c->d_pose64;
+    a.partial = c->d_partial;
     a.n_bodies = (int32_t)c->B;
     a.shapes = c->d_shapes;
     a.tb = c->d_tb;
@@ -194,7 +210,7 @@ StepArgs make_args(const mpcd_ctx *c)
 void build_tiles(mpcd_ctx *c)
 {
     c->tiles.clear();
-    const int64_t T = std::max<int64_t>(64, c->tune.tile & ~(int64_t)7);
+    const int64_t T = c->tune.tile;   // a multiple of 8 (set_tuning rounds it)
     for (int r = 0; r < c->nrep; ++r) {
         const DevReplica &R = c->reps[r];
         for (int64_t b = R.solv_begin; b < R.solv_begin + R.n_solvent; b += T)
@@ -205,7 +221,7 @@ void build_tiles(mpcd_ctx *c)
 void build_ctiles(mpcd_ctx *c)
 {
     c->ctiles.clear();
-    const int64_t T = 2048;
+    const int64_t T = 256;   // the parameter and canonical-sort kernels take one tile per CTA
     for (int r = 0; r < c->nrep; ++r) {
         const DevReplica &R = c->reps[r];
         int64_t n = (int64_t)R.L[0] * R.L[1] * R.L[2];
@@ -281,10 +297,29 @@ double solvent_bytes(const mpcd_ctx *c, int flags)
 }
 
 // ----------------------------------------------------------- step pieces
+bool staged_fits(const mpcd_ctx *c, int tile, int block)
+{
+    return solvent_smem_bytes(c->prm.precision, c->prm.rule, tile, block) <= 200 * 1024;
+}
+
+LaunchCfg solvent_cfg(const mpcd_ctx *c)
+{
+    LaunchCfg cfg{c->tune.block, 1, c->tune.staged && staged_fits(c, c->tune.tile, c->tune.block) ? 1 : 0,
+                  c->tune.tile};
+    int per_sm = c->tune.ctas_per_sm;
+    if (cfg.staged) {
+        size_t bytes = solvent_smem_bytes(c->prm.precision, c->prm.rule, c->tune.tile, c->tune.block) + 1024;
+        per_sm = std::max(1, std::min<int>(per_sm, (int)(c->smem_per_sm / bytes)));
+    }
+    per_sm = std::max(1, std::min(per_sm, 2048 / c->tune.block));
+    cfg.grid = std::max(1, std::min((int)c->tiles.size(), c->num_sms * per_sm));
+    return cfg;
+}
+
 int k_stream(mpcd_ctx *c, cudaStream_t s)
 {
     StepArgs a = make_args(c);
-    LaunchCfg cfg{c->tune.block, std::max(1, std::min((int)c->tiles.size(), c->num_sms * c->tune.ctas_per_sm))};
+    LaunchCfg cfg = solvent_cfg(c);
     int e = timed(c, "solvent_stream", solvent_bytes(c, SOLV_STREAM), s, [&] { launch_solvent(a, SOLV_STREAM, cfg, s); });
     if (e) return e;
     e = timed(c, "body_md", 0, s, [&] { launch_body_md(a, s); });
@@ -318,13 +353,15 @@ int k_post(mpcd_ctx *c, cudaStream_t s)
 {
     StepArgs a = make_args(c);
     double bytes = (double)c->Nsite * (3.0 * c->realsz + 4.0);
-    return timed(c, "sites_post", bytes, s, [&] { launch_sites_post(a, c->max_sites, s); });
+    int e = timed(c, "sites_post", bytes, s, [&] { launch_sites_post(a, c->max_sites, s); });
+    if (e) return e;
+    return timed(c, "body_impulse", 0, s, [&] { launch_body_impulse(a, s); });
 }
 
 int k_solvent(mpcd_ctx *c, int flags, cudaStream_t s)
 {
     StepArgs a = make_args(c);
-    LaunchCfg cfg{c->tune.block, std::max(1, std::min((int)c->tiles.size(), c->num_sms * c->tune.ctas_per_sm))};
+    LaunchCfg cfg = solvent_cfg(c);
     const char *name = flags == (SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN) ? "solvent_fused"
                        : flags == SOLV_COLLIDE                          ? "solvent_collide"
                        : flags == SOLV_BIN                              ? "solvent_bin"
@@ -439,7 +476,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     c->nrep = n_replicas;
     c->nshapes = n_shapes;
     c->realsz = p.precision == MPCD_P32 ? 4 : 8;
-    c->nw = p.precision == MPCD_P32 ? (p.rule == MPCD_SRD ? 5 : 7) : (p.rule == MPCD_SRD ? 6 : 8);
+    c->nw = p.precision == MPCD_P32 ? (p.rule == MPCD_SRD ? 3 : 4) : (p.rule == MPCD_SRD ? 6 : 8);
     c->param_bytes = p.precision == MPCD_P32 ? 32 : 64;
     if (p.sort_period > 0) c->tune.sort_period = p.sort_period;
 
@@ -475,6 +512,12 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
                             std::fabs(d.m[j] * b[1] * b[2])});
             for (int k = 0; k < 3; ++k) tb.push_back(b[k]);
             tm.push_back(d.m[j]);
+            // the P32 cell record counts sites and needs one site mass per context
+            if (c->m_site == 0.0) c->m_site = d.m[j];
+            if (p.precision == MPCD_P32 && d.m[j] != c->m_site) {
+                delete c;
+                return MPCD_ERR_ARG;
+            }
         }
         // the template must be centred and principal (Eqs. 3-5 with R = site COM)
         double Ix = 0, Iy = 0, Iz = 0;
@@ -563,6 +606,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
         return MPCD_ERR_CUDA;
     }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
     if (configure_body_kernels(c->max_sites, p.precision) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -582,6 +626,13 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     ok &= (c->d_shapes = (DevShape *)A(std::max<size_t>(1, c->shapes.size()) * sizeof(DevShape))) != nullptr;
     ok &= (c->d_bodies = (DevBody *)A(std::max<int64_t>(1, c->B) * sizeof(DevBody))) != nullptr;
     ok &= (c->d_bpos = (float4 *)A(std::max<int64_t>(1, c->B) * sizeof(float4))) != nullptr;
+    ok &= (c->d_bpos_build = (float4 *)A(std::max<int64_t>(1, c->B) * sizeof(float4))) != nullptr;
+    ok &= (c->d_nlist = (int32_t *)A(std::max<int64_t>(1, c->B) * NLIST_MAX * 4)) != nullptr;
+    ok &= (c->d_ncount = (int32_t *)A(std::max<int64_t>(1, c->B) * 4)) != nullptr;
+    ok &= (c->d_nl_dirty = (int *)A(8)) != nullptr;
+    ok &= (c->d_pose32 = (float *)A(std::max<int64_t>(1, c->B) * POSE_W * 4)) != nullptr;
+    ok &= (c->d_pose64 = (double *)A(std::max<int64_t>(1, c->B) * POSE_W * 8)) != nullptr;
+    ok &= (c->d_partial = A(std::max<int64_t>(1, c->B) * SITE_WARPS * 6 * 8)) != nullptr;
     ok &= (c->d_tb = (double *)A(std::max<size_t>(1, tb.size()) * 8)) != nullptr;
     ok &= (c->d_tbf = (float *)A(std::max<size_t>(1, tb.size()) * 4)) != nullptr;
     ok &= (c->d_tm = (double *)A(std::max<size_t>(1, tm.size()) * 8)) != nullptr;
@@ -636,6 +687,9 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     if (cudaMemset(c->sums, 0, (size_t)c->C * c->nw * 8) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->params, 0, (size_t)c->C * c->param_bytes) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_step, 0, 8) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (cudaMemset(c->d_ncount, 0, std::max<int64_t>(1, c->B) * 4) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (cudaMemset(c->d_bpos_build, 0, std::max<int64_t>(1, c->B) * sizeof(float4)) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (cudaMemset(c->d_nl_dirty, 0xFF, sizeof(int)) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_err, 0, 8) != cudaSuccess) st = MPCD_ERR_CUDA;
     build_tiles(c);
     build_ctiles(c);
@@ -735,6 +789,7 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
     CK(c, cudaMemsetAsync(c->sums, 0, (size_t)c->C * c->nw * 8, s));
     int64_t stp = h->step;
     CK(c, cudaMemcpyAsync(c->d_step, &stp, 8, cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemsetAsync(c->d_nl_dirty, 0xFF, sizeof(int), s));   // build the neighbour lists
     launch_body_force(a, 0, s);
     CK(c, cudaGetLastError());
     // the upload kernel flags positions outside [0, L): reject the state
@@ -991,10 +1046,11 @@ int mpcd_set_tuning(mpcd_ctx *c, const mpcd_tuning *t)
     }
     if (t->tile > 0) {
         if (t->tile < 64) return MPCD_ERR_ARG;
-        c->tune.tile = t->tile;
+        c->tune.tile = t->tile & ~7;   // tiles start on 8-element boundaries (bulk-copy alignment)
     }
     if (t->ctas_per_sm > 0) c->tune.ctas_per_sm = std::min(t->ctas_per_sm, 32);
     if (t->sort_period > 0) c->tune.sort_period = t->sort_period;
+    if (t->staged >= 0) c->tune.staged = t->staged ? 1 : 0;
     CK(c, cudaSetDevice(c->device));
     build_tiles(c);
     int e = upload_tiles(c);
@@ -1037,36 +1093,39 @@ int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
     };
     mpcd_tuning best = c->tune;
     float best_ms = 1e30f;
-    const int blocks[] = {128, 256, 512};
-    const int tiles_[] = {2048, 8192, 32768};
-    const int ctas[] = {2, 4, 8};
+    std::vector<mpcd_tuning> cand;
+    for (int bl : {128, 256, 512})
+        for (int tl : {1024, 2048, 4096})
+            for (int ct : {1, 2, 4})
+                if (staged_fits(c, tl, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 1});
+    for (int bl : {256, 512})
+        for (int ct : {2, 4})
+            cand.push_back(mpcd_tuning{bl, 8192, ct, c->tune.sort_period, 0});
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
     const bool prof = c->profiling;
     c->profiling = false;
     int st = MPCD_OK;
-    for (int bl : blocks)
-        for (int tl : tiles_)
-            for (int ct : ctas) {
-                if (bl * ct > 2048) continue;
-                mpcd_tuning t{bl, tl, ct, c->tune.sort_period};
-                c->tune = t;
-                build_tiles(c);
-                if ((st = upload_tiles(c))) goto out;
-                if ((st = run_steps(c, 1, s))) goto out;   // warm-up
-                CK(c, cudaEventRecord(e0, s));
-                if ((st = run_steps(c, steps_per_trial, s))) goto out;
-                CK(c, cudaEventRecord(e1, s));
-                CK(c, cudaEventSynchronize(e1));
-                float ms;
-                CK(c, cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = t;
-                }
-                if ((st = restore())) goto out;
+    for (const mpcd_tuning &t : cand) {
+        c->tune = t;
+        build_tiles(c);
+        if ((st = upload_tiles(c))) goto out;
+        if ((st = run_steps(c, 1, s))) goto out;   // warm-up
+        CK(c, cudaEventRecord(e0, s));
+        if ((st = run_steps(c, steps_per_trial, s))) goto out;
+        CK(c, cudaEventRecord(e1, s));
+        CK(c, cudaEventSynchronize(e1));
+        {
+            float ms = 0.f;
+            CK(c, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
             }
+        }
+        if ((st = restore())) goto out;
+    }
 out:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

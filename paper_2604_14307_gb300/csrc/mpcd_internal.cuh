@@ -5,8 +5,10 @@
 //             uint32 tag, double-buffered for the periodic spatial re-sort.
 //             Each replica owns slots [solv_begin, solv_begin + n_solvent),
 //             solv_begin a multiple of 8; padding slots carry tag 0xFFFFFFFF.
-//   cells     `sums`:   NW word arrays of n_cells entries (int64 fixed point
-//                       for P32, double for P64), zero between collisions;
+//   cells     `sums`:   NW word arrays of n_cells entries (SoA: the lanes of a
+//                       warp handle neighbouring cells, so their atomics share
+//                       sectors): int64 fixed point for P32 (3 words SRD, 4 AT),
+//                       double for P64.  Zero between collisions.
 //             `params`: one record per cell (32 B for P32, 64 B for P64):
 //                       u, kappa (< 0 marks a cell that does not collide),
 //                       and the SRD axis or the AT mean noise.
@@ -24,9 +26,14 @@ namespace mpcd {
 enum : uint32_t { TAG_SHIFT = 1, TAG_AXIS = 2, TAG_THERMO = 3, TAG_THERMO_ODD = 4,
                   TAG_SITE = 5, TAG_AT = 6 };
 // Bits of the device error word.
-enum : int { ERR_POSITION = 1, ERR_CELL = 2 };
+enum : int { ERR_POSITION = 1, ERR_CELL = 2, ERR_TIMEOUT = 4 };
 
 constexpr uint32_t PAD_TAG = 0xFFFFFFFFu;
+constexpr int NLIST_MAX = 96;       // neighbour-list capacity per body
+constexpr float NLIST_SKIN = 0.5f;  // Verlet skin of the body neighbour lists
+constexpr int POSE_W = 20;          // words of a pose record
+constexpr int SITE_THREADS = 128;   // threads of the per-body site kernels
+constexpr int SITE_WARPS = SITE_THREADS / 32;
 
 struct DevReplica {
     int32_t L[3];
@@ -71,7 +78,8 @@ struct StepArgs {
     int32_t precision, rule, thermostat, naive;
     double kT, dt, m_solvent, cos_a, sin_a;
     float kTf, dtf, m_solvent_f, cos_af, sin_af;
-    long long w0_solvent;           // fixed-point count|mass word of a solvent particle
+    long long qm_solvent, qm_site;  // round(m 2^24) of the solvent and of the sites (P32)
+    float m_site_f;                 // site mass of the P32 form (uniform)
     const DevReplica *reps;
     int32_t n_rep;
     const Tile *tiles;              // solvent tiles
@@ -87,6 +95,13 @@ struct StepArgs {
     int32_t nw;
     DevBody *bodies;
     float4 *bpos;                   // per body: R in float, bounding radius (force prefilter)
+    float4 *bpos_build;             // positions when the neighbour lists were built
+    int32_t *nlist;                 // [n_bodies][NLIST_MAX] neighbour candidates, ascending
+    int32_t *ncount;                // candidates per body, -1 after an overflow
+    int *nl_dirty;                  // set when a body moved more than half the skin
+    float *pose32;                  // per body [POSE_W]: Q (9), R (3), V (3), omega (3) in float
+    double *pose64;                 // the same in double
+    void *partial;                  // per body [SITE_WARPS][6] transfer partial sums (Real)
     int32_t n_bodies;
     const DevShape *shapes;
     const double *tb;               // template offsets [sites][3]
@@ -142,6 +157,89 @@ __host__ __device__ __forceinline__ void grid_shift(const DevReplica &r, int64_t
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-point conversions on the integer/FP32 pipes.  On sm_103a the 64-bit
+// integer <-> float conversion instructions run at the reduced FP64 rate, so
+// they are written out with bit operations here.
+// ---------------------------------------------------------------------------
+// round-half-even(f * 2^S) as int64, identical to __float2ll_rn(f * 2^S)
+// while |f * 2^S| < 2^62 (every physical velocity, energy and mass term)
+template <int S>
+__device__ __forceinline__ long long qfix(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const uint32_t man = (b & 0x7FFFFFu) | 0x800000u;
+    const int sh = e - 150 + S;             // f * 2^S = man * 2^(e - 150 + S)
+    long long q;
+    if (e == 0 || sh < -25) {
+        q = 0;                              // |f * 2^40| < 1/2 rounds to 0
+    } else if (sh >= 0) {
+        q = (long long)man << (sh < 38 ? sh : 38);
+    } else {
+        const int rs = -sh;                 // 1..25
+        uint32_t qq = rs < 32 ? man >> rs : 0u;
+        const uint32_t rem = man & ((1u << rs) - 1u), half = 1u << (rs - 1);
+        qq += (rem > half || (rem == half && (qq & 1u))) ? 1u : 0u;
+        q = (long long)qq;
+    }
+    return (b >> 31) ? -q : q;
+}
+__device__ __forceinline__ long long q40(float f) { return qfix<40>(f); }
+__device__ __forceinline__ long long pack2(long long hi, long long lo)
+{
+    return (long long)((unsigned long long)hi << 32) + lo;
+}
+
+// The P32 cell words (SoA arrays of n_cells int64), exact sums over a cell of
+//   w0 = (p_x, p_y),  w1 = (p_z, count)           p = round(fl32(m v) 2^20)
+//   SRD: w2 = round(e 2^28), e = fl32(fl32(fl32(px vx) + fl32(py vy)) + fl32(pz vz))
+//   AT:  w2 = (q_x, q_y), w3 = (q_z, 0)           q = round(fl32(m xi) 2^20)
+// where (hi, lo) is the signed 32-bit pair hi 2^32 + lo and count is 1 for a
+// solvent particle, 2^12 for a site.
+template <int RULE> struct Words32 { static constexpr int n = RULE == 0 ? 3 : 4; };
+
+template <int RULE>
+__device__ __forceinline__ void record_terms(float m, float vx, float vy, float vz, const float *xi, bool site,
+                                             long long w[4])
+{
+    const float px = __fmul_rn(m, vx), py = __fmul_rn(m, vy), pz = __fmul_rn(m, vz);
+    const long long cnt = site ? (1LL << 12) : 1LL;
+    w[0] = pack2(qfix<20>(px), qfix<20>(py));
+    w[1] = pack2(qfix<20>(pz), cnt);
+    if (RULE == 0) {
+        const float e = __fadd_rn(__fadd_rn(__fmul_rn(px, vx), __fmul_rn(py, vy)), __fmul_rn(pz, vz));
+        w[2] = qfix<28>(e);
+        w[3] = 0;
+    } else {
+        w[2] = pack2(qfix<20>(__fmul_rn(m, xi[0])), qfix<20>(__fmul_rn(m, xi[1])));
+        w[3] = pack2(qfix<20>(__fmul_rn(m, xi[2])), 0);
+    }
+}
+
+// split a pair word into its signed 32-bit halves
+__device__ __forceinline__ void unpack2(long long w, long long &hi, long long &lo)
+{
+    lo = (long long)(int)(unsigned)(w & 0xFFFFFFFFll);
+    hi = (w - lo) >> 32;
+}
+
+// uint64 / int64 -> float (rounded twice, |error| <= 1 ulp) without the 64-bit
+// convert: the magnitude is split into 20 + 22 + 22 bits, each converted
+// exactly, and the sign applied last (no cancellation between the pieces)
+__device__ __forceinline__ float ull2f(unsigned long long w)
+{
+    const uint32_t h = (uint32_t)(w >> 44), m = (uint32_t)(w >> 22) & 0x3FFFFFu, l = (uint32_t)w & 0x3FFFFFu;
+    const float hf = __uint_as_float(0x4B000000u | h) - 8388608.0f;   // exact for h < 2^23
+    const float mf = __uint_as_float(0x4B000000u | m) - 8388608.0f;
+    const float lf = __uint_as_float(0x4B000000u | l) - 8388608.0f;
+    return fmaf(hf, 17592186044416.0f, fmaf(mf, 4194304.0f, lf));    // h 2^44 + m 2^22 + l
+}
+__device__ __forceinline__ float ll2f(long long w)
+{
+    return w < 0 ? -ull2f(0ull - (unsigned long long)w) : ull2f((unsigned long long)w);
+}
+
+// ---------------------------------------------------------------------------
 // Launch wrappers (defined in the kernel translation units).
 // ---------------------------------------------------------------------------
 enum : int { SOLV_COLLIDE = 1, SOLV_STREAM = 2, SOLV_BIN = 4 };
@@ -149,11 +247,15 @@ enum : int { SOLV_COLLIDE = 1, SOLV_STREAM = 2, SOLV_BIN = 4 };
 struct LaunchCfg {
     int block;      // threads per CTA of the solvent pass
     int grid;       // CTAs (persistent over tiles)
+    int staged;     // 1: tiles staged through shared memory by bulk async copies
+    int cap;        // particles per shared-memory stage (>= the tile size)
 };
 
 // solvent pass (kernels_solvent.cu)
 void launch_solvent(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s);
 void launch_params(const StepArgs &a, int grid, cudaStream_t s);
+size_t solvent_stage_bytes(int precision, int rule, int cap);
+size_t solvent_smem_bytes(int precision, int rule, int cap, int block);  // dynamic smem of the staged pass
 void launch_aos_to_soa(const StepArgs &a, const void *xaos, const void *vaos, cudaStream_t s);
 void launch_soa_to_aos(const StepArgs &a, void *xaos, void *vaos, const int64_t *out_off,
                        cudaStream_t s);
@@ -174,6 +276,7 @@ void launch_sites_pre(const StepArgs &a, int max_sites, cudaStream_t s);
 void launch_sites_post(const StepArgs &a, int max_sites, cudaStream_t s);
 void launch_advance_step(const StepArgs &a, cudaStream_t s);
 void launch_body_diag(const StepArgs &a, double *acc, cudaStream_t s);
+void launch_body_impulse(const StepArgs &a, cudaStream_t s);
 cudaError_t configure_body_kernels(int max_sites, int precision);
 
 }  // namespace mpcd

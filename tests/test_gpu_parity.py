@@ -52,6 +52,27 @@ def site_mask_cells(osys, tr):
     return m
 
 
+def halves(x):
+    lo = (x & 0xFFFFFFFF).astype(np.int64)
+    lo = np.where(lo >= 2**31, lo - 2**32, lo)
+    return (x - lo) >> 32, lo
+
+
+def decode_record(w, rule):
+    """P32 cell words -> physical sums (see include/mpcd.h)"""
+    out = {}
+    px, py = halves(w[0])
+    pz, _ = halves(w[1])
+    out["p0"], out["p1"], out["p2"] = px * 2.0**-20, py * 2.0**-20, pz * 2.0**-20
+    if rule == I.SRD:
+        out["e"] = w[2] * 2.0**-28
+    else:
+        qx, qy = halves(w[2])
+        qz, _ = halves(w[3])
+        out["q0"], out["q1"], out["q2"] = qx * 2.0**-20, qy * 2.0**-20, qz * 2.0**-20
+    return out
+
+
 def one_step(B, system, check_sums=True):
     prec = system.params.precision
     tol = TOL[prec]
@@ -91,21 +112,20 @@ def one_step(B, system, check_sums=True):
     n = tr["sums"][0]
     if check_sums:
         if prec == I.P32:
-            w = d["sums"]
-            # count | mass word: integer, bit-exact everywhere
-            assert np.array_equal(w[0], tr["fixed"][0])
-            # momentum (and energy / AT noise) words: bit-exact where only solvent
-            # enters (identical float inputs); within tolerance where sites enter
+            w, fx = d["sums"], tr["fixed"]
             sm = site_mask_cells(osys, tr)
-            nw = w.shape[0]
+            # counts (low half of w1): integer, bit-exact everywhere
+            assert np.array_equal(halves(w[1])[1], halves(fx[1])[1])
             if system.params.rule == I.SRD:
-                assert np.array_equal(w[1:, ~sm], tr["fixed"][1:, ~sm])
+                # only solvent (identical float inputs): every word bit-exact
+                assert np.array_equal(w[:, ~sm], fx[:3, ~sm])
             else:
-                assert np.array_equal(w[1:4, ~sm], tr["fixed"][1:4, ~sm])
+                assert np.array_equal(w[:2, ~sm], fx[:2, ~sm])
+            # with sites: decoded values within the tolerance
+            gd, od = decode_record(w, system.params.rule), decode_record(fx, system.params.rule)
             M = tr["sums"][1]
-            for k in range(1, nw):
-                diff = np.abs(w[k] - tr["fixed"][k]) * 2.0**-40
-                assert np.all(diff <= tol * (M * 4.0 + 1.0))
+            for k in gd:
+                assert np.all(np.abs(gd[k] - od[k]) <= tol * (4.0 * M + 1.0)), k
         else:
             w = d["sums"]
             assert np.array_equal(w[0], n)
@@ -158,7 +178,7 @@ def test_one_step_ragged_replicas(B):
     prm = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=9)
     shapes = [I.sphere_shape(2.0, 2, 5.0), I.dumbbell_shape(2.0, 2.0, 2, 5.0)]
     rng = np.random.default_rng(0)
-    Ls = [(12, 12, 12), (3, 3, 3), (9, 14, 11), (20, 20, 20)]
+    Ls = [(16, 16, 16), (3, 3, 3), (9, 14, 11), (20, 20, 20)]
     ids = [[0, 1], [], [0], [1, 0, 1]]
     system = I.build_system(prm, shapes, Ls, 3.3, ids, "ragged", placement_seed=5)
     system.replicas[1].n_solvent = 7          # ragged tail, not a multiple of 4
@@ -275,3 +295,26 @@ def test_invalid_arguments_are_rejected(B):
     with pytest.raises(B.MPCDError):
         sim.step(-1)
     sim.close()
+
+
+@pytest.mark.parametrize("rule", [I.SRD, I.AT])
+def test_staged_and_direct_solvent_passes_agree_bitwise(B, rule):
+    """The shared-memory staged pass (bulk async copies) and the direct pass
+    compute the same thing; every launch shape gives bit-identical P32 states."""
+    system = I.suspension(18, 5.0, 0.15, 2.0, 2, 5.0, rule, 1, I.P32, seed=12, name="ab")
+    system.replicas[0].n_solvent -= 3          # a ragged tail
+    st = I.initial_state(system)
+    ref = None
+    for staged, block, tile, ctas in [(0, 256, 8192, 4), (1, 128, 1024, 1), (1, 256, 2048, 2),
+                                      (1, 512, 4096, 1), (1, 96, 1000, 3)]:
+        sim = B.Simulation(system)
+        sim.set_tuning(block=block, tile=tile, ctas_per_sm=ctas, staged=staged)
+        sim.set_state(st)
+        sim.step(6)
+        g = sim.get_state()
+        sim.close()
+        if ref is None:
+            ref = g
+            continue
+        for k in ("x", "v", "R", "q", "P", "Lm"):
+            assert np.array_equal(getattr(g, k), getattr(ref, k)), (staged, block, tile, k)

@@ -107,58 +107,78 @@ def test_cell_sums_and_canonical_order_brute_force():
         assert list(ids) == list(np.flatnonzero(sel))
 
 
-def quantised_sums_numpy(cell, m, v, C):
-    """Fixed-point terms of the P32 form computed with numpy float32 ops."""
+def rne(x):
+    """round-to-nearest-even of float32 values (already scaled) to int64"""
+    return np.rint(x).astype(np.int64)
+
+
+def pack2(hi, lo):
+    return ((hi.astype(np.uint64) << np.uint64(32)).astype(np.int64) + lo)
+
+
+def record_numpy(cell, m, v, is_site, C, rule=I.SRD, xi=None):
+    """The P32 cell words recomputed with numpy float32 arithmetic:
+    w0 = (p_x, p_y), w1 = (p_z, count) at 2^20; SRD w2 = round(e 2^28);
+    AT w2 = (q_x, q_y), w3 = (q_z, 0), q = m xi."""
     mf = m.astype(np.float32)
     vf = v.astype(np.float32)
-    p = mf[:, None] * vf                                  # float32 products
+    p = mf[:, None] * vf                                   # float32 products
     e = (p[:, 0] * vf[:, 0] + p[:, 1] * vf[:, 1]) + p[:, 2] * vf[:, 2]
-    s40 = np.float32(2.0**40)
-    w = np.zeros((5, len(m)), dtype=np.int64)
-    w[0] = (np.rint(mf * np.float32(2.0**24)).astype(np.int64) << 16) + 1
-    for a in range(3):
-        w[1 + a] = np.rint(p[:, a] * s40).astype(np.int64)
-    w[4] = np.rint(e * s40).astype(np.int64)
-    out = np.zeros((5, C), dtype=np.int64)
-    for k in range(5):
+    cnt = np.where(is_site, 1 << 12, 1).astype(np.int64)
+    s20 = np.float32(2.0**20)
+    w = np.zeros((4, len(m)), dtype=np.int64)
+    w[0] = pack2(rne(p[:, 0] * s20), rne(p[:, 1] * s20))
+    w[1] = pack2(rne(p[:, 2] * s20), cnt)
+    if rule == I.SRD:
+        w[2] = rne(e * np.float32(2.0**28))
+    else:
+        q = mf[:, None] * xi.astype(np.float32)
+        w[2] = pack2(rne(q[:, 0] * s20), rne(q[:, 1] * s20))
+        w[3] = pack2(rne(q[:, 2] * s20), np.zeros(len(m), dtype=np.int64))
+    out = np.zeros((4, C), dtype=np.int64)
+    for k in range(4):
         np.add.at(out[k], cell, w[k])
     return out
 
 
-def test_fixed_point_sums_are_exact_integer_sums():
-    s, st = tiny_system(L=4, density=6.0, precision=I.P32, site_mass=5.0)
+def unpack2(w):
+    lo = (w & 0xFFFFFFFF).astype(np.int64)
+    lo = np.where(lo >= 2**31, lo - 2**32, lo)
+    return (w - lo) >> 32, lo
+
+
+def test_fixed_point_record_is_an_exact_integer_sum():
+    s, st = tiny_system(L=4, density=6.0, precision=I.P32, site_mass=5.0, thermostat=1)
     osys, ost, pre, tr = run_collision(s, st)
     cell, m, v0, _ = members(osys, pre, tr, ost)
-    ref = quantised_sums_numpy(cell, m, v0, 64)
+    is_site = np.arange(len(m)) >= osys.n_solvent
+    ref = record_numpy(cell, m, v0, is_site, 64)
     assert np.array_equal(tr["fixed"], ref)
-    # decoding recovers the counts, masses and momenta
-    n = tr["fixed"][0] & 0xFFFF
+    # decoding recovers the counts, the masses, the momenta and the energy
+    px, py = unpack2(tr["fixed"][0])
+    pz, cnt = unpack2(tr["fixed"][1])
+    n = (cnt & 0xFFF) + ((cnt >> 12) & 0x3FF)
     assert np.array_equal(n, tr["sums"][0].astype(np.int64))
-    M = (tr["fixed"][0] >> 16) * 2.0**-24
-    assert np.allclose(M, tr["sums"][1], rtol=0, atol=1e-6)
-    assert np.allclose(tr["fixed"][1:4] * 2.0**-40, tr["sums"][2:5], atol=1e-9)
+    M = (cnt & 0xFFF) * 1.0 + ((cnt >> 12) & 0x3FF) * 5.0
+    assert np.allclose(M, tr["sums"][1], rtol=0, atol=1e-12)
+    for k, h in enumerate((px, py, pz)):
+        assert np.allclose(h * 2.0**-20, tr["sums"][2 + k], atol=1e-4)
+    assert np.allclose(tr["fixed"][2] * 2.0**-28, tr["sums"][5], rtol=1e-6, atol=1e-6)
 
 
-def test_fixed_point_words_of_the_at_rule():
-    """AT form: words are count|mass, m v (3) and m xi (3) - no energy word."""
+def test_fixed_point_record_of_the_at_rule():
+    """AT form: no energy; noise sums as 32-bit pairs at 2^-20."""
     s, st = tiny_system(L=4, density=6.0, precision=I.P32, site_mass=5.0, rule=I.AT)
     osys, ost, pre, tr = run_collision(s, st)
     cell, m, v0, _ = members(osys, pre, tr, ost)
-    ref = quantised_sums_numpy(cell, m, v0, 64)
-    assert np.array_equal(tr["fixed"][:4], ref[:4])
     ns = osys.n_solvent
     ids = np.concatenate([np.arange(ns), ns + np.arange(osys.n_sites)])
-    xi = O.normals(osys, 0, pre_step(st), ids, O.TAG_AT) * np.sqrt(1.0 / m)[:, None]
-    pf = m.astype(np.float32)[:, None] * xi.astype(np.float32)
-    w = np.rint(pf * np.float32(2.0**40)).astype(np.int64)
-    for a in range(3):
-        out = np.zeros(64, dtype=np.int64)
-        np.add.at(out, cell, w[:, a])
-        assert np.array_equal(tr["fixed"][4 + a], out)
-
-
-def pre_step(st):
-    return st.step
+    xi = O.normals(osys, 0, st.step, ids, O.TAG_AT) * np.sqrt(1.0 / m)[:, None]
+    ref = record_numpy(cell, m, v0, ids >= ns, 64, rule=I.AT, xi=xi)
+    assert np.array_equal(tr["fixed"], ref)
+    px, py = unpack2(tr["fixed"][0])
+    assert np.allclose(px * 2.0**-20, tr["sums"][2], atol=1e-4)
+    assert np.allclose(py * 2.0**-20, tr["sums"][3], atol=1e-4)
 
 
 # --------------------------------------------------------------- collision ---
@@ -201,6 +221,28 @@ def test_srd_rotates_relative_velocity_by_alpha():
         assert abs(np.linalg.norm(p0) - np.linalg.norm(p1)) < 1e-12
         n_checked += 1
     assert n_checked > 100
+
+
+def test_p32_thermostat_uses_the_fixed_point_energy():
+    """In the P32 form kappa^2 = E'/E_rel with E_rel formed from the cell's
+    fixed-point sums (float32 products m v.v of the stored velocities)."""
+    s, st = tiny_system(L=4, density=6.0, precision=I.P32, site_mass=5.0, thermostat=1)
+    osys, ost, pre, tr = run_collision(s, st)
+    cell, m, v0, v1 = members(osys, pre, tr, ost)
+    fx = tr["fixed"]
+    for c in range(64):
+        sel = cell == c
+        if sel.sum() < 2:
+            continue
+        px, py = unpack2(fx[0:1, c])
+        pz, _ = unpack2(fx[1:2, c])
+        S1 = np.array([px[0], py[0], pz[0]]) * 2.0**-20
+        S2 = fx[2, c] * 2.0**-28
+        Erel = 0.5 * (S2 - (S1 @ S1) / m[sel].sum())
+        u = tr["cell_u"][c]
+        Epost = 0.5 * (m[sel, None] * (v1[sel] - u) ** 2).sum()
+        # the post-collision relative energy is kappa^2 E_rel (rotation keeps |v - u|)
+        assert abs(Epost - tr["cell_kappa"][c] ** 2 * Erel) < 1e-5 * max(Epost, 1e-3)
 
 
 def test_thermostat_energy_follows_eq6_gamma():
