@@ -236,6 +236,61 @@ int mpcd_get_tuning(const mpcd_ctx *ctx, mpcd_tuning *out);
 int mpcd_set_tuning(mpcd_ctx *ctx, const mpcd_tuning *t);
 int mpcd_autotune(mpcd_ctx *ctx, int32_t steps_per_trial, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Solvent collision without any device allocation.
+ *
+ * The paper has no counterpart to this call: it is a library service for
+ * callers that must not allocate device memory at the point where they need a
+ * collision, e.g. a host code whose framework owns the whole device pool (a
+ * new cudaMalloc would fail or fragment it) or a time-critical loop where
+ * cudaMalloc/cudaFree would stall (cudaFree synchronises the device).  Such a
+ * caller cannot use mpcd_create, which allocates the context's state.
+ *
+ * One collision (Sec. II.A) of a single periodic box of solvent only, at
+ * `step`: random grid shift, binning, exact fixed-point cell sums, then SRD
+ * rotation by alpha about a random per-cell axis (with the cell-level
+ * thermostat if params->thermostat) or MPCD-AT.  It computes what
+ * mpcd_collide computes for a context holding the same box with no colloids
+ * at the same step (P32 form; same Philox streams, keyed by params->seed,
+ * replica 0, and the particle ids in `tag`).  Positions are not changed;
+ * velocities are updated in place.
+ *
+ * Arguments (device pointers, caller-owned, on the current CUDA device):
+ *   params     host struct; precision must be MPCD_P32 and reserved 0
+ *              (sort_period and naive_transfer are ignored)
+ *   L          host int32[3], cells per edge, each >= 3
+ *   n_solvent  particles, 0 <= n <= MPCD_STATIC_MAX_SOLVENT, a multiple of 4
+ *   x, y, z    float[n] positions in [0, L) (not checked)
+ *   vx, vy, vz float[n] velocities, updated in place
+ *   tag        uint32[n] particle ids (the counter of the MPCD-AT draws);
+ *              may be NULL for MPCD_SRD
+ *   step       collision index (>= 0), keys the grid shift and all draws
+ *   stream     cudaStream_t as void*; the work is enqueued asynchronously
+ *   msg        optional host buffer of msg_len bytes for an error message
+ * Every device array must be 16-byte aligned.  The P32 per-cell limits of
+ * mpcd_debug_cells apply (at most 4095 particles and |sum m v| < 2048 per cell).
+ *
+ * Scratch: the cell sums and collision parameters live in one statically
+ * reserved device array of the library (about 4.1 MB per device, reserved by
+ * the CUDA runtime when it loads that part of the library on the device, at
+ * the latest on the first call), sized for MPCD_STATIC_MAX_CELLS cells.  A box with more cells, more particles than
+ * MPCD_STATIC_MAX_SOLVENT, a misaligned pointer or an n that is not a multiple
+ * of 4 is rejected with MPCD_ERR_ARG and a message before any device work.  The
+ * call allocates nothing; it zeroes the cell sums it uses before binning.  The
+ * first call on each device looks up the scratch address (cudaGetSymbolAddress)
+ * and the SM count; make that first call before any stream capture begins.
+ *
+ * The scratch is shared by all calls on a device: calls that overlap in time
+ * (other streams, other host threads) race on it and give wrong results.
+ * Serialise them, e.g. on one stream.  Returns MPCD_OK, MPCD_ERR_ARG or
+ * MPCD_ERR_CUDA (a launch failed). */
+#define MPCD_STATIC_MAX_CELLS 65536
+#define MPCD_STATIC_MAX_SOLVENT 4194304
+int mpcd_collide_solvent_static(const mpcd_params *params, const int32_t L[3], int64_t n_solvent,
+                                const float *x, const float *y, const float *z, float *vx,
+                                float *vy, float *vz, const uint32_t *tag, int64_t step,
+                                void *stream, char *msg, size_t msg_len);
+
 #ifdef __cplusplus
 }
 #endif

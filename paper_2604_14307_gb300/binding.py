@@ -31,7 +31,7 @@ EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "m
            "mpcd_couple", "mpcd_collide", "mpcd_step", "mpcd_sort", "mpcd_diagnostics",
            "mpcd_sizes", "mpcd_last_error", "mpcd_set_debug", "mpcd_debug_cells",
            "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
-           "mpcd_set_tuning", "mpcd_autotune"]
+           "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static"]
 
 
 class MPCDError(RuntimeError):
@@ -127,6 +127,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "mpcd_get_tuning": [vp, C.POINTER(Tuning)],
             "mpcd_set_tuning": [vp, C.POINTER(Tuning)],
             "mpcd_autotune": [vp, i32, vp],
+            "mpcd_collide_solvent_static": [C.POINTER(Params), C.POINTER(C.c_int32 * 3), i64, vp, vp, vp,
+                                            vp, vp, vp, vp, i64, vp, C.c_char_p, C.c_size_t],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -360,3 +362,30 @@ class Simulation:
     def autotune(self, steps_per_trial: int = 3, stream=None) -> dict:
         self._check(self.lib.mpcd_autotune(self.ctx, steps_per_trial, self._s(stream)))
         return self.tuning()
+
+
+def collide_solvent_static(params: I.Params, L, x, y, z, vx, vy, vz, tag=None, step: int = 0,
+                           stream=None) -> None:
+    """mpcd_collide_solvent_static: one collision of a single solvent-only box
+    on caller-owned CUDA float32 tensors (vx, vy, vz updated in place), with
+    the library's static scratch instead of any device allocation.  `tag`
+    (int32/uint32 particle ids) is needed for MPCD_AT.  Calls on one device
+    must not overlap in time: they share the scratch."""
+    lib = load()
+    prm = Params(params.kT, params.dt, params.alpha_deg, params.m_solvent, params.rule,
+                 params.thermostat, params.precision, params.naive_transfer, params.seed, 0, 0)
+    arrs = [x, y, z, vx, vy, vz]
+    n = int(x.numel())
+    for t in arrs + ([tag] if tag is not None else []):
+        if not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("solvent arrays must be contiguous CUDA tensors of one length")
+    for t in arrs:
+        if t.element_size() != 4 or not t.is_floating_point():
+            raise ValueError("solvent arrays must be float32")
+    Ls = (C.c_int32 * 3)(*[int(a) for a in L])
+    msg = C.create_string_buffer(256)
+    rc = lib.mpcd_collide_solvent_static(C.byref(prm), C.byref(Ls), n, *[t.data_ptr() for t in arrs],
+                                         tag.data_ptr() if tag is not None else None, int(step),
+                                         current_stream() if stream is None else int(stream), msg, 256)
+    if rc != MPCD_OK:
+        raise MPCDError(rc, msg.value.decode())

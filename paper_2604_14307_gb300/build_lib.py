@@ -1,6 +1,6 @@
 """Build ``libmpcd.so`` (the C-ABI library of include/mpcd.h) for sm_103a.
 
-The three translation units are compiled in parallel with nvcc and linked
+The translation units are compiled in parallel with nvcc and linked
 into ``paper_2604_14307_gb300/_build/libmpcd.so`` (in-tree).  The rigid-body
 unit is compiled without fused multiply-add so that the FP64 body and
 site-position arithmetic rounds exactly as written; host code never fuses.
@@ -23,6 +23,7 @@ UNITS = {
     "mpcd_api.cu": [],
     "kernels_solvent.cu": [],
     "kernels_bodies.cu": ["-fmad=false"],
+    "static_collide.cu": [],
 }
 
 
