@@ -760,68 +760,117 @@ __device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long 
     return 0.5f * fmaxf(e2, 0.0f);
 }
 
-// FP32 form: cell words -> collision parameters with FP32/integer pipes only
+// FP32 form: cell words -> collision parameters with FP32/integer pipes only.
+// Each CTA takes PARAM_TILES consecutive 256-cell tiles, one cell of each per
+// thread.  The word loads of all of them are issued before any arithmetic (a
+// warp keeps PARAM_TILES x NW loads in flight instead of a chain of dependent
+// loads) and parked in shared memory, so the registers of the arithmetic that
+// follows are not tied up by the parked words.
+constexpr int PARAM_TILES = 2;
+
 template <int RULE>
-__global__ void __launch_bounds__(256) k_params32(StepArgs a)
+__device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplica &r, int64_t step, int64_t c,
+                                              const long long (&w)[4])
+{
+    const float kT = a.kTf;
+    const float s20 = 9.5367431640625e-07f;   // 2^-20
+    long long S1[3], cnt;
+    unpack2(w[0], S1[0], S1[1]);
+    unpack2(w[1], S1[2], cnt);
+    const int ns = (int)(cnt & 0xFFF), nb = (int)((cnt >> 12) & 0x3FF), n = ns + nb;
+    float rec[8] = {0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, 0.f};
+    if (n >= 2) {
+        const long long Mq = (long long)ns * a.qm_solvent + (long long)nb * a.qm_site;
+        const float M = (float)ns * a.m_solvent_f + (float)nb * a.m_site_f;
+        const float iM = 1.0f / M;
+        float u[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u[k] = ll2f(S1[k]) * s20 * iM;
+        rec[0] = u[0]; rec[1] = u[1]; rec[2] = u[2];
+        const uint32_t lc = (uint32_t)(c - r.cell_base);
+        if (RULE == 0) {
+            // axis: z = u1 - (1 - u1), rho = 2 sqrt(u1 (1 - u1)), phi = 2 pi u2
+            const uint4 wa = draw(r, step, lc, TAG_AXIS, 0u);
+            const float ua = u01f(wa.x), ub = u01f(~wa.x);
+            const float zz = ua - ub, rho = 2.0f * sqrtf(ua * ub);
+            float sn, cs;
+            __sincosf(6.283185307179586f * (u01f(wa.y) - 0.5f), &sn, &cs);   // angle shifted by pi
+            rec[4] = -rho * cs; rec[5] = -rho * sn; rec[6] = zz;
+            float kappa = 1.0f;
+            if (a.thermostat) {
+                const float erel = rel_energy_fixed(Mq, S1, w[2], M, u);
+                const float g = gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
+                kappa = erel > 0.0f ? sqrtf(kT * g / erel) : 1.0f;
+            }
+            rec[3] = kappa;
+        } else {
+            long long qx, qy, qz, zero;
+            unpack2(w[2], qx, qy);
+            unpack2(w[3], qz, zero);
+            rec[3] = 1.0f;
+            rec[4] = ll2f(qx) * s20 * iM; rec[5] = ll2f(qy) * s20 * iM; rec[6] = ll2f(qz) * s20 * iM;
+        }
+    }
+    float4 *o = reinterpret_cast<float4 *>(a.params) + 2 * c;
+    o[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
+    o[1] = make_float4(rec[4], rec[5], rec[6], 0.0f);
+}
+
+template <int RULE>
+__global__ void __launch_bounds__(256, 4) k_params32(StepArgs a)
 {
     constexpr int NW = Words32<RULE>::n;
-    const int64_t step = *a.d_step;
+    constexpr int K = PARAM_TILES;
+    __shared__ long long sw[K][NW][256];
+    __shared__ Tile stile[K];
     long long *sums = reinterpret_cast<long long *>(a.sums);
     long long *dbg = reinterpret_cast<long long *>(a.dbg_sums);
     const int64_t C = a.n_cells;
-    const float kT = a.kTf;
-    const float s20 = 9.5367431640625e-07f;   // 2^-20
-    for (int t = blockIdx.x; t < a.n_ctiles; t += gridDim.x) {
-        const Tile tl = a.ctiles[t];
-        const DevReplica r = a.reps[tl.rep];
-        for (int64_t c = tl.begin + threadIdx.x; c < tl.end; c += blockDim.x) {
-            long long w[4] = {0, 0, 0, 0};
+    const int t0 = blockIdx.x * K;
+    int64_t cell[K];
+    int rep[K];
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                w[k] = sums[k * C + c];
-                sums[k * C + c] = 0;
-                if (dbg) dbg[k * C + c] = w[k];
-            }
-            long long S1[3], cnt;
-            unpack2(w[0], S1[0], S1[1]);
-            unpack2(w[1], S1[2], cnt);
-            const int ns = (int)(cnt & 0xFFF), nb = (int)((cnt >> 12) & 0x3FF), n = ns + nb;
-            float rec[8] = {0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, 0.f};
-            if (n >= 2) {
-                const long long Mq = (long long)ns * a.qm_solvent + (long long)nb * a.qm_site;
-                const float M = (float)ns * a.m_solvent_f + (float)nb * a.m_site_f;
-                const float iM = 1.0f / M;
-                float u[3];
+    for (int k = 0; k < K; ++k) {
+        cell[k] = -1;
+        rep[k] = 0;
+        if (t0 + k < a.n_ctiles) {
+            const Tile tl = a.ctiles[t0 + k];
+            const int64_t c = tl.begin + threadIdx.x;
+            if (c < tl.end) { cell[k] = c; rep[k] = tl.rep; }
+            if (threadIdx.x == 0) stile[k] = tl;
+        } else if (threadIdx.x == 0) {
+            stile[k] = Tile{0, 0, 0, 0};
+        }
+    }
+    {
+        long long w[K][NW];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) u[k] = ll2f(S1[k]) * s20 * iM;
-                rec[0] = u[0]; rec[1] = u[1]; rec[2] = u[2];
-                const uint32_t lc = (uint32_t)(c - r.cell_base);
-                if (RULE == 0) {
-                    // axis: z = u1 - (1 - u1), rho = 2 sqrt(u1 (1 - u1)), phi = 2 pi u2
-                    const uint4 wa = draw(r, step, lc, TAG_AXIS, 0u);
-                    const float ua = u01f(wa.x), ub = u01f(~wa.x);
-                    const float zz = ua - ub, rho = 2.0f * sqrtf(ua * ub);
-                    float sn, cs;
-                    __sincosf(6.283185307179586f * (u01f(wa.y) - 0.5f), &sn, &cs);   // angle shifted by pi
-                    rec[4] = -rho * cs; rec[5] = -rho * sn; rec[6] = zz;
-                    float kappa = 1.0f;
-                    if (a.thermostat) {
-                        const float erel = rel_energy_fixed(Mq, S1, w[2], M, u);
-                        const float g = gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
-                        kappa = erel > 0.0f ? sqrtf(kT * g / erel) : 1.0f;
-                    }
-                    rec[3] = kappa;
-                } else {
-                    long long qx, qy, qz, zero;
-                    unpack2(w[2], qx, qy);
-                    unpack2(w[3], qz, zero);
-                    rec[3] = 1.0f;
-                    rec[4] = ll2f(qx) * s20 * iM; rec[5] = ll2f(qy) * s20 * iM; rec[6] = ll2f(qz) * s20 * iM;
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int j = 0; j < NW; ++j) w[k][j] = cell[k] >= 0 ? __ldcs(sums + j * C + cell[k]) : 0ll;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                sw[k][j][threadIdx.x] = w[k][j];
+                if (cell[k] >= 0) {
+                    sums[j * C + cell[k]] = 0;
+                    if (dbg) dbg[j * C + cell[k]] = w[k][j];
                 }
             }
-            float4 *o = reinterpret_cast<float4 *>(a.params) + 2 * c;
-            o[0] = make_float4(rec[0], rec[1], rec[2], rec[3]);
-            o[1] = make_float4(rec[4], rec[5], rec[6], 0.0f);
+    }
+    __syncthreads();   // stile; the words are re-read from shared memory below
+    const int64_t step = *a.d_step;
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const Tile tl = stile[k];
+        const int64_t c = tl.begin + threadIdx.x;
+        if (c < tl.end) {
+            long long w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < NW; ++j) w[j] = sw[k][j][threadIdx.x];
+            const DevReplica r = a.reps[tl.rep];
+            params32_cell<RULE>(a, r, step, c, w);
         }
     }
 }
@@ -908,8 +957,9 @@ void launch_params(const StepArgs &a, int, cudaStream_t s)
     if (a.n_ctiles == 0) return;
     const int grid = a.n_ctiles;   // one 256-cell tile per CTA, one cell per thread
     if (a.precision == 1) {
-        if (a.rule == 0) k_params32<0><<<grid, 256, 0, s>>>(a);
-        else k_params32<1><<<grid, 256, 0, s>>>(a);
+        const int grid32 = (a.n_ctiles + PARAM_TILES - 1) / PARAM_TILES;
+        if (a.rule == 0) k_params32<0><<<grid32, 256, 0, s>>>(a);
+        else k_params32<1><<<grid32, 256, 0, s>>>(a);
     } else {
         if (a.rule == 0) k_params<double, 0><<<grid, 256, 0, s>>>(a);
         else k_params<double, 1><<<grid, 256, 0, s>>>(a);

@@ -198,21 +198,39 @@ __device__ __forceinline__ long long pack2(long long hi, long long lo)
 // solvent particle, 2^12 for a site.
 template <int RULE> struct Words32 { static constexpr int n = RULE == 0 ? 3 : 4; };
 
+// round-half-even(f 2^20) for |f 2^20| < 2^31 (every momentum term within the
+// P32 limits): the power-of-two scale is exact, so one 32-bit conversion gives
+// the same integer as qfix<20>
+__device__ __forceinline__ long long q20(float f) { return (long long)__float2int_rn(__fmul_rn(f, 1048576.0f)); }
+
+// round-half-even(e 2^28) as int64 for 0 <= e < 2^28 (a kinetic-energy term),
+// with 32-bit conversions only: e = 16 h + r with h = floor(e / 16) (exact) and
+// r in [0, 16) formed exactly by one fused multiply-add (r is a multiple of
+// ulp(e) below 16); then e 2^28 = h 2^32 + r 2^28 and r 2^28 < 2^32 rounds
+// within the low word.  Identical to qfix<28>(e) on that range.
+__device__ __forceinline__ long long q28_nonneg(float e)
+{
+    const int h = __float2int_rd(__fmul_rn(e, 0.0625f));
+    const float r = __fmaf_rn(-16.0f, __int2float_rn(h), e);
+    const unsigned lo = __float2uint_rn(__fmul_rn(r, 268435456.0f));
+    return (long long)(((unsigned long long)(unsigned)h << 32) | lo);
+}
+
 template <int RULE>
 __device__ __forceinline__ void record_terms(float m, float vx, float vy, float vz, const float *xi, bool site,
                                              long long w[4])
 {
     const float px = __fmul_rn(m, vx), py = __fmul_rn(m, vy), pz = __fmul_rn(m, vz);
     const long long cnt = site ? (1LL << 12) : 1LL;
-    w[0] = pack2(qfix<20>(px), qfix<20>(py));
-    w[1] = pack2(qfix<20>(pz), cnt);
+    w[0] = pack2(q20(px), q20(py));
+    w[1] = pack2(q20(pz), cnt);
     if (RULE == 0) {
         const float e = __fadd_rn(__fadd_rn(__fmul_rn(px, vx), __fmul_rn(py, vy)), __fmul_rn(pz, vz));
-        w[2] = qfix<28>(e);
+        w[2] = q28_nonneg(e);
         w[3] = 0;
     } else {
-        w[2] = pack2(qfix<20>(__fmul_rn(m, xi[0])), qfix<20>(__fmul_rn(m, xi[1])));
-        w[3] = pack2(qfix<20>(__fmul_rn(m, xi[2])), 0);
+        w[2] = pack2(q20(__fmul_rn(m, xi[0])), q20(__fmul_rn(m, xi[1])));
+        w[3] = pack2(q20(__fmul_rn(m, xi[2])), 0);
     }
 }
 
