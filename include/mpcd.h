@@ -94,6 +94,11 @@ typedef struct {
     int32_t L[3];             /* cells per edge (>= 3 each) */
     int64_t n_solvent;        /* solvent particles of this replica */
     int32_t n_bodies;
+    int32_t stream_id;        /* >= 0, distinct within a context: the replica's random
+                                 streams use the Philox key (seed_lo, seed_hi ^ stream_id).
+                                 Give each replica its index in the whole ensemble and
+                                 its trajectory does not depend on how the ensemble is
+                                 split over contexts or GPUs. */
     const int32_t *body_shape;  /* [n_bodies] shape index (copied) */
 } mpcd_replica_desc;
 
@@ -138,7 +143,10 @@ typedef struct {
 /* Create a context on CUDA device `device`.  Validates every argument
  * (MPCD_ERR_ARG), builds the per-shape mass and principal moments, allocates
  * the device state (MPCD_ERR_OOM) and zeroes it; call mpcd_set_state next.
- * The paper's cell size a = 1 is the only one supported. */
+ * The paper's cell size a = 1 is the only one supported.  A replica with more
+ * than one body needs every box edge above twice the largest WCA cutoff
+ * (d_ij - sigma + 2^(1/6) sigma, Eq. 1) so that each centre pair has one
+ * minimum image; the P32 form needs one site mass for all shapes. */
 int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_desc *shapes,
                 int32_t n_replicas, const mpcd_replica_desc *replicas,
                 const mpcd_allocator *allocator, int32_t device, mpcd_ctx **out);

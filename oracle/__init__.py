@@ -48,7 +48,8 @@ class _Sys(C.Structure):
                 ("n_rep", C.c_int32), ("L", C.c_void_p), ("solv_off", C.c_void_p),
                 ("body_off", C.c_void_p), ("n_shapes", C.c_int32), ("site_off", C.c_void_p),
                 ("b", C.c_void_p), ("m", C.c_void_p), ("cent_off", C.c_void_p),
-                ("cent", C.c_void_p), ("wca_d", C.c_void_p), ("body_shape", C.c_void_p)]
+                ("cent", C.c_void_p), ("wca_d", C.c_void_p), ("body_shape", C.c_void_p),
+                ("stream_id", C.c_void_p)]
 
 
 class _State(C.Structure):
@@ -106,6 +107,7 @@ class OracleSystem:
         so, b, m, co, cen, d = system.shape_tables()
         self.site_off, self.b, self.m = so, b, m
         self.cent_off, self.cent, self.wca_d = co, cen, d
+        self.stream_id = np.ascontiguousarray(system.stream_ids(), dtype=np.int32)
         self.body_shape = np.ascontiguousarray(system.body_shape_array(), dtype=np.int32)
         if self.body_shape.size == 0:
             self.body_shape = np.zeros(1, dtype=np.int32)
@@ -119,7 +121,8 @@ class OracleSystem:
                       vals["naive_transfer"], vals["seed"], len(self.L), _ptr(self.L),
                       _ptr(self.solv_off), _ptr(self.body_off), len(system.shapes),
                       _ptr(self.site_off), _ptr(self.b), _ptr(self.m), _ptr(self.cent_off),
-                      _ptr(self.cent), _ptr(self.wca_d), _ptr(self.body_shape))
+                      _ptr(self.cent), _ptr(self.wca_d), _ptr(self.body_shape),
+                      _ptr(self.stream_id))
         self.n_solvent = int(self.solv_off[-1])
         self.n_bodies = int(self.body_off[-1])
         sizes = [int(so[s + 1] - so[s]) for s in self.body_shape[: self.n_bodies]]

@@ -24,7 +24,7 @@
  * Readings where the paper is silent (binding on both implementations):
  *   binning  X = floor(x * 2^20), S = integer shift in [-2^19, 2^19),
  *            cell = floor((X - S) / 2^20) mod L, particles binned at x - s;
- *   RNG      Philox4x32-10 (Salmon et al., SC'11), key (seed_lo, seed_hi ^ replica),
+ *   RNG      Philox4x32-10 (Salmon et al., SC'11), key (seed_lo, seed_hi ^ stream id),
  *            counter (step, id, tag, j); uniform u = (x + 0.5) 2^-32;
  *            Box-Muller normals; axis z = 2u1 - 1, phi = 2 pi u2;
  *   thermostat E' ~ Gamma(3(Nc-1)/2, kT) (Eq. 6 with n = 3(Nc-1)) drawn as a sum
@@ -63,6 +63,8 @@ typedef struct {
     const double *cent;        /* [centres][3] body-frame WCA centres */
     const double *wca_d;       /* [n_shapes] */
     const int32_t *body_shape; /* [bodies] */
+    const int32_t *stream_id;  /* [n_rep] stream id of each replica (its index in the
+                                  whole ensemble); NULL: the replica's position */
 } orc_sys;
 
 typedef struct {
@@ -119,7 +121,8 @@ static void draw(const orc_sys *s, int rep, int64_t step, uint32_t id, uint32_t 
                  uint32_t j, uint32_t out[4])
 {
     uint32_t ctr[4] = { (uint32_t)step, id, tag, j };
-    uint32_t key[2] = { (uint32_t)s->seed, (uint32_t)(s->seed >> 32) ^ (uint32_t)rep };
+    const uint32_t sid = s->stream_id ? (uint32_t)s->stream_id[rep] : (uint32_t)rep;
+    uint32_t key[2] = { (uint32_t)s->seed, (uint32_t)(s->seed >> 32) ^ sid };
     orc_philox4x32_10(ctr, key, out);
 }
 

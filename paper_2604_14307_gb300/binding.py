@@ -54,7 +54,7 @@ class ShapeDesc(C.Structure):
 
 class ReplicaDesc(C.Structure):
     _fields_ = [("L", C.c_int32 * 3), ("n_solvent", C.c_int64), ("n_bodies", C.c_int32),
-                ("body_shape", C.c_void_p)]
+                ("stream_id", C.c_int32), ("body_shape", C.c_void_p)]
 
 
 AllocFn = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -201,10 +201,11 @@ class Simulation:
             shapes[k] = ShapeDesc(len(m), b.ctypes.data, m.ctypes.data, len(cen),
                                   cen.ctypes.data if len(cen) else None, sh.wca_d)
         reps = (ReplicaDesc * system.n_rep)()
+        sids = system.stream_ids()
         for r, rep in enumerate(system.replicas):
             ids = np.ascontiguousarray(rep.body_shapes, dtype=np.int32)
             self._keep.append(ids)
-            reps[r] = ReplicaDesc((C.c_int32 * 3)(*rep.L), rep.n_solvent, len(ids),
+            reps[r] = ReplicaDesc((C.c_int32 * 3)(*rep.L), rep.n_solvent, len(ids), int(sids[r]),
                                   ids.ctypes.data if len(ids) else None)
         self._alloc = None
         t = _torch_cuda()

@@ -550,14 +550,16 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
 
     // replicas, slots, cells, bodies
     std::vector<int32_t> body_shape;
+    std::vector<int32_t> ids;
     int64_t slot = 0, cells = 0, bodies = 0, sites = 0, rows = 0;
     for (int r = 0; r < n_replicas; ++r) {
         const mpcd_replica_desc &d = replicas[r];
         if (d.L[0] < 3 || d.L[1] < 3 || d.L[2] < 3 || d.L[0] > 4096 || d.L[1] > 4096 || d.L[2] > 4096 ||
-            d.n_solvent < 0 || d.n_bodies < 0 || (d.n_bodies > 0 && !d.body_shape)) {
+            d.n_solvent < 0 || d.n_bodies < 0 || (d.n_bodies > 0 && !d.body_shape) || d.stream_id < 0) {
             delete c;
             return MPCD_ERR_ARG;
         }
+        ids.push_back(d.stream_id);
         DevReplica R{};
         for (int k = 0; k < 3; ++k) R.L[k] = d.L[k];
         R.cell_base = (int32_t)cells;
@@ -568,7 +570,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
         R.site_begin = sites;
         R.row_begin = rows;
         R.key0 = (uint32_t)p.seed;
-        R.key1 = (uint32_t)(p.seed >> 32) ^ (uint32_t)r;
+        R.key1 = (uint32_t)(p.seed >> 32) ^ (uint32_t)d.stream_id;
         for (int b = 0; b < d.n_bodies; ++b) {
             int s = d.body_shape[b];
             if (s < 0 || s >= n_shapes) {
@@ -577,9 +579,10 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
             }
             body_shape.push_back(s);
             sites += c->shapes[s].n_sites;
-            // the minimum image must be unique for every centre pair
-            double reach = 2 * c->shapes[s].bound + c->shapes[s].wca_d + 1.2;
-            if (d.n_bodies > 1 && (reach > 0.5 * d.L[0] || reach > 0.5 * d.L[1] || reach > 0.5 * d.L[2])) {
+            // forces take the minimum image of every centre pair (Eq. 1), which is
+            // unique when the cutoff is below half of every box edge
+            const double rcut = 0.5 * (c->shapes[s].wca_d + c->max_wca_d) - 1.0 + 1.122462048309373;
+            if (d.n_bodies > 1 && (2.0 * rcut >= d.L[0] || 2.0 * rcut >= d.L[1] || 2.0 * rcut >= d.L[2])) {
                 delete c;
                 return MPCD_ERR_ARG;
             }
@@ -590,7 +593,9 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
         rows += d.n_solvent;
         c->reps.push_back(R);
     }
-    if (cells >= ((int64_t)1 << 31) || slot >= ((int64_t)1 << 31) || sites >= ((int64_t)1 << 31)) {
+    std::sort(ids.begin(), ids.end());
+    if (cells >= ((int64_t)1 << 31) || slot >= ((int64_t)1 << 31) || sites >= ((int64_t)1 << 31) ||
+        std::adjacent_find(ids.begin(), ids.end()) != ids.end()) {   // stream ids must be distinct
         delete c;
         return MPCD_ERR_ARG;
     }

@@ -219,6 +219,8 @@ class Replica:
     L: tuple                      # (Lx, Ly, Lz) cells per edge
     n_solvent: int
     body_shapes: List[int]        # shape index of each body
+    id: int = -1                  # index in the whole ensemble (-1: its position);
+                                  # keys the replica's random streams
 
 
 @dataclasses.dataclass
@@ -244,6 +246,24 @@ class System:
         for r in self.replicas:
             out += list(r.body_shapes)
         return np.array(out, dtype=np.int32)
+
+    def stream_ids(self) -> np.ndarray:
+        """Per-replica stream id: the replica's index in the whole ensemble, so
+        that its random streams do not depend on how the ensemble is split."""
+        return np.array([r.id if r.id >= 0 else i for i, r in enumerate(self.replicas)], dtype=np.int32)
+
+    def subset(self, ids: Sequence[int]) -> "System":
+        """The replicas `ids` (indices into this system) as a system of their own;
+        each keeps its stream id, so it evolves exactly as it does here."""
+        sid = self.stream_ids()
+        reps = [dataclasses.replace(self.replicas[i], body_shapes=list(self.replicas[i].body_shapes),
+                                    id=int(sid[i])) for i in ids]
+        sub = System(params=dataclasses.replace(self.params), shapes=self.shapes, replicas=reps,
+                     name=f"{self.name}[{len(reps)}]")
+        pl = getattr(self, "_placements", None)
+        if pl is not None:
+            sub._placements = [pl[i] for i in ids]
+        return sub
 
     def L_array(self) -> np.ndarray:
         return np.array([r.L for r in self.replicas], dtype=np.int32).reshape(-1, 3)
@@ -388,12 +408,15 @@ def initial_state(system: System, seed: Optional[int] = None) -> State:
     """Seeded initial state: uniform solvent with Maxwell-Boltzmann velocities
     at kT (zero net momentum per replica), bodies from the given placements
     with MB linear momentum and isotropic angular momentum of matching scale.
+    Each replica draws from its own generator, seeded by (seed, stream id), so
+    a subset of an ensemble starts from the same state as in the whole.
 
     For the P32 form every solvent value is rounded to float32 so that both
     implementations start from the same stored numbers.
     """
     p = system.params
-    rng = np.random.default_rng(p.seed if seed is None else seed)
+    base = p.seed if seed is None else seed
+    sids = system.stream_ids()
     Ns, B = system.n_solvent, system.n_bodies
     soff, boff = system.solvent_offsets(), system.body_offsets()
     x = np.empty((Ns, 3))
@@ -404,6 +427,7 @@ def initial_state(system: System, seed: Optional[int] = None) -> State:
     Lm = np.empty((B, 3))
     placements = getattr(system, "_placements", None)
     for r, rep in enumerate(system.replicas):
+        rng = np.random.default_rng([int(base), int(sids[r])])   # per replica: independent of the split
         L = np.array(rep.L, dtype=np.float64)
         s0, s1 = soff[r], soff[r + 1]
         b0, b1 = boff[r], boff[r + 1]

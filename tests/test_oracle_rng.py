@@ -77,7 +77,7 @@ def test_normals_are_standard_normal():
 
 
 def test_streams_differ_by_tag_step_replica():
-    osys = _sys()
+    osys = O.OracleSystem(I.batched_single_sphere(n_rep=2, Ls=(12,)))
     a = O.normals(osys, 0, 1, np.arange(100), O.TAG_SITE)
     b = O.normals(osys, 0, 1, np.arange(100), O.TAG_AT)
     c = O.normals(osys, 0, 2, np.arange(100), O.TAG_SITE)
