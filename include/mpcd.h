@@ -237,7 +237,9 @@ typedef struct {
     int32_t tile;           /* particles per work tile */
     int32_t ctas_per_sm;    /* persistent CTAs per SM (capped by shared memory) */
     int32_t sort_period;    /* steps between re-sorts */
-    int32_t staged;         /* 1: stage tiles in shared memory with bulk async copies,
+    int32_t staged;         /* 1: stage tiles in shared memory with bulk async copies (two-stage
+                               ring, CTA barriers); 2: warp-specialised - a producer warp drives
+                               a three-stage ring of bulk copies for the computing warps;
                                0: direct 128-bit loads; -1 keeps the current value */
 } mpcd_tuning;
 int mpcd_get_tuning(const mpcd_ctx *ctx, mpcd_tuning *out);

@@ -24,6 +24,7 @@ UNITS = {
     "kernels_solvent.cu": [],
     "kernels_bodies.cu": ["-fmad=false"],
     "static_collide.cu": [],
+    "kernels_sort.cu": [],
 }
 
 

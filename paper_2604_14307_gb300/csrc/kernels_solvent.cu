@@ -610,6 +610,214 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
     if (bad) atomicOr(a.d_err, ERR_POSITION);
 }
 
+// --------------------------- warp-specialised pass (producer + consumers)
+// The last warp of the CTA is the producer: one lane loads the tile
+// metadata (range, box, grid shifts), issues the bulk copies of each tile into
+// a three-stage shared-memory ring and, once the consumer warps have signalled
+// that a tile is done, its bulk stores.  The consumer warps only compute: no
+// CTA-wide barrier inside the loop, so tile set-up and write-back overlap with
+// the arithmetic of other tiles.  Stage s of local tile k: loads complete on
+// full[s], the consumers arrive on done[s]; a stage is refilled only after the
+// store issued from it two tiles earlier has finished reading it.  Every wait
+// is bounded; on a timeout the error word gets ERR_TIMEOUT and the CTA drains.
+constexpr int WS_STAGES = 3;
+
+struct TileMeta {
+    int32_t S[6];     // grid shifts: collision (0..2), binning (3..5)
+    int32_t L[3];
+    int32_t base;     // first global cell of the replica
+    int32_t n;        // particles in the tile
+    uint32_t key0, key1;
+    int32_t pad;
+    int64_t beg;      // first slot
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+
+template <typename Real, int RULE, int FLAGS>
+__global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
+{
+    constexpr bool COLLIDE = FLAGS & SOLV_COLLIDE;
+    constexpr bool STREAM = FLAGS & SOLV_STREAM;
+    constexpr bool BIN = FLAGS & SOLV_BIN;
+    typedef typename SumWord<Real>::type W;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[WS_STAGES], done[WS_STAGES];
+    __shared__ TileMeta meta[WS_STAGES];
+
+    const int n_cons = (int)blockDim.x - 32;           // consumer threads
+    const int n_cwarps = n_cons >> 5;
+    const bool producer = (int)threadIdx.x >= n_cons;
+    const size_t SB = stage_bytes<Real, RULE>(cap);
+    const int64_t step = *a.d_step;
+    Real *G[6] = {reinterpret_cast<Real *>(a.x), reinterpret_cast<Real *>(a.y), reinterpret_cast<Real *>(a.z),
+                  reinterpret_cast<Real *>(a.vx), reinterpret_cast<Real *>(a.vy), reinterpret_cast<Real *>(a.vz)};
+    const int K = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < WS_STAGES; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&done[q], (uint32_t)n_cwarps);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();   // the only CTA-wide barrier
+
+    if (producer) {
+        if (threadIdx.x != (unsigned)n_cons) return;   // one lane drives the ring
+        auto store_tile = [&](int j) -> bool {          // local tile j, after its consumers are done
+            const int q = j % WS_STAGES;
+            if (!mbar_wait_bounded(&done[q], (uint32_t)((j / WS_STAGES) & 1))) return false;
+            if (STREAM || COLLIDE) {
+                const TileMeta &m = meta[q];
+                const uint32_t nb = (uint32_t)(((m.n + 3) & ~3) * sizeof(Real));
+                unsigned char *base = smem + q * SB;
+                if (STREAM)
+                    for (int c = 0; c < 3; ++c) bulk_store(G[c] + m.beg, base + (size_t)c * cap * sizeof(Real), nb);
+                if (COLLIDE)
+                    for (int c = 3; c < 6; ++c) bulk_store(G[c] + m.beg, base + (size_t)c * cap * sizeof(Real), nb);
+            }
+            bulk_commit();
+            return true;
+        };
+        bool ok = true;
+        for (int k = 0; k < K && ok; ++k) {
+            const int q = k % WS_STAGES;
+            if (k >= WS_STAGES) bulk_wait_read_1();     // the store of tile k - 3 has read stage q
+            const Tile tl = a.tiles[blockIdx.x + k * gridDim.x];
+            const DevReplica r = a.reps[tl.rep];
+            TileMeta &m = meta[q];
+            if (COLLIDE) grid_shift(r, step, &m.S[0]);
+            if (BIN) grid_shift(r, step + (COLLIDE ? 1 : 0), &m.S[3]);
+            m.L[0] = r.L[0]; m.L[1] = r.L[1]; m.L[2] = r.L[2];
+            m.base = r.cell_base;
+            m.n = (int)(tl.end - tl.begin);
+            m.key0 = r.key0;
+            m.key1 = r.key1;
+            m.beg = tl.begin;
+            const int n4 = (m.n + 3) & ~3;
+            const uint32_t nb = (uint32_t)(n4 * sizeof(Real));
+            unsigned char *base = smem + q * SB;
+            mbar_expect_tx(&full[q], 6 * nb + (RULE == 1 ? (uint32_t)(n4 * 4) : 0u));
+            for (int c = 0; c < 6; ++c) bulk_load(base + (size_t)c * cap * sizeof(Real), G[c] + tl.begin, nb, &full[q]);
+            if (RULE == 1) bulk_load(base + (size_t)6 * cap * sizeof(Real), a.tag + tl.begin, (uint32_t)(n4 * 4), &full[q]);
+            if (k >= 1) ok = store_tile(k - 1);
+        }
+        if (ok && K >= 1) ok = store_tile(K - 1);
+        if (!ok) atomicOr(a.d_err, ERR_TIMEOUT);
+        bulk_wait_all();
+        return;
+    }
+
+    // consumers
+    const Real dt = Consts<Real>::dt(a), m = Consts<Real>::m(a), kT = Consts<Real>::kT(a);
+    const Real ca = Consts<Real>::ca(a), sa = Consts<Real>::sa(a);
+    const Real sc = sqrt(kT / m);
+    W *sums = reinterpret_cast<W *>(a.sums);
+    const int64_t C = a.n_cells;
+    int bad = 0;
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < K; ++k) {
+        const int q = k % WS_STAGES;
+        if (!mbar_wait_bounded(&full[q], (uint32_t)((k / WS_STAGES) & 1))) {
+            if (lane == 0) atomicOr(a.d_err, ERR_TIMEOUT);
+            break;
+        }
+        const TileMeta &mt = meta[q];
+        int32_t sS[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sS[c] = mt.S[c];
+        const int L0 = mt.L[0], L1 = mt.L[1], L2 = mt.L[2], base = mt.base, n = mt.n;
+        const Real Lx = (Real)L0, Ly = (Real)L1, Lz = (Real)L2;
+        DevReplica rr;
+        rr.key0 = mt.key0;
+        rr.key1 = mt.key1;
+        Real *S[6];
+        for (int c = 0; c < 6; ++c) S[c] = reinterpret_cast<Real *>(smem + q * SB + (size_t)c * cap * sizeof(Real));
+        const uint32_t *stag = reinterpret_cast<const uint32_t *>(smem + q * SB + (size_t)6 * cap * sizeof(Real));
+
+        // uniform trip count: every lane of a warp reaches the warp-wide flush
+        for (int i0 = 0; i0 < n; i0 += 4 * n_cons) {
+            const int i = i0 + 4 * (int)threadIdx.x;
+            const int nv = max(0, min(4, n - i));
+            Real x[4], y[4], z[4], vx[4], vy[4], vz[4];
+            if (nv > 0) {
+                sld4(S[0] + i, x); sld4(S[1] + i, y); sld4(S[2] + i, z);
+                sld4(S[3] + i, vx); sld4(S[4] + i, vy); sld4(S[5] + i, vz);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[j] = y[j] = z[j] = vx[j] = vy[j] = vz[j] = Real(0);
+            }
+            uint32_t tg[4] = {0, 0, 0, 0};
+            if (RULE == 1 && nv > 0) {
+                uint4 t4 = *reinterpret_cast<const uint4 *>(stag + i);
+                tg[0] = t4.x; tg[1] = t4.y; tg[2] = t4.z; tg[3] = t4.w;
+            }
+            if (COLLIDE) {
+                CellParams<Real> p[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int c = base + cell_axis(x[j], sS[0], L0) +
+                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    c = j < nv ? c : base;
+                    p[j] = get_params<Real>(a.params, c);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j < nv && p[j].kappa >= Real(0)) {
+                        if (RULE == 0) {
+                            srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
+                        } else {
+                            Real nn[3];
+                            normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn);
+                            vx[j] = p[j].ux + sc * nn[0] - p[j].ax;
+                            vy[j] = p[j].uy + sc * nn[1] - p[j].ay;
+                            vz[j] = p[j].uz + sc * nn[2] - p[j].az;
+                        }
+                    }
+                }
+            }
+            if (STREAM) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < nv) {
+                        x[j] = drift(x[j], vx[j], dt, Lx, bad);
+                        y[j] = drift(y[j], vy[j], dt, Ly, bad);
+                        z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                    }
+            }
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+                                                m, sc, sums, C);
+            if (nv > 0) {
+                if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
+                if (COLLIDE) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
+            }
+        }
+        fence_async_smem();   // results visible to the bulk stores
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&done[q]);
+    }
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+template <typename Real, int RULE, int FLAGS>
+static void launch_ws(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
+{
+    static bool configured = false;
+    const size_t bytes = (size_t)WS_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
+    if (!configured) {
+        cudaFuncSetAttribute(k_solvent_ws<Real, RULE, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        configured = true;
+    }
+    k_solvent_ws<Real, RULE, FLAGS><<<cfg.grid, cfg.block + 32, bytes, s>>>(a, cfg.cap);
+}
+
 template <typename Real, int RULE, int FLAGS>
 static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
@@ -626,6 +834,19 @@ static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 template <typename Real, int RULE>
 static void dispatch_flags(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s)
 {
+    if (cfg.staged == 2) {
+        switch (flags) {
+        case SOLV_STREAM: launch_ws<Real, RULE, SOLV_STREAM>(a, cfg, s); break;
+        case SOLV_BIN: launch_ws<Real, RULE, SOLV_BIN>(a, cfg, s); break;
+        case SOLV_COLLIDE: launch_ws<Real, RULE, SOLV_COLLIDE>(a, cfg, s); break;
+        case SOLV_STREAM | SOLV_BIN: launch_ws<Real, RULE, SOLV_STREAM | SOLV_BIN>(a, cfg, s); break;
+        case SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN:
+            launch_ws<Real, RULE, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN>(a, cfg, s);
+            break;
+        default: break;
+        }
+        return;
+    }
     if (cfg.staged) {
         switch (flags) {
         case SOLV_STREAM: launch_staged<Real, RULE, SOLV_STREAM>(a, cfg, s); break;

@@ -79,11 +79,13 @@ struct mpcd_ctx {
     int *d_err = nullptr;
     double *d_diag = nullptr;
     int32_t *counts = nullptr, *ex = nullptr, *cursor = nullptr, *scan_bs = nullptr;
+    int32_t *rs_hist = nullptr, *rs_ex = nullptr, *rs_bs = nullptr;   // radix-sort digit counts
+    void *rec = nullptr;            // [Nslots][8] Real: particle records for the state permutations
     void *staging = nullptr;
 
     int64_t step = 0, since_sort = 0, last_key = -1;
     int num_sms = 0;
-    mpcd_tuning tune{256, 2048, 2, 20, 1};
+    mpcd_tuning tune{512, 2048, 1, 20, 2};
     int smem_per_sm = 0;
 
     bool profiling = false;
@@ -297,21 +299,30 @@ double solvent_bytes(const mpcd_ctx *c, int flags)
 }
 
 // ----------------------------------------------------------- step pieces
-bool staged_fits(const mpcd_ctx *c, int tile, int block)
+// dynamic shared memory of the staged (two-stage ring) or warp-specialised
+// (three-stage ring) solvent pass
+size_t ring_bytes(const mpcd_ctx *c, int mode, int tile)
 {
-    return solvent_smem_bytes(c->prm.precision, c->prm.rule, tile, block) <= 200 * 1024;
+    const size_t stage = solvent_stage_bytes(c->prm.precision, c->prm.rule, tile);
+    return (mode == 2 ? 3 : 2) * stage;
+}
+
+bool staged_fits(const mpcd_ctx *c, int tile, int mode)
+{
+    return ring_bytes(c, mode, tile) <= 200 * 1024;
 }
 
 LaunchCfg solvent_cfg(const mpcd_ctx *c)
 {
-    LaunchCfg cfg{c->tune.block, 1, c->tune.staged && staged_fits(c, c->tune.tile, c->tune.block) ? 1 : 0,
-                  c->tune.tile};
+    const int mode = c->tune.staged && staged_fits(c, c->tune.tile, c->tune.staged) ? c->tune.staged : 0;
+    LaunchCfg cfg{c->tune.block, 1, mode, c->tune.tile};
     int per_sm = c->tune.ctas_per_sm;
-    if (cfg.staged) {
-        size_t bytes = solvent_smem_bytes(c->prm.precision, c->prm.rule, c->tune.tile, c->tune.block) + 1024;
+    if (mode) {
+        size_t bytes = ring_bytes(c, mode, c->tune.tile) + 1024;
         per_sm = std::max(1, std::min<int>(per_sm, (int)(c->smem_per_sm / bytes)));
     }
-    per_sm = std::max(1, std::min(per_sm, 2048 / c->tune.block));
+    const int threads = c->tune.block + (mode == 2 ? 32 : 0);
+    per_sm = std::max(1, std::min(per_sm, 2048 / threads));
     cfg.grid = std::max(1, std::min((int)c->tiles.size(), c->num_sms * per_sm));
     return cfg;
 }
@@ -433,6 +444,11 @@ int check_device_error(mpcd_ctx *c, cudaStream_t s)
     CK(c, cudaStreamSynchronize(s));
     if (h & ERR_POSITION)
         return fail(c, MPCD_ERR_STATE, "a particle or body left the periodic box in one step (|v dt| >= L)");
+    if (h & ERR_INDEX) {
+        int w[2] = {0, 0};
+        CK(c, cudaMemcpy(w, c->d_err, sizeof w, cudaMemcpyDeviceToHost));
+        return fail(c, MPCD_ERR_STATE, "an index check failed (check %d); no access was made", w[1]);
+    }
     if (h) return fail(c, MPCD_ERR_STATE, "device error word 0x%x", h);
     return MPCD_OK;
 }
@@ -653,6 +669,10 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     ok &= (c->cursor = (int32_t *)A(c->C * 4)) != nullptr;
     ok &= (c->scan_bs = (int32_t *)A(scan_block_sums_size(c->C) * 4)) != nullptr;
     ok &= (c->staging = A(std::max<int64_t>(1, c->Ns) * 6 * c->realsz)) != nullptr;
+    ok &= (c->rec = A((size_t)c->Nslots * 8 * c->realsz)) != nullptr;
+    ok &= (c->rs_hist = (int32_t *)A(radix_hist_ints(c->Nslots) * 4)) != nullptr;
+    ok &= (c->rs_ex = (int32_t *)A(radix_hist_ints(c->Nslots) * 4)) != nullptr;
+    ok &= (c->rs_bs = (int32_t *)A(scan_block_sums_size((int64_t)radix_hist_ints(c->Nslots)) * 4)) != nullptr;
     if (!ok) {
         mpcd_destroy(c);
         return MPCD_ERR_OOM;
@@ -786,10 +806,20 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
         CK(c, cudaMemcpyAsync(stg + n3 * c->realsz, h->v, n3 * c->realsz, cudaMemcpyHostToDevice, s));
     }
     c->cur = 0;
-    for (int k = 0; k < 6; ++k) CK(c, cudaMemsetAsync(c->sol[0][k], 0, c->Nslots * c->realsz, s));
-    CK(c, cudaMemsetAsync(c->tag[0], 0xFF, c->Nslots * 4, s));
     StepArgs a = make_args(c);
-    launch_aos_to_soa(a, stg, stg + n3 * c->realsz, s);
+    {
+        // cell-sorted storage from the tag-ordered rows: stable radix sort of
+        // (cell, row) pairs in the spare buffer, then one gather (memory
+        // locality only; results do not depend on the order)
+        uint32_t *kA = (uint32_t *)c->sol[1][0], *vA = (uint32_t *)c->sol[1][1];
+        uint32_t *kB = (uint32_t *)c->sol[1][2], *vB = (uint32_t *)c->sol[1][3];
+        launch_keys_in(a, stg, kA, vA, c->Nslots, s);
+        launch_pack_rows(a, stg, stg + n3 * c->realsz, c->rec, c->Ns, c->num_sms, s);
+        const int nb = key_bits((uint64_t)std::max<int64_t>(c->C - 1, 0));
+        const int inB =
+            launch_radix_sort(kA, vA, kB, vB, c->Nslots, nb, c->rs_hist, c->rs_ex, c->rs_bs, c->d_err, s);
+        launch_gather_in(a, c->rec, inB ? vB : vA, c->Nslots, c->Ns, c->num_sms, s);
+    }
     if (c->B) CK(c, cudaMemcpyAsync(c->d_bodies, hb.data(), c->B * sizeof(DevBody), cudaMemcpyHostToDevice, s));
     CK(c, cudaMemsetAsync(c->sums, 0, (size_t)c->C * c->nw * 8, s));
     int64_t stp = h->step;
@@ -798,10 +828,12 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
     launch_body_force(a, 0, s);
     CK(c, cudaGetLastError());
     // the upload kernel flags positions outside [0, L): reject the state
-    int flag = 0;
-    CK(c, cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int flag[2] = {0, 0};
+    CK(c, cudaMemcpyAsync(flag, c->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(c, cudaStreamSynchronize(s));
-    if (flag) {
+    if (flag[0] & ~ERR_POSITION)
+        return fail(c, MPCD_ERR_STATE, "set_state: device error word 0x%x (check %d)", flag[0], flag[1]);
+    if (flag[0]) {
         CK(c, cudaMemset(c->d_err, 0, sizeof(int)));
         CK(c, cudaMemset(c->tag[0], 0xFF, c->Nslots * 4));
         return MPCD_ERR_ARG;
@@ -809,12 +841,6 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
     c->step = h->step;
     c->since_sort = 0;
     c->last_key = -1;
-    // start from cell-sorted storage (memory locality; no effect on results)
-    if (c->prm.sort_period >= 0) {
-        int e = do_sort(c, 0, s);
-        if (e) return e;
-        CK(c, cudaGetLastError());
-    }
     return MPCD_OK;
 }
 
@@ -828,7 +854,19 @@ int mpcd_get_state(mpcd_ctx *c, mpcd_host_state *h, void *stream)
     const size_t n3 = (size_t)c->Ns * 3;
     char *stg = (char *)c->staging;
     StepArgs a = make_args(c);
-    launch_soa_to_aos(a, stg, stg + n3 * c->realsz, nullptr, s);
+    {
+        // tag order from the cell-sorted storage: stable radix sort of
+        // (host row, slot) pairs in the spare buffer, then a gather whose
+        // stores are row-contiguous
+        const int alt = c->cur ^ 1;
+        uint32_t *kA = (uint32_t *)c->sol[alt][0], *vA = (uint32_t *)c->sol[alt][1];
+        uint32_t *kB = (uint32_t *)c->sol[alt][2], *vB = (uint32_t *)c->sol[alt][3];
+        launch_keys_out(a, kA, vA, c->Nslots, (uint32_t)c->Ns, s);
+        const int nb = key_bits((uint64_t)c->Ns);
+        const int inB =
+            launch_radix_sort(kA, vA, kB, vB, c->Nslots, nb, c->rs_hist, c->rs_ex, c->rs_bs, c->d_err, s);
+        launch_gather_out(a, inB ? vB : vA, c->rec, stg, stg + n3 * c->realsz, c->Ns, c->Nslots, c->num_sms, s);
+    }
     CK(c, cudaGetLastError());
     if (c->Ns) {
         CK(c, cudaMemcpyAsync(h->x, stg, n3 * c->realsz, cudaMemcpyDeviceToHost, s));
@@ -1055,7 +1093,7 @@ int mpcd_set_tuning(mpcd_ctx *c, const mpcd_tuning *t)
     }
     if (t->ctas_per_sm > 0) c->tune.ctas_per_sm = std::min(t->ctas_per_sm, 32);
     if (t->sort_period > 0) c->tune.sort_period = t->sort_period;
-    if (t->staged >= 0) c->tune.staged = t->staged ? 1 : 0;
+    if (t->staged >= 0) c->tune.staged = std::min(t->staged, 2);
     CK(c, cudaSetDevice(c->device));
     build_tiles(c);
     int e = upload_tiles(c);
@@ -1102,7 +1140,11 @@ int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
     for (int bl : {128, 256, 512})
         for (int tl : {1024, 2048, 4096})
             for (int ct : {1, 2, 4})
-                if (staged_fits(c, tl, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 1});
+                if (staged_fits(c, tl, 1)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 1});
+    for (int bl : {256, 512})
+        for (int tl : {1024, 2048})
+            for (int ct : {1, 2})
+                if (staged_fits(c, tl, 2)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 2});
     for (int bl : {256, 512})
         for (int ct : {2, 4})
             cand.push_back(mpcd_tuning{bl, 8192, ct, c->tune.sort_period, 0});

@@ -26,7 +26,7 @@ namespace mpcd {
 enum : uint32_t { TAG_SHIFT = 1, TAG_AXIS = 2, TAG_THERMO = 3, TAG_THERMO_ODD = 4,
                   TAG_SITE = 5, TAG_AT = 6 };
 // Bits of the device error word.
-enum : int { ERR_POSITION = 1, ERR_CELL = 2, ERR_TIMEOUT = 4 };
+enum : int { ERR_POSITION = 1, ERR_CELL = 2, ERR_TIMEOUT = 4, ERR_INDEX = 8 };
 
 constexpr uint32_t PAD_TAG = 0xFFFFFFFFu;
 constexpr int NLIST_MAX = 96;       // neighbour-list capacity per body
@@ -286,6 +286,26 @@ void launch_sort_scatter(const StepArgs &a, const int32_t *offsets, int32_t *cur
 void launch_sort_canonical(const StepArgs &a, void *const arr[6], uint32_t *tag,
                            const int32_t *offsets, cudaStream_t s);
 size_t scan_block_sums_size(int64_t n);
+
+// host-state ingest / egress by stable radix sort (kernels_sort.cu)
+size_t radix_hist_ints(int64_t n);          // ints of the per-pass digit histogram
+int key_bits(uint64_t max_key);             // bits needed for keys <= max_key
+// stable sort of (key, value) pairs by the low nbits; returns 1 if the result
+// is in (kB, vB), 0 if in (kA, vA)
+int launch_radix_sort(uint32_t *kA, uint32_t *vA, uint32_t *kB, uint32_t *vB, int64_t n, int nbits,
+                      int32_t *hist, int32_t *hist_ex, int32_t *scan_bs, int *err, cudaStream_t s);
+void launch_keys_in(const StepArgs &a, const void *xa, uint32_t *keys, uint32_t *vals, int64_t nslots,
+                    cudaStream_t s);
+// host rows -> 8-word records rec[n_rows][8] (the ingest gather reads one record per particle)
+void launch_pack_rows(const StepArgs &a, const void *xa, const void *va, void *rec, int64_t n_rows, int num_sms,
+                      cudaStream_t s);
+void launch_gather_in(const StepArgs &a, const void *rec, const uint32_t *vals, int64_t nslots, int64_t n_rows,
+                      int num_sms, cudaStream_t s);
+void launch_keys_out(const StepArgs &a, uint32_t *keys, uint32_t *vals, int64_t nslots, uint32_t n_rows,
+                     cudaStream_t s);
+// slots -> records rec[nslots][8], then host rows in order from them
+void launch_gather_out(const StepArgs &a, const uint32_t *vals, void *rec, void *xa, void *va, int64_t n_rows,
+                       int64_t nslots, int num_sms, cudaStream_t s);
 
 // bodies and sites (kernels_bodies.cu)
 void launch_body_md(const StepArgs &a, cudaStream_t s);

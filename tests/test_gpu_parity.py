@@ -299,14 +299,16 @@ def test_invalid_arguments_are_rejected(B):
 
 @pytest.mark.parametrize("rule", [I.SRD, I.AT])
 def test_staged_and_direct_solvent_passes_agree_bitwise(B, rule):
-    """The shared-memory staged pass (bulk async copies) and the direct pass
-    compute the same thing; every launch shape gives bit-identical P32 states."""
+    """The direct pass, the shared-memory staged pass (bulk async copies) and
+    the warp-specialised pass compute the same thing; every launch shape gives
+    bit-identical P32 states."""
     system = I.suspension(18, 5.0, 0.15, 2.0, 2, 5.0, rule, 1, I.P32, seed=12, name="ab")
     system.replicas[0].n_solvent -= 3          # a ragged tail
     st = I.initial_state(system)
     ref = None
     for staged, block, tile, ctas in [(0, 256, 8192, 4), (1, 128, 1024, 1), (1, 256, 2048, 2),
-                                      (1, 512, 4096, 1), (1, 96, 1000, 3)]:
+                                      (1, 512, 4096, 1), (1, 96, 1000, 3), (2, 256, 1024, 2),
+                                      (2, 512, 2048, 1), (2, 96, 1000, 3)]:
         sim = B.Simulation(system)
         sim.set_tuning(block=block, tile=tile, ctas_per_sm=ctas, staged=staged)
         sim.set_state(st)
@@ -318,3 +320,23 @@ def test_staged_and_direct_solvent_passes_agree_bitwise(B, rule):
             continue
         for k in ("x", "v", "R", "q", "P", "Lm"):
             assert np.array_equal(getattr(g, k), getattr(ref, k)), (staged, block, tile, k)
+
+
+@pytest.mark.parametrize("prec", [I.P32, I.P64])
+def test_state_round_trip_is_exact(B, prec):
+    """mpcd_set_state stores the solvent cell-sorted (radix sort of (cell, row)
+    pairs, then a gather) and mpcd_get_state brings it back to row order (radix
+    sort of (row, slot) pairs): with no step in between the round trip is the
+    identity, for uneven replicas with ragged tails and a box large enough for
+    three digit passes."""
+    for system in (I.batched_single_sphere(n_rep=5, precision=prec, seed=6, Ls=(6, 8, 12)),
+                   I.suspension(60, 10.0, 0.1, 4.0, 3, 10.0, I.SRD, 1, prec, seed=2, name="rt")):
+        system.replicas[0].n_solvent -= 5
+        st = I.initial_state(system)
+        sim = B.Simulation(system)
+        sim.set_state(st)
+        g = sim.get_state()
+        sim.close()
+        real = np.float32 if prec == I.P32 else np.float64
+        assert np.array_equal(g.x, st.x.astype(real)) and np.array_equal(g.v, st.v.astype(real))
+        assert np.array_equal(g.R, st.R) and np.array_equal(g.P, st.P)
