@@ -240,6 +240,7 @@ typedef struct {
     int32_t staged;         /* 1: stage tiles in shared memory with bulk async copies (two-stage
                                ring, CTA barriers); 2: warp-specialised - a producer warp drives
                                a three-stage ring of bulk copies for the computing warps;
+                               3: a three-stage ring per warp (tile = particles per warp tile);
                                0: direct 128-bit loads; -1 keeps the current value */
 } mpcd_tuning;
 int mpcd_get_tuning(const mpcd_ctx *ctx, mpcd_tuning *out);

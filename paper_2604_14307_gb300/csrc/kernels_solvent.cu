@@ -805,6 +805,216 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
     if (bad) atomicOr(a.d_err, ERR_POSITION);
 }
 
+// ----------------------------------------------- warp-tiled pass (per warp)
+// Every warp runs its own three-stage ring of small tiles (the tile table is
+// built with the warp-tile size): lane 0 issues the bulk loads of tile k+1
+// and the bulk stores of tile k, the warp computes tile k.  Warps share no
+// barrier, so they drift apart and the latency of one warp's parameter
+// gathers is covered by the arithmetic of others.  The tile record of the
+// next fetch is loaded one tile ahead; the grid shifts are computed once per
+// replica a warp meets.  Every wait is bounded.
+constexpr int WT_STAGES = 3, WT_MAX_WARPS = 16;
+
+template <typename Real, int RULE, int FLAGS>
+__global__ void __launch_bounds__(512) k_solvent_wt(StepArgs a, int cap)
+{
+    constexpr bool COLLIDE = FLAGS & SOLV_COLLIDE;
+    constexpr bool STREAM = FLAGS & SOLV_STREAM;
+    constexpr bool BIN = FLAGS & SOLV_BIN;
+    typedef typename SumWord<Real>::type W;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[WT_MAX_WARPS][WT_STAGES];
+    __shared__ TileMeta meta[WT_MAX_WARPS][WT_STAGES];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const size_t SB = stage_bytes<Real, RULE>(cap);
+    unsigned char *wsm = smem + (size_t)warp * WT_STAGES * SB;
+    const int64_t step = *a.d_step;
+    // the global arrays are read from the kernel parameters where lane 0 needs them
+    auto garr = [&](int c) -> Real * {
+        void *p = c == 0 ? a.x : c == 1 ? a.y : c == 2 ? a.z : c == 3 ? a.vx : c == 4 ? a.vy : a.vz;
+        return reinterpret_cast<Real *>(p);
+    };
+    const int gw = blockIdx.x * nwarps + warp, GW = gridDim.x * nwarps;
+    const int K = a.n_tiles > gw ? (a.n_tiles - 1 - gw) / GW + 1 : 0;   // tiles of this warp
+
+    if (lane == 0) {
+        for (int q = 0; q < WT_STAGES; ++q) mbar_init(&full[warp][q], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+
+    // lane 0 only: metadata and bulk loads of local tile k into stage q.  The
+    // replica fields and grid shifts of the last replica met stay in shared
+    // memory (wcache), so they take no registers in the computing lanes.
+    __shared__ TileMeta wcache[WT_MAX_WARPS];
+    __shared__ int wrep[WT_MAX_WARPS];
+    if (lane == 0) wrep[warp] = -1;
+    int32_t nrep = 0;
+    int64_t nbeg = 0, nend = 0;   // tile record of the next fetch
+    if (lane == 0 && K > 0) {
+        const Tile t0 = a.tiles[gw];
+        nrep = t0.rep; nbeg = t0.begin; nend = t0.end;
+    }
+    auto fetch = [&](int k, int q) {
+        const int rep = nrep;
+        const int64_t tbeg = nbeg, tend = nend;
+        if (k + 1 < K) {   // used by the following fetch
+            const Tile tn = a.tiles[gw + (k + 1) * GW];
+            nrep = tn.rep; nbeg = tn.begin; nend = tn.end;
+        }
+        TileMeta &wc = wcache[warp];
+        if (rep != wrep[warp]) {
+            const DevReplica cr = a.reps[rep];
+            if (COLLIDE) grid_shift(cr, step, &wc.S[0]);
+            if (BIN) grid_shift(cr, step + (COLLIDE ? 1 : 0), &wc.S[3]);
+            wc.L[0] = cr.L[0]; wc.L[1] = cr.L[1]; wc.L[2] = cr.L[2];
+            wc.base = cr.cell_base;
+            wc.key0 = cr.key0;
+            wc.key1 = cr.key1;
+            wrep[warp] = rep;
+        }
+        TileMeta &m = meta[warp][q];
+        m = wc;
+        m.n = (int)(tend - tbeg);
+        m.beg = tbeg;
+        const Tile tl{rep, 0, tbeg, tend};
+        const int n4 = (m.n + 3) & ~3;
+        const uint32_t nb = (uint32_t)(n4 * sizeof(Real));
+        unsigned char *base = wsm + q * SB;
+        mbar_expect_tx(&full[warp][q], 6 * nb + (RULE == 1 ? (uint32_t)(n4 * 4) : 0u));
+        for (int c = 0; c < 6; ++c) bulk_load(base + (size_t)c * cap * sizeof(Real), garr(c) + tl.begin, nb, &full[warp][q]);
+        if (RULE == 1) bulk_load(base + (size_t)6 * cap * sizeof(Real), a.tag + tl.begin, (uint32_t)(n4 * 4), &full[warp][q]);
+    };
+
+    const Real dt = Consts<Real>::dt(a), m = Consts<Real>::m(a), kT = Consts<Real>::kT(a);
+    const Real ca = Consts<Real>::ca(a), sa = Consts<Real>::sa(a);
+    const Real sc = sqrt(kT / m);
+    W *sums = reinterpret_cast<W *>(a.sums);
+    const int64_t C = a.n_cells;
+    int bad = 0;
+    if (lane == 0 && K > 0) fetch(0, 0);
+    __syncwarp();
+    for (int k = 0; k < K; ++k) {
+        const int q = k % WT_STAGES;
+        if (lane == 0 && k + 1 < K) {
+            if (k + 1 >= WT_STAGES) bulk_wait_read_1();   // the store of tile k - 2 has read that stage
+            fetch(k + 1, (k + 1) % WT_STAGES);
+        }
+        const bool got = mbar_wait_bounded(&full[warp][q], (uint32_t)((k / WT_STAGES) & 1));
+        if (!__all_sync(0xffffffffu, got)) {
+            if (lane == 0) {
+                atomicOr(a.d_err, ERR_TIMEOUT);
+                // let the copies in flight land before the CTA leaves (bounded)
+                mbar_wait_bounded(&full[warp][q], (uint32_t)((k / WT_STAGES) & 1));
+                if (k + 1 < K)
+                    mbar_wait_bounded(&full[warp][(k + 1) % WT_STAGES], (uint32_t)(((k + 1) / WT_STAGES) & 1));
+            }
+            break;
+        }
+        const TileMeta &mt = meta[warp][q];
+        int32_t sS[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sS[c] = mt.S[c];
+        const int L0 = mt.L[0], L1 = mt.L[1], L2 = mt.L[2], base = mt.base, n = mt.n;
+        const Real Lx = (Real)L0, Ly = (Real)L1, Lz = (Real)L2;
+        DevReplica rr;
+        rr.key0 = mt.key0;
+        rr.key1 = mt.key1;
+        Real *S[6];
+        for (int c = 0; c < 6; ++c) S[c] = reinterpret_cast<Real *>(wsm + q * SB + (size_t)c * cap * sizeof(Real));
+        const uint32_t *stag = reinterpret_cast<const uint32_t *>(wsm + q * SB + (size_t)6 * cap * sizeof(Real));
+
+        for (int i0 = 0; i0 < n; i0 += 128) {
+            const int i = i0 + 4 * lane;
+            const int nv = max(0, min(4, n - i));
+            Real x[4], y[4], z[4], vx[4], vy[4], vz[4];
+            if (nv > 0) {
+                sld4(S[0] + i, x); sld4(S[1] + i, y); sld4(S[2] + i, z);
+                sld4(S[3] + i, vx); sld4(S[4] + i, vy); sld4(S[5] + i, vz);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) x[j] = y[j] = z[j] = vx[j] = vy[j] = vz[j] = Real(0);
+            }
+            uint32_t tg[4] = {0, 0, 0, 0};
+            if (RULE == 1 && nv > 0) {
+                uint4 t4 = *reinterpret_cast<const uint4 *>(stag + i);
+                tg[0] = t4.x; tg[1] = t4.y; tg[2] = t4.z; tg[3] = t4.w;
+            }
+            if (COLLIDE) {
+                CellParams<Real> p[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int c = base + cell_axis(x[j], sS[0], L0) +
+                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    c = j < nv ? c : base;
+                    p[j] = get_params<Real>(a.params, c);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j < nv && p[j].kappa >= Real(0)) {
+                        if (RULE == 0) {
+                            srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
+                        } else {
+                            Real nn[3];
+                            normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn);
+                            vx[j] = p[j].ux + sc * nn[0] - p[j].ax;
+                            vy[j] = p[j].uy + sc * nn[1] - p[j].ay;
+                            vz[j] = p[j].uz + sc * nn[2] - p[j].az;
+                        }
+                    }
+                }
+            }
+            if (STREAM) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < nv) {
+                        x[j] = drift(x[j], vx[j], dt, Lx, bad);
+                        y[j] = drift(y[j], vy[j], dt, Ly, bad);
+                        z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                    }
+            }
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+                                                m, sc, sums, C);
+            if (nv > 0) {
+                if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
+                if (COLLIDE) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
+            }
+        }
+        fence_async_smem();   // results visible to the bulk stores
+        __syncwarp();
+        if (lane == 0 && (STREAM || COLLIDE)) {
+            const uint32_t nb = (uint32_t)(((n + 3) & ~3) * sizeof(Real));
+            unsigned char *sb = wsm + q * SB;
+            const int64_t beg = mt.beg;
+            if (STREAM)
+                for (int c = 0; c < 3; ++c) bulk_store(garr(c) + beg, sb + (size_t)c * cap * sizeof(Real), nb);
+            if (COLLIDE)
+                for (int c = 3; c < 6; ++c) bulk_store(garr(c) + beg, sb + (size_t)c * cap * sizeof(Real), nb);
+        }
+        if (lane == 0) bulk_commit();
+        __syncwarp();
+    }
+    if (lane == 0) bulk_wait_all();
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+template <typename Real, int RULE, int FLAGS>
+static void launch_wt(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
+{
+    static bool configured = false;
+    const int warps = cfg.block / 32;
+    const size_t bytes = (size_t)warps * WT_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
+    if (!configured) {
+        cudaFuncSetAttribute(k_solvent_wt<Real, RULE, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             220 * 1024);
+        configured = true;
+    }
+    k_solvent_wt<Real, RULE, FLAGS><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
+}
+
 template <typename Real, int RULE, int FLAGS>
 static void launch_ws(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
@@ -834,6 +1044,19 @@ static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 template <typename Real, int RULE>
 static void dispatch_flags(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s)
 {
+    if (cfg.staged == 3) {
+        switch (flags) {
+        case SOLV_STREAM: launch_wt<Real, RULE, SOLV_STREAM>(a, cfg, s); break;
+        case SOLV_BIN: launch_wt<Real, RULE, SOLV_BIN>(a, cfg, s); break;
+        case SOLV_COLLIDE: launch_wt<Real, RULE, SOLV_COLLIDE>(a, cfg, s); break;
+        case SOLV_STREAM | SOLV_BIN: launch_wt<Real, RULE, SOLV_STREAM | SOLV_BIN>(a, cfg, s); break;
+        case SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN:
+            launch_wt<Real, RULE, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN>(a, cfg, s);
+            break;
+        default: break;
+        }
+        return;
+    }
     if (cfg.staged == 2) {
         switch (flags) {
         case SOLV_STREAM: launch_ws<Real, RULE, SOLV_STREAM>(a, cfg, s); break;

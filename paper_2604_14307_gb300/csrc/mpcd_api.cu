@@ -301,24 +301,27 @@ double solvent_bytes(const mpcd_ctx *c, int flags)
 // ----------------------------------------------------------- step pieces
 // dynamic shared memory of the staged (two-stage ring) or warp-specialised
 // (three-stage ring) solvent pass
-size_t ring_bytes(const mpcd_ctx *c, int mode, int tile)
+size_t ring_bytes(const mpcd_ctx *c, int mode, int tile, int block)
 {
     const size_t stage = solvent_stage_bytes(c->prm.precision, c->prm.rule, tile);
+    if (mode == 3) return (size_t)(block / 32) * 3 * stage;   // one three-stage ring per warp
     return (mode == 2 ? 3 : 2) * stage;
 }
 
-bool staged_fits(const mpcd_ctx *c, int tile, int mode)
+bool staged_fits(const mpcd_ctx *c, int tile, int mode, int block)
 {
-    return ring_bytes(c, mode, tile) <= 200 * 1024;
+    if (mode == 3 && (block > 512 || block % 32)) return false;
+    return ring_bytes(c, mode, tile, block) <= (mode == 3 ? 220 : 200) * 1024;
 }
 
 LaunchCfg solvent_cfg(const mpcd_ctx *c)
 {
-    const int mode = c->tune.staged && staged_fits(c, c->tune.tile, c->tune.staged) ? c->tune.staged : 0;
+    const int mode =
+        c->tune.staged && staged_fits(c, c->tune.tile, c->tune.staged, c->tune.block) ? c->tune.staged : 0;
     LaunchCfg cfg{c->tune.block, 1, mode, c->tune.tile};
     int per_sm = c->tune.ctas_per_sm;
     if (mode) {
-        size_t bytes = ring_bytes(c, mode, c->tune.tile) + 1024;
+        size_t bytes = ring_bytes(c, mode, c->tune.tile, c->tune.block) + 4096;
         per_sm = std::max(1, std::min<int>(per_sm, (int)(c->smem_per_sm / bytes)));
     }
     const int threads = c->tune.block + (mode == 2 ? 32 : 0);
@@ -1093,7 +1096,7 @@ int mpcd_set_tuning(mpcd_ctx *c, const mpcd_tuning *t)
     }
     if (t->ctas_per_sm > 0) c->tune.ctas_per_sm = std::min(t->ctas_per_sm, 32);
     if (t->sort_period > 0) c->tune.sort_period = t->sort_period;
-    if (t->staged >= 0) c->tune.staged = std::min(t->staged, 2);
+    if (t->staged >= 0) c->tune.staged = std::min(t->staged, 3);
     CK(c, cudaSetDevice(c->device));
     build_tiles(c);
     int e = upload_tiles(c);
@@ -1140,11 +1143,15 @@ int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
     for (int bl : {128, 256, 512})
         for (int tl : {1024, 2048, 4096})
             for (int ct : {1, 2, 4})
-                if (staged_fits(c, tl, 1)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 1});
+                if (staged_fits(c, tl, 1, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 1});
     for (int bl : {256, 512})
         for (int tl : {1024, 2048})
             for (int ct : {1, 2})
-                if (staged_fits(c, tl, 2)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 2});
+                if (staged_fits(c, tl, 2, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 2});
+    for (int bl : {256, 384, 512})
+        for (int tl : {128, 256})
+            for (int ct : {1, 2, 3})
+                if (staged_fits(c, tl, 3, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 3});
     for (int bl : {256, 512})
         for (int ct : {2, 4})
             cand.push_back(mpcd_tuning{bl, 8192, ct, c->tune.sort_period, 0});
