@@ -1018,12 +1018,12 @@ static void launch_wt(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 template <typename Real, int RULE, int FLAGS>
 static void launch_ws(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
-    static bool configured = false;
+    static size_t configured = 0;   // dynamic shared memory the kernel is opted in for
     const size_t bytes = (size_t)WS_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
-    if (!configured) {
+    if (bytes > configured) {
         cudaFuncSetAttribute(k_solvent_ws<Real, RULE, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        configured = true;
+                             (int)bytes);
+        configured = bytes;
     }
     k_solvent_ws<Real, RULE, FLAGS><<<cfg.grid, cfg.block + 32, bytes, s>>>(a, cfg.cap);
 }

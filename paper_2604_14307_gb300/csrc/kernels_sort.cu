@@ -242,20 +242,33 @@ __global__ void k_gather_in(StepArgs a, const Real *rec, const uint32_t *vals, i
 {
     Real *X[3] = {(Real *)a.x, (Real *)a.y, (Real *)a.z};
     Real *V[3] = {(Real *)a.vx, (Real *)a.vy, (Real *)a.vz};
+    // four records in flight per thread: all loads are issued before any store
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += stride) {
-        const uint32_t row = vals[i];
-        if (row == NO_VAL) {
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nslots; i0 += 4 * stride) {
+        Real r[4][6];
+        uint32_t row[4];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) { X[k][i] = Real(0); V[k][i] = Real(0); }
-            a.tag[i] = PAD_TAG;
-        } else if ((int64_t)row >= n_rows) {
-            bad_index(a.d_err, 3);
-        } else {
-            Real r[6];
-            rec_load(rec + 8 * (int64_t)row, r);
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * stride;
+            row[u] = i < nslots ? vals[i] : NO_VAL;
+            if (row[u] != NO_VAL && (int64_t)row[u] >= n_rows) {
+                bad_index(a.d_err, 3);
+                row[u] = NO_VAL - 1;   // skip: neither a record nor padding
+            }
+            if ((int64_t)row[u] < n_rows) rec_load(rec + 8 * (int64_t)row[u], r[u]);
+        }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) { X[k][i] = r[k]; V[k][i] = r[3 + k]; }
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= nslots || row[u] == NO_VAL - 1) continue;
+            if (row[u] == NO_VAL) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { X[k][i] = Real(0); V[k][i] = Real(0); }
+                a.tag[i] = PAD_TAG;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { X[k][i] = r[u][k]; V[k][i] = r[u][3 + k]; }
+            }
         }
     }
 }
@@ -307,14 +320,26 @@ template <typename Real>
 __global__ void k_gather_out(const uint32_t *vals, const Real *rec, Real *xa, Real *va, int64_t n_rows,
                              int64_t nslots, int *err)
 {
+    // four records in flight per thread: all loads are issued before any store
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows; i += stride) {
-        const int64_t p = vals[i];
-        if (p >= nslots) { bad_index(err, 5); continue; }
-        Real r[6];
-        rec_load(rec + 8 * p, r);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n_rows; i0 += 4 * stride) {
+        Real r[4][6];
+        bool ok[4];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { xa[3 * i + k] = r[k]; va[3 * i + k] = r[3 + k]; }
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * stride;
+            const int64_t p = i < n_rows ? (int64_t)vals[i] : -1;
+            ok[u] = p >= 0 && p < nslots;
+            if (p >= nslots) bad_index(err, 5);
+            if (ok[u]) rec_load(rec + 8 * p, r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (!ok[u]) continue;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { xa[3 * i + k] = r[u][k]; va[3 * i + k] = r[u][3 + k]; }
+        }
     }
 }
 

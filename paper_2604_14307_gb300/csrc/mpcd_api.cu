@@ -58,6 +58,10 @@ struct mpcd_ctx {
     DevReplica *d_reps = nullptr;
     Tile *d_tiles = nullptr, *d_ctiles = nullptr;
     int64_t tiles_cap = 0;
+    // fixed 2048-particle tiles of the helper passes (sort, state I/O,
+    // diagnostics), whatever tile size the solvent pass is tuned to
+    std::vector<Tile> io_tiles;
+    Tile *d_io_tiles = nullptr;
     DevShape *d_shapes = nullptr;
     DevBody *d_bodies = nullptr;
     float4 *d_bpos = nullptr, *d_bpos_build = nullptr;
@@ -95,6 +99,8 @@ struct mpcd_ctx {
 
     std::map<std::tuple<int64_t, int, int64_t>, GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t io_stream = nullptr;           // host copies that overlap with kernels
+    cudaEvent_t io_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -209,6 +215,16 @@ StepArgs make_args(const mpcd_ctx *c)
     return a;
 }
 
+// arguments of the helper passes: the same as make_args but over the fixed
+// 2048-particle tiles
+StepArgs make_io_args(const mpcd_ctx *c)
+{
+    StepArgs a = make_args(c);
+    a.tiles = c->d_io_tiles;
+    a.n_tiles = (int32_t)c->io_tiles.size();
+    return a;
+}
+
 void build_tiles(mpcd_ctx *c)
 {
     c->tiles.clear();
@@ -311,7 +327,8 @@ size_t ring_bytes(const mpcd_ctx *c, int mode, int tile, int block)
 bool staged_fits(const mpcd_ctx *c, int tile, int mode, int block)
 {
     if (mode == 3 && (block > 512 || block % 32)) return false;
-    return ring_bytes(c, mode, tile, block) <= (mode == 3 ? 220 : 200) * 1024;
+    const size_t lim = (mode == 3 ? 220 : 200) * 1024;
+    return ring_bytes(c, mode, tile, block) <= lim;
 }
 
 LaunchCfg solvent_cfg(const mpcd_ctx *c)
@@ -396,7 +413,7 @@ int k_advance(mpcd_ctx *c, cudaStream_t s)
 int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
 {
     if (c->Ns == 0) return MPCD_OK;
-    StepArgs a = make_args(c);
+    StepArgs a = make_io_args(c);
     const int nxt = c->cur ^ 1;
     double bytes = (double)c->Ns * (2.0 * (6.0 * c->realsz + 4.0) + 3.0 * c->realsz);
     int e = timed(c, "sort", bytes, s, [&] {
@@ -719,6 +736,20 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     if (cudaMemset(c->d_bpos_build, 0, std::max<int64_t>(1, c->B) * sizeof(float4)) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_nl_dirty, 0xFF, sizeof(int)) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_err, 0, 8) != cudaSuccess) st = MPCD_ERR_CUDA;
+    // default launch form: a ring per warp of 128-particle tiles, else the
+    // warp-specialised pass with the largest tile whose ring fits in shared
+    // memory (the FP64 form), else direct loads
+    if (staged_fits(c, 128, 3, 512)) {
+        c->tune = mpcd_tuning{512, 128, 1, c->tune.sort_period, 3};
+    } else {
+        c->tune = mpcd_tuning{512, 2048, 1, c->tune.sort_period, 0};
+        for (int t : {2048, 1536, 1024, 512})
+            if (staged_fits(c, t, 2, 512)) {
+                c->tune.tile = t;
+                c->tune.staged = 2;
+                break;
+            }
+    }
     build_tiles(c);
     build_ctiles(c);
     if (!st) st = upload_tiles(c);
@@ -727,7 +758,20 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
         if (!c->d_ctiles) st = MPCD_ERR_OOM;
         else H2D(c->d_ctiles, c->ctiles.data(), c->ctiles.size() * sizeof(Tile));
     }
+    if (!st) {
+        for (int r = 0; r < c->nrep; ++r) {
+            const DevReplica &R = c->reps[r];
+            for (int64_t b = R.solv_begin; b < R.solv_begin + R.n_solvent; b += 2048)
+                c->io_tiles.push_back(Tile{r, 0, b, std::min<int64_t>(b + 2048, R.solv_begin + R.n_solvent)});
+        }
+        c->d_io_tiles = (Tile *)dalloc(c, std::max<size_t>(1, c->io_tiles.size()) * sizeof(Tile));
+        if (!c->d_io_tiles) st = MPCD_ERR_OOM;
+        else H2D(c->d_io_tiles, c->io_tiles.data(), c->io_tiles.size() * sizeof(Tile));
+    }
     if (!st && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (!st && cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
+    for (int k = 0; k < 2 && !st; ++k)
+        if (cudaEventCreateWithFlags(&c->io_ev[k], cudaEventDisableTiming) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (st) {
         cudaGetLastError();
         mpcd_destroy(c);
@@ -749,6 +793,9 @@ int mpcd_destroy(mpcd_ctx *c)
     }
     for (auto e : c->evpool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->io_stream) cudaStreamDestroy(c->io_stream);
+    for (auto e : c->io_ev)
+        if (e) cudaEventDestroy(e);
     for (void *p : c->allocations) {
         if (c->use_alloc) c->alloc.free(p, c->alloc.user);
         else cudaFree(p);
@@ -804,24 +851,32 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
     const size_t n3 = (size_t)c->Ns * 3;
     clear_graphs(c);
     char *stg = (char *)c->staging;
-    if (c->Ns) {
-        CK(c, cudaMemcpyAsync(stg, h->x, n3 * c->realsz, cudaMemcpyHostToDevice, s));
-        CK(c, cudaMemcpyAsync(stg + n3 * c->realsz, h->v, n3 * c->realsz, cudaMemcpyHostToDevice, s));
-    }
     c->cur = 0;
     StepArgs a = make_args(c);
+    const StepArgs aio = make_io_args(c);
     {
         // cell-sorted storage from the tag-ordered rows: stable radix sort of
         // (cell, row) pairs in the spare buffer, then one gather (memory
-        // locality only; results do not depend on the order)
+        // locality only; results do not depend on the order).  The velocities
+        // travel on the copy stream while the positions are keyed and sorted.
         uint32_t *kA = (uint32_t *)c->sol[1][0], *vA = (uint32_t *)c->sol[1][1];
         uint32_t *kB = (uint32_t *)c->sol[1][2], *vB = (uint32_t *)c->sol[1][3];
-        launch_keys_in(a, stg, kA, vA, c->Nslots, s);
-        launch_pack_rows(a, stg, stg + n3 * c->realsz, c->rec, c->Ns, c->num_sms, s);
+        if (c->Ns) {
+            // positions first at full link bandwidth, then the velocities
+            // while the positions are keyed and sorted
+            CK(c, cudaMemcpyAsync(stg, h->x, n3 * c->realsz, cudaMemcpyHostToDevice, s));
+            CK(c, cudaEventRecord(c->io_ev[0], s));
+            CK(c, cudaStreamWaitEvent(c->io_stream, c->io_ev[0], 0));
+            CK(c, cudaMemcpyAsync(stg + n3 * c->realsz, h->v, n3 * c->realsz, cudaMemcpyHostToDevice, c->io_stream));
+            CK(c, cudaEventRecord(c->io_ev[1], c->io_stream));
+        }
+        launch_keys_in(aio, stg, kA, vA, c->Nslots, s);
         const int nb = key_bits((uint64_t)std::max<int64_t>(c->C - 1, 0));
         const int inB =
             launch_radix_sort(kA, vA, kB, vB, c->Nslots, nb, c->rs_hist, c->rs_ex, c->rs_bs, c->d_err, s);
-        launch_gather_in(a, c->rec, inB ? vB : vA, c->Nslots, c->Ns, c->num_sms, s);
+        if (c->Ns) CK(c, cudaStreamWaitEvent(s, c->io_ev[1], 0));
+        launch_pack_rows(aio, stg, stg + n3 * c->realsz, c->rec, c->Ns, c->num_sms, s);
+        launch_gather_in(aio, c->rec, inB ? vB : vA, c->Nslots, c->Ns, c->num_sms, s);
     }
     if (c->B) CK(c, cudaMemcpyAsync(c->d_bodies, hb.data(), c->B * sizeof(DevBody), cudaMemcpyHostToDevice, s));
     CK(c, cudaMemsetAsync(c->sums, 0, (size_t)c->C * c->nw * 8, s));
@@ -856,7 +911,7 @@ int mpcd_get_state(mpcd_ctx *c, mpcd_host_state *h, void *stream)
     CK(c, cudaSetDevice(c->device));
     const size_t n3 = (size_t)c->Ns * 3;
     char *stg = (char *)c->staging;
-    StepArgs a = make_args(c);
+    const StepArgs a = make_io_args(c);
     {
         // tag order from the cell-sorted storage: stable radix sort of
         // (host row, slot) pairs in the spare buffer, then a gather whose
@@ -984,7 +1039,7 @@ int mpcd_diagnostics(mpcd_ctx *c, mpcd_diag *o, void *stream)
     CK(c, cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
     CK(c, cudaMemsetAsync(c->d_diag, 0, 16 * 8, s));
-    StepArgs a = make_args(c);
+    StepArgs a = make_io_args(c);
     launch_solvent_diag(a, c->d_diag, s);
     launch_body_diag(a, c->d_diag, s);
     CK(c, cudaGetLastError());
