@@ -41,8 +41,8 @@ FALLBACK_HBM_GBS = 6800.0
 def args_():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-p64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -72,7 +72,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -266,18 +266,24 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.set_state_buffers(hb, step0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     sim.step(a.steps)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
     sim.get_state_buffers(hb)
     diag = sim.diagnostics()
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
+    e2e_parts = {"set_state_ms": (t1 - t0) * 1e3, "steps_ms": (t2 - t1) * 1e3,
+                 "get_state_and_diagnostics_ms": (time.perf_counter() - t2) * 1e3}
     te_t = torch.tensor([te], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
     e2e = {"value": n_upd * a.steps * ws / float(te_t.item()), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes / a.steps, "d2h_bytes_per_step": (state_bytes + 80) / a.steps,
            "how": "mpcd_set_state from pinned host + mpcd_step(steps) + mpcd_get_state to pinned host "
-                  "+ mpcd_diagnostics, wall clock"}
+                  "+ mpcd_diagnostics, wall clock", "parts": e2e_parts}
     sim.close()
     del hb
 

@@ -76,6 +76,9 @@ def lib():
             _lib.orc_cell_axis.argtypes = [C.c_double, C.c_int32, C.c_int32]
             _lib.orc_cell_axis.restype = C.c_int32
             _lib.orc_grid_shift.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p]
+            _lib.orc_srd_axis.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_uint32, C.c_void_p]
+            _lib.orc_thermostat_energy.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_uint32, C.c_int64]
+            _lib.orc_thermostat_energy.restype = C.c_double
             for fn in ("orc_forces",):
                 getattr(_lib, fn).argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
             for fn in ("orc_stream",):
@@ -240,6 +243,18 @@ def philox(ctr, key) -> np.ndarray:
     o = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
     return o
+
+
+def srd_axis(osys: OracleSystem, rep: int, step_: int, cell: int) -> np.ndarray:
+    """SRD rotation axis of replica-local cell `cell` at collision `step_`."""
+    out = np.zeros(3)
+    lib().orc_srd_axis(C.byref(osys.c), int(rep), int(step_), int(cell), _ptr(out))
+    return out
+
+
+def thermostat_energy(osys: OracleSystem, rep: int, step_: int, cell: int, n: int) -> float:
+    """E' of the cell-level thermostat for a cell of n particles (Eq. 6)."""
+    return float(lib().orc_thermostat_energy(C.byref(osys.c), int(rep), int(step_), int(cell), int(n)))
 
 
 def grid_shift(osys: OracleSystem, rep: int, step_: int) -> np.ndarray:

@@ -516,6 +516,23 @@ static double thermostat_energy(const orc_sys *s, int rep, int64_t step, uint32_
 
 static float f32(double x) { return (float)x; }
 
+/* SRD rotation axis of replica-local cell `cell` at collision `step`: uniform
+ * on the sphere, z = 2u1 - 1, phi = 2 pi u2 (Sec. II.A) */
+void orc_srd_axis(const orc_sys *s, int rep, int64_t step, uint32_t cell, double axis[3])
+{
+    uint32_t w[4];
+    draw(s, rep, step, cell, TAG_AXIS, 0u, w);
+    double z = 2.0 * u01(w[0]) - 1.0, ph = 6.283185307179586476925286766559 * u01(w[1]);
+    double rho = sqrt(1.0 - z * z);
+    axis[0] = rho * cos(ph); axis[1] = rho * sin(ph); axis[2] = z;
+}
+
+/* E' of the cell-level thermostat for a cell of Nc particles (Eq. 6) */
+double orc_thermostat_energy(const orc_sys *s, int rep, int64_t step, uint32_t cell, int64_t Nc)
+{
+    return thermostat_energy(s, rep, step, cell, Nc);
+}
+
 int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
 {
     const int p32 = (s->precision == ORC_P32);
@@ -677,11 +694,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
             double axis[3] = { 0, 0, 0 }, kappa = 1.0, xib[3] = { 0, 0, 0 };
             int collide = (n >= 2);
             if (s->rule == ORC_SRD && collide) {
-                uint32_t w[4];
-                draw(s, r, st->step, lc, TAG_AXIS, 0u, w);
-                double z = 2.0 * u01(w[0]) - 1.0, ph = 6.283185307179586476925286766559 * u01(w[1]);
-                double rho = sqrt(1.0 - z * z);
-                axis[0] = rho * cos(ph); axis[1] = rho * sin(ph); axis[2] = z;
+                orc_srd_axis(s, r, st->step, lc, axis);
                 if (s->thermostat && p32) {
                     /* P32 form: the kinetic energy entering the thermostat is the
                      * one its fixed-point sums carry, i.e. of the stored float

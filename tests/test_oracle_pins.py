@@ -536,3 +536,26 @@ def test_templates_are_principal_and_centred(maker):
                                  - sh.b[:, :, None] * sh.b[:, None, :])).sum(0)
     off = Ib - np.diag(np.diag(Ib))
     assert np.abs(off).max() < 1e-9 * np.abs(Ib).max()
+
+
+def test_exported_axis_and_thermostat_match_the_collision():
+    """orc_srd_axis / orc_thermostat_energy are the pieces orc_collide uses:
+    the axis it traces, and the kappa = sqrt(E'/E_rel) it traces with E_rel from
+    the P32 fixed-point words (Sec. II.A, Eq. 6)."""
+    s = I.suspension(16, 5.0, 0.15, 2.0, 2, 5.0, I.SRD, 1, I.P32, seed=3, name="small")
+    osys = O.OracleSystem(s)
+    ost = O.OracleState(osys, I.initial_state(s))
+    O.stream(osys, ost)
+    tr = O.collide(osys, ost)
+    n = tr["sums"][0]
+    M = tr["sums"][1]
+    sel = np.where(n >= 2)[0][:300]
+    for c in sel:
+        assert np.array_equal(O.srd_axis(osys, 0, 0, int(c)), tr["cell_axis"][c])
+        fx = tr["fixed"][:, c]
+        lo0 = (int(fx[0]) + 2**31) % 2**32 - 2**31
+        lo1 = (int(fx[1]) + 2**31) % 2**32 - 2**31
+        S1 = np.array([(int(fx[0]) - lo0) >> 32, lo0, (int(fx[1]) - lo1) >> 32], dtype=np.float64) * 2.0**-20
+        erel = 0.5 * (float(fx[2]) * 2.0**-28 - float(S1 @ S1) / M[c])
+        kappa = np.sqrt(O.thermostat_energy(osys, 0, 0, int(c), int(n[c])) / erel)
+        assert abs(kappa - tr["cell_kappa"][c]) <= 1e-12 * kappa
