@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(SITE_THREADS) k_sites_pre(StepArgs a)
     const int64_t site_begin = B.site_begin;
     const DevShape sh = a.shapes[shape];
     const DevReplica r = a.reps[rep];
-    const int64_t step = *a.d_step;
+    const int64_t step = *a.d_step + a.step_offset;
     if (threadIdx.x < POSE_W) sPose[threadIdx.x] = pose_ptr(a, blockIdx.x, Real(0))[threadIdx.x];
     if (threadIdx.x == 0) grid_shift(r, step, sS);
     __syncthreads();

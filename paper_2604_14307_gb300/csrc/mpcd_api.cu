@@ -101,6 +101,8 @@ struct mpcd_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t io_stream = nullptr;           // host copies that overlap with kernels
     cudaEvent_t io_ev[2] = {nullptr, nullptr};
+    cudaStream_t side = nullptr;                // site/body chain beside the solvent pass
+    cudaEvent_t side_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -366,9 +368,10 @@ int k_bodies(mpcd_ctx *c, cudaStream_t s)
     return timed(c, "body_force", 0, s, [&] { launch_body_force(a, 1, s); });
 }
 
-int k_pre(mpcd_ctx *c, cudaStream_t s)
+int k_pre(mpcd_ctx *c, cudaStream_t s, int step_offset = 0)
 {
     StepArgs a = make_args(c);
+    a.step_offset = step_offset;
     double bytes = (double)c->Nsite * (3.0 * c->realsz + 4.0);
     return timed(c, "sites_pre", bytes, s, [&] { launch_sites_pre(a, c->max_sites, s); });
 }
@@ -434,20 +437,35 @@ int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
 }
 
 // whole steps, software-pipelined: the solvent pass of step k collides (k),
-// streams and bins for step k+1
+// streams and bins for step k+1; beside it, on a second stream, run the site
+// POST coupling of step k and the body step and site PRE coupling of step k+1
+// (they need step k's cell parameters and impulse, not its solvent pass; both
+// branches add to the cleared cell sums of step k+1 with integer atomics, so
+// the order between them changes no result).  The branches join before the
+// cell parameters of step k+1.
 int run_steps(mpcd_ctx *c, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return MPCD_OK;
     int e = k_solvent(c, SOLV_STREAM | SOLV_BIN, s);
+    if (!e) e = k_bodies(c, s);
+    if (!e) e = k_pre(c, s);
     for (int64_t k = 0; k < n && !e; ++k) {
-        if ((e = k_bodies(c, s))) break;
-        if ((e = k_pre(c, s))) break;
         if ((e = k_params(c, s))) break;
-        if ((e = k_post(c, s))) break;
-        const bool last = (k == n - 1);
-        if ((e = k_solvent(c, last ? SOLV_COLLIDE : (SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN), s))) break;
-        if (!last && c->prm.sort_period >= 0 && ++c->since_sort >= c->tune.sort_period)
-            if ((e = do_sort(c, 0, s))) break;
+        if (k == n - 1) {
+            if ((e = k_post(c, s))) break;
+            if ((e = k_solvent(c, SOLV_COLLIDE, s))) break;
+        } else {
+            CK(c, cudaEventRecord(c->side_ev[0], s));
+            CK(c, cudaStreamWaitEvent(c->side, c->side_ev[0], 0));
+            if ((e = k_post(c, c->side))) break;
+            if ((e = k_bodies(c, c->side))) break;
+            if ((e = k_pre(c, c->side, 1))) break;   // step k+1, before the counter advances
+            CK(c, cudaEventRecord(c->side_ev[1], c->side));
+            if ((e = k_solvent(c, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN, s))) break;
+            CK(c, cudaStreamWaitEvent(s, c->side_ev[1], 0));
+            if (c->prm.sort_period >= 0 && ++c->since_sort >= c->tune.sort_period)
+                if ((e = do_sort(c, 0, s))) break;
+        }
         if ((e = k_advance(c, s))) break;
     }
     if (!e && !c->profiling) {
@@ -770,8 +788,12 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     }
     if (!st && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (!st && cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
-    for (int k = 0; k < 2 && !st; ++k)
+    if (!st && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
+    for (int k = 0; k < 2 && !st; ++k) {
         if (cudaEventCreateWithFlags(&c->io_ev[k], cudaEventDisableTiming) != cudaSuccess) st = MPCD_ERR_CUDA;
+        if (!st && cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming) != cudaSuccess)
+            st = MPCD_ERR_CUDA;
+    }
     if (st) {
         cudaGetLastError();
         mpcd_destroy(c);
@@ -794,7 +816,10 @@ int mpcd_destroy(mpcd_ctx *c)
     for (auto e : c->evpool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->io_stream) cudaStreamDestroy(c->io_stream);
+    if (c->side) cudaStreamDestroy(c->side);
     for (auto e : c->io_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto e : c->side_ev)
         if (e) cudaEventDestroy(e);
     for (void *p : c->allocations) {
         if (c->use_alloc) c->alloc.free(p, c->alloc.user);

@@ -114,6 +114,8 @@ struct StepArgs {
     int32_t *site_cell;             // replica-local cell of each site
     int64_t n_sites;
     const int64_t *d_step;          // completed steps (device)
+    int32_t step_offset;            // added to *d_step by the site PRE pass (1 when it runs
+                                    // for the next step before the counter advances)
     int *d_err;
 };
 
