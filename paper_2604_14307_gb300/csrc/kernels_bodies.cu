@@ -458,8 +458,12 @@ template <> __device__ __forceinline__ void load_cell<double>(const StepArgs &a,
 // PRE coupling: site poses, thermal draws, Eq. 7, binning of the sites.
 // Arithmetic in the form's precision only (the pose record carries the FP64
 // body quantities already reduced to it).
+// FP32 site kernels are held to 64 registers (8 CTAs of 128 threads per SM)
+// so that they fit beside the solvent pass they overlap with.
+template <typename Real> struct SiteMinBlocks { static constexpr int n = sizeof(Real) == 4 ? 8 : 1; };
+
 template <typename Real>
-__global__ void __launch_bounds__(SITE_THREADS) k_sites_pre(StepArgs a)
+__global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_pre(StepArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     Real *vt = reinterpret_cast<Real *>(smem_raw);          // [n_sites][3] thermal draws
@@ -570,7 +574,7 @@ __global__ void __launch_bounds__(SITE_THREADS) k_sites_pre(StepArgs a)
 // momentum dP = sum m (v' - v) and angular momentum dL = sum d x m (v' - v)
 // transferred to the body (Eqs. 3-4); k_body_impulse adds them in FP64.
 template <typename Real>
-__global__ void __launch_bounds__(SITE_THREADS) k_sites_post(StepArgs a)
+__global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_post(StepArgs a)
 {
     __shared__ Real sPose[POSE_W];
     const DevBody &B = a.bodies[blockIdx.x];

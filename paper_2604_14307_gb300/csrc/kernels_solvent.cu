@@ -815,8 +815,17 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
 // replica a warp meets.  Every wait is bounded.
 constexpr int WT_STAGES = 3, WT_MAX_WARPS = 16;
 
+// Register cap of the FP32 SRD form (80, at most 512 threads): 512 x 80
+// registers leave 24 K of the SM's 64 K registers to the site/body kernels
+// that run beside this pass on the second stream (a cap of 96 left room for
+// one of their CTAs per SM, none without a cap; 72 and below spill in the
+// loop).  The AT form, with its Philox normals, keeps 96.
+template <typename Real, int RULE> struct WtRegs {
+    static constexpr int n = sizeof(Real) == 4 ? (RULE == 0 ? 80 : 96) : 128;
+};
+
 template <typename Real, int RULE, int FLAGS>
-__global__ void __launch_bounds__(512) k_solvent_wt(StepArgs a, int cap)
+__global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, int cap)
 {
     constexpr bool COLLIDE = FLAGS & SOLV_COLLIDE;
     constexpr bool STREAM = FLAGS & SOLV_STREAM;
