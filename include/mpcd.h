@@ -228,6 +228,55 @@ int mpcd_set_profiling(mpcd_ctx *ctx, int32_t on);
 int mpcd_get_profile(mpcd_ctx *ctx, mpcd_kernel_time *out, int32_t max);
 int mpcd_reset_profile(mpcd_ctx *ctx);
 
+/* Reverse non-equilibrium momentum exchange (Mueller-Plathe), the shear-
+ * viscosity protocol of Sec. III.B (Eq. 14).  While enabled, before the
+ * collision of every step n with n % period == 0 (after the solvent has
+ * streamed to the positions of that collision), the solvent particles of slab A
+ * (y in [y_a, y_a + width)) are ranked by |v_x - v_target| and those of slab B
+ * (y in [y_b, y_b + width)) by |v_x + v_target|, ascending, ties by particle id;
+ * the first min(max_pairs, n_A, n_B) of each list are paired in rank order and
+ * exchange v_x.  Slab membership and ranks are decided on the stored values in
+ * the context's precision (float for P32: y >= (float)y_a && y < (float)(y_a +
+ * width), key fabsf(v_x -+ (float)v_target)).  Each pair moves m (v_A - v_B) of
+ * x momentum from slab A to slab B; the totals accumulate on the device.
+ * Only contexts with one replica (else MPCD_ERR_ARG).  At most
+ * MPCD_RNEMD_MAX_PAIRS pairs.  The candidates of a slab are the particles whose
+ * rank key lies at or below the 1/8-octave bucket that holds the max_pairs-th
+ * smallest key; if more than MPCD_RNEMD_MAX_CANDIDATES of them exist, that
+ * exchange is skipped and the next synchronising call (e.g. mpcd_rnemd_totals)
+ * returns MPCD_ERR_STATE.  enabled = 0 turns the exchange off.  Setting a
+ * configuration clears the totals and synchronises the device.  The exchange
+ * conserves momentum and kinetic energy exactly.  In mpcd_step the exchange
+ * runs after the solvent pass that streamed and binned for the collision, and
+ * the exchanged particles' cell words are corrected exactly; mpcd_collide runs
+ * it before binning. */
+#define MPCD_RNEMD_MAX_PAIRS 1024
+#define MPCD_RNEMD_MAX_CANDIDATES 4096
+typedef struct {
+    int32_t enabled;
+    int32_t max_pairs;     /* 0 .. MPCD_RNEMD_MAX_PAIRS */
+    int32_t period;        /* >= 1 steps */
+    int32_t reserved;      /* must be 0 */
+    double y_a, y_b;       /* lower edges of slabs A and B, in [0, L_y) */
+    double width;          /* slab width (> 0; the slabs must not overlap) */
+    double v_target;       /* >= 0 */
+} mpcd_rnemd;
+int mpcd_set_rnemd(mpcd_ctx *ctx, const mpcd_rnemd *cfg);
+
+/* Totals since the last mpcd_set_rnemd: x momentum moved from slab A to slab B
+ * (sum of m (v_A - v_B), FP64) and the number of exchanged pairs.  Synchronises
+ * the stream. */
+int mpcd_rnemd_totals(mpcd_ctx *ctx, double *p_exchanged, int64_t *n_pairs, void *stream);
+
+/* Velocity profile (Sec. III.B): the solvent of replica 0 binned by the
+ * coordinate `bin_axis` into n_bins equal bins over [0, L), and each bin's mass
+ * and momentum along `vel_axis` summed in FP64; the bodies add M and P at their
+ * centre of mass.  mass and momentum are host arrays of n_bins doubles.
+ * Synchronises the stream. */
+#define MPCD_PROFILE_MAX_BINS 2048
+int mpcd_velocity_profile(mpcd_ctx *ctx, int32_t bin_axis, int32_t vel_axis, int32_t n_bins, double *mass,
+                          double *momentum, void *stream);
+
 /* Launch configuration of the solvent pass and the re-sort period.  The
  * autotuner times candidate configurations on the current state (which it
  * restores afterwards) and keeps the fastest; set_tuning fixes one directly.

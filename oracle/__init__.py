@@ -292,3 +292,64 @@ def normals(osys: OracleSystem, rep: int, step_: int, ids, tag: int) -> np.ndarr
 
 
 TAG_SHIFT, TAG_AXIS, TAG_THERMO, TAG_THERMO_ODD, TAG_SITE, TAG_AT = 1, 2, 3, 4, 5, 6
+
+
+# --------------------------------------------------------------------------
+# Transport protocols of Sec. III.B (shear viscosity, Eq. 14)
+# --------------------------------------------------------------------------
+def rnemd_exchange(osys: OracleSystem, st: OracleState, y_a: float, y_b: float, width: float,
+                   v_target: float, max_pairs: int, rep: int = 0):
+    """Reverse non-equilibrium (Mueller-Plathe) momentum exchange, Sec. III.B.
+
+    The solvent particles of slab A, y in [y_a, y_a + width), are ranked by how
+    close their v_x is to +v_target, those of slab B, y in [y_b, y_b + width), by
+    how close it is to -v_target (ascending |v_x -+ v_target|, equal distances by
+    particle id); the first min(max_pairs, n_A, n_B) of each ranking are paired in
+    rank order and every pair exchanges v_x.  In the P32 form the slab test and
+    the distances are evaluated on the stored float32 values in float32, the
+    precision in which that form takes these decisions.  Returns (x momentum
+    moved from A to B = sum of m (v_A - v_B), number of pairs).  Modifies st.v.
+    """
+    so = osys.solv_off
+    i0, i1 = int(so[rep]), int(so[rep + 1])
+    y = st.x[i0:i1, 1]
+    vx = st.v[i0:i1, 0]
+    if osys.params["precision"] == P32:
+        f = np.float32
+        y, vxk = y.astype(f), vx.astype(f)
+        a0, a1, b0, b1 = f(y_a), f(y_a + width), f(y_b), f(y_b + width)
+        key_a, key_b = np.abs(vxk - f(v_target)), np.abs(vxk + f(v_target))
+    else:
+        a0, a1, b0, b1 = y_a, y_a + width, y_b, y_b + width
+        key_a, key_b = np.abs(vx - v_target), np.abs(vx + v_target)
+    ids = np.arange(i1 - i0)
+    in_a = (y >= a0) & (y < a1)
+    in_b = (y >= b0) & (y < b1)
+    rank_a = ids[in_a][np.lexsort((ids[in_a], key_a[in_a]))]
+    rank_b = ids[in_b][np.lexsort((ids[in_b], key_b[in_b]))]
+    n = min(int(max_pairs), len(rank_a), len(rank_b))
+    pa, pb = rank_a[:n], rank_b[:n]
+    va, vb = vx[pa].copy(), vx[pb].copy()
+    st.v[i0 + pa, 0] = vb
+    st.v[i0 + pb, 0] = va
+    m = osys.params["m_solvent"]
+    if osys.params["precision"] == P32:
+        m = float(np.float32(m))
+    return float(np.sum(m * (va - vb))), n
+
+
+def step_rnemd(osys: OracleSystem, st: OracleState, n: int, y_a: float, y_b: float, width: float,
+               v_target: float, max_pairs: int, period: int = 1):
+    """n whole steps with the exchange before the collision of every step whose
+    index is a multiple of `period` (after streaming, the order of the stream,
+    collide sequence of Sec. II).  Returns the summed (momentum, pairs)."""
+    dp, npairs = 0.0, 0
+    for _ in range(n):
+        stream(osys, st)
+        if st.step % period == 0:
+            d, k = rnemd_exchange(osys, st, y_a, y_b, width, v_target, max_pairs)
+            dp += d
+            npairs += k
+        collide(osys, st, trace=False)
+        st.step += 1
+    return dp, npairs

@@ -31,7 +31,8 @@ EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "m
            "mpcd_couple", "mpcd_collide", "mpcd_step", "mpcd_sort", "mpcd_diagnostics",
            "mpcd_sizes", "mpcd_last_error", "mpcd_set_debug", "mpcd_debug_cells",
            "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
-           "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static"]
+           "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static", "mpcd_set_rnemd",
+           "mpcd_rnemd_totals", "mpcd_velocity_profile"]
 
 
 class MPCDError(RuntimeError):
@@ -87,6 +88,12 @@ class KernelTime(C.Structure):
                 ("bytes_per_launch", C.c_double)]
 
 
+class Rnemd(C.Structure):
+    _fields_ = [("enabled", C.c_int32), ("max_pairs", C.c_int32), ("period", C.c_int32),
+                ("reserved", C.c_int32), ("y_a", C.c_double), ("y_b", C.c_double), ("width", C.c_double),
+                ("v_target", C.c_double)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("block", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("sort_period", C.c_int32), ("staged", C.c_int32)]
@@ -127,6 +134,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "mpcd_get_tuning": [vp, C.POINTER(Tuning)],
             "mpcd_set_tuning": [vp, C.POINTER(Tuning)],
             "mpcd_autotune": [vp, i32, vp],
+            "mpcd_set_rnemd": [vp, C.POINTER(Rnemd)],
+            "mpcd_rnemd_totals": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), vp],
+            "mpcd_velocity_profile": [vp, i32, i32, i32, vp, vp, vp],
             "mpcd_collide_solvent_static": [C.POINTER(Params), C.POINTER(C.c_int32 * 3), i64, vp, vp, vp,
                                             vp, vp, vp, vp, i64, vp, C.c_char_p, C.c_size_t],
         }
@@ -317,6 +327,29 @@ class Simulation:
         self._check(self.lib.mpcd_diagnostics(self.ctx, C.byref(d), self._s(stream)))
         return dict(p_solvent=np.array(d.p_solvent[:]), p_bodies=np.array(d.p_bodies[:]),
                     ke_solvent=d.ke_solvent, ke_trans=d.ke_trans, ke_rot=d.ke_rot, step=d.step)
+
+    # ------------------------------------------------- transport protocols
+    def set_rnemd(self, y_a: float, y_b: float, width: float = 1.0, v_target: float = 0.5,
+                  max_pairs: int = 100, period: int = 1, enabled: bool = True):
+        """Reverse non-equilibrium exchange of v_x between slabs [y_a, y_a + width)
+        and [y_b, y_b + width) (Sec. III.B); see mpcd_set_rnemd."""
+        cfg = Rnemd(int(enabled), int(max_pairs), int(period), 0, float(y_a), float(y_b), float(width),
+                    float(v_target))
+        self._check(self.lib.mpcd_set_rnemd(self.ctx, C.byref(cfg)))
+
+    def rnemd_totals(self, stream=None):
+        """(x momentum moved from slab A to slab B, number of exchanged pairs)."""
+        p, n = C.c_double(), C.c_int64()
+        self._check(self.lib.mpcd_rnemd_totals(self.ctx, C.byref(p), C.byref(n), self._s(stream)))
+        return p.value, n.value
+
+    def velocity_profile(self, n_bins: int, bin_axis: int = 1, vel_axis: int = 0, stream=None):
+        """(mass, momentum) per bin of coordinate `bin_axis` (solvent and bodies)."""
+        mass = np.zeros(n_bins)
+        mom = np.zeros(n_bins)
+        self._check(self.lib.mpcd_velocity_profile(self.ctx, int(bin_axis), int(vel_axis), int(n_bins),
+                                                   mass.ctypes.data, mom.ctypes.data, self._s(stream)))
+        return mass, mom
 
     # ------------------------------------------------------------------ debug
     def set_debug(self, on: bool = True):

@@ -1706,4 +1706,305 @@ void launch_sort_canonical(const StepArgs &a, void *const d[6], uint32_t *tag, c
                                                            ex);
 }
 
+
+// ------------------------------------------ RNEMD exchange (Sec. III.B)
+// Reverse non-equilibrium (Mueller-Plathe) exchange of v_x between the solvent
+// particles of slab A closest to +v_t and those of slab B closest to -v_t.
+// Three launches: a histogram of the rank keys per slab (1/8-octave buckets of
+// the non-negative key), a collection of the candidates up to the bucket that
+// holds the max_pairs-th smallest key, and one CTA that sorts the candidates
+// (key, then id) and exchanges the pairs.  When the solvent is already binned
+// for the coming collision, the exchanged particles' contributions to the cell
+// words are corrected exactly (the difference of their old and new terms).
+__device__ __forceinline__ int rn_bucket(float k) { return (int)(__float_as_uint(k) >> 20); }
+__device__ __forceinline__ unsigned long long rn_bits(float k) { return (unsigned long long)__float_as_uint(k); }
+__device__ __forceinline__ unsigned long long rn_bits(double k)
+{
+    return (unsigned long long)__double_as_longlong(k);
+}
+__device__ __forceinline__ int rn_slab(const RnemdArgs &g, float y)
+{
+    return (y >= g.ya0f && y < g.ya1f) ? 0 : (y >= g.yb0f && y < g.yb1f) ? 1 : -1;
+}
+__device__ __forceinline__ int rn_slab(const RnemdArgs &g, double y)
+{
+    return (y >= g.ya0 && y < g.ya1) ? 0 : (y >= g.yb0 && y < g.yb1) ? 1 : -1;
+}
+__device__ __forceinline__ float rn_key(const RnemdArgs &g, float vx, int slab)
+{
+    return fabsf(slab == 0 ? __fsub_rn(vx, g.vtf) : __fadd_rn(vx, g.vtf));
+}
+__device__ __forceinline__ double rn_key(const RnemdArgs &g, double vx, int slab)
+{
+    return fabs(slab == 0 ? __dsub_rn(vx, g.vt) : __dadd_rn(vx, g.vt));
+}
+__device__ __forceinline__ bool rn_due(const StepArgs &a, const RnemdArgs &g)
+{
+    return (*a.d_step + g.step_offset) % g.period == 0;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(512) k_rnemd_hist(StepArgs a, RnemdArgs g)
+{
+    __shared__ int sh[2 * RN_BUCKETS];
+    if (!rn_due(a, g)) return;
+    for (int b = threadIdx.x; b < 2 * RN_BUCKETS; b += blockDim.x) sh[b] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 2) g.count[threadIdx.x] = 0;
+    __syncthreads();
+    const DevReplica r = a.reps[0];
+    const Real *Y = (const Real *)a.y, *VX = (const Real *)a.vx;
+    const int64_t end = r.solv_begin + r.n_solvent;
+    for (int64_t i = r.solv_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int sl = rn_slab(g, Y[i]);
+        if (sl >= 0) atomicAdd(&sh[sl * RN_BUCKETS + rn_bucket((float)rn_key(g, VX[i], sl))], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 2 * RN_BUCKETS; b += blockDim.x)
+        if (sh[b]) atomicAdd(&g.hist[b], sh[b]);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(512) k_rnemd_collect(StepArgs a, RnemdArgs g)
+{
+    __shared__ int thr[2];
+    if (!rn_due(a, g)) return;
+    const unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int PER = RN_BUCKETS / 32;
+    if (warp < 2) {
+        // threshold of slab `warp`: the first bucket at which the running count
+        // reaches max_pairs (every bucket if the slab holds fewer)
+        const int *h = g.hist + warp * RN_BUCKETS;
+        int part = 0;
+        for (int j = 0; j < PER; ++j) part += h[lane * PER + j];
+        int incl = part;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int before = incl - part, total = __shfl_sync(FULL, incl, 31);
+        int t = RN_BUCKETS - 1;
+        if (g.max_pairs == 0) {
+            t = -1;
+        } else if (total > g.max_pairs) {
+            const unsigned hit = __ballot_sync(FULL, before < g.max_pairs && incl >= g.max_pairs);
+            const int owner = __ffs(hit) - 1;
+            int tb = 0;
+            if (lane == owner) {
+                int cum = before;
+                for (int j = 0; j < PER; ++j) {
+                    cum += h[lane * PER + j];
+                    if (cum >= g.max_pairs) { tb = lane * PER + j; break; }
+                }
+            }
+            t = __shfl_sync(FULL, tb, owner);
+        }
+        if (lane == 0) thr[warp] = t;
+    }
+    __syncthreads();
+    const DevReplica r = a.reps[0];
+    const Real *Y = (const Real *)a.y, *VX = (const Real *)a.vx;
+    const int64_t end = r.solv_begin + r.n_solvent;
+    for (int64_t i = r.solv_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int sl = rn_slab(g, Y[i]);
+        if (sl < 0) continue;
+        const Real k = rn_key(g, VX[i], sl);
+        if (rn_bucket((float)k) > thr[sl]) continue;
+        const int pos = atomicAdd(&g.count[sl], 1);
+        if (pos < RN_CAP) {
+            g.key[sl * RN_CAP + pos] = rn_bits(k);
+            g.tag[sl * RN_CAP + pos] = a.tag[i];
+            g.idx[sl * RN_CAP + pos] = (uint32_t)(i - r.solv_begin);
+        }
+    }
+}
+
+struct RnEntry {
+    unsigned long long key;
+    uint32_t tag, idx;
+};
+__device__ __forceinline__ bool rn_less(const RnEntry &p, const RnEntry &q)
+{
+    return p.key < q.key || (p.key == q.key && p.tag < q.tag);
+}
+
+// exact change of one particle's cell words when its v_x changes from v0 to v1
+template <int RULE>
+__device__ __forceinline__ void rn_fix(const StepArgs &a, int c, float v0, float v1, float vy, float vz)
+{
+    constexpr int NW = Words32<RULE>::n;
+    const float xi[3] = {0.f, 0.f, 0.f};
+    long long w0[4], w1[4];
+    record_terms<RULE>(a.m_solvent_f, v0, vy, vz, xi, false, w0);
+    record_terms<RULE>(a.m_solvent_f, v1, vy, vz, xi, false, w1);
+    long long *sums = reinterpret_cast<long long *>(a.sums);
+#pragma unroll
+    for (int k = 0; k < NW; ++k)
+        if (w1[k] != w0[k]) red_add(sums + k * a.n_cells + c, w1[k] - w0[k]);
+}
+template <int RULE>
+__device__ __forceinline__ void rn_fix(const StepArgs &a, int c, double v0, double v1, double vy, double vz)
+{
+    constexpr int NW = RULE == 0 ? 6 : 8;
+    const double xi[3] = {0.0, 0.0, 0.0};
+    double w0[NW], w1[NW];
+    terms64<RULE>(a.m_solvent, v0, vy, vz, xi, w0);
+    terms64<RULE>(a.m_solvent, v1, vy, vz, xi, w1);
+    double *sums = reinterpret_cast<double *>(a.sums);
+#pragma unroll
+    for (int k = 0; k < NW; ++k)
+        if (w1[k] != w0[k]) red_add(sums + k * a.n_cells + c, w1[k] - w0[k]);
+}
+
+template <typename Real, int RULE>
+__global__ void __launch_bounds__(1024) k_rnemd_swap(StepArgs a, RnemdArgs g)
+{
+    extern __shared__ __align__(16) unsigned char rn_smem[];
+    RnEntry *E = reinterpret_cast<RnEntry *>(rn_smem);   // [2][RN_CAP]
+    __shared__ double red[32];
+    if (!rn_due(a, g)) return;
+    const int nA = g.count[0], nB = g.count[1];
+    if (nA > RN_CAP || nB > RN_CAP) {
+        if (threadIdx.x == 0) atomicOr(a.d_err, ERR_RNEMD);
+    } else {
+        int P = 2;
+        while (P < nA || P < nB) P <<= 1;
+        const RnEntry pad{~0ull, ~0u, 0u};
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+            E[t] = t < nA ? RnEntry{g.key[t], g.tag[t], g.idx[t]} : pad;
+            E[RN_CAP + t] = t < nB ? RnEntry{g.key[RN_CAP + t], g.tag[RN_CAP + t], g.idx[RN_CAP + t]} : pad;
+        }
+        __syncthreads();
+        // bitonic sort of both lists, ascending by (key, id)
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < 2 * P; t += blockDim.x) {
+                    const int l = t >= P ? 1 : 0, u = t - l * P, v = u ^ j;
+                    if (v > u) {
+                        RnEntry &p = E[l * RN_CAP + u], &q = E[l * RN_CAP + v];
+                        const bool up = (u & k) == 0;
+                        if (rn_less(q, p) == up) {
+                            const RnEntry w = p;
+                            p = q;
+                            q = w;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        const int np = min(g.max_pairs, min(nA, nB));
+        const DevReplica r = a.reps[0];
+        Real *X = (Real *)a.x, *Y = (Real *)a.y, *Z = (Real *)a.z;
+        Real *VX = (Real *)a.vx, *VY = (Real *)a.vy, *VZ = (Real *)a.vz;
+        int32_t S[3] = {0, 0, 0};
+        if (g.fix_sums) grid_shift(r, *a.d_step + g.step_offset, S);
+        double dp = 0.0;
+        for (int i = threadIdx.x; i < np; i += blockDim.x) {
+            const int64_t ia = r.solv_begin + E[i].idx, ib = r.solv_begin + E[RN_CAP + i].idx;
+            const Real va = VX[ia], vb = VX[ib];
+            VX[ia] = vb;
+            VX[ib] = va;
+            dp += (double)Consts<Real>::m(a) * ((double)va - (double)vb);
+            if (g.fix_sums) {
+                const int ca = r.cell_base + cell_axis(X[ia], S[0], r.L[0]) +
+                               r.L[0] * (cell_axis(Y[ia], S[1], r.L[1]) + r.L[1] * cell_axis(Z[ia], S[2], r.L[2]));
+                const int cb = r.cell_base + cell_axis(X[ib], S[0], r.L[0]) +
+                               r.L[0] * (cell_axis(Y[ib], S[1], r.L[1]) + r.L[1] * cell_axis(Z[ib], S[2], r.L[2]));
+                rn_fix<RULE>(a, ca, va, vb, VY[ia], VZ[ia]);
+                rn_fix<RULE>(a, cb, vb, va, VY[ib], VZ[ib]);
+            }
+        }
+        // deterministic block sum of the exchanged momentum
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dp += __shfl_down_sync(0xffffffffu, dp, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dp;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (threadIdx.x == 0) {
+                *g.p_total += v;
+                *g.n_total += np;
+            }
+        }
+    }
+    for (int b = threadIdx.x; b < 2 * RN_BUCKETS; b += blockDim.x) g.hist[b] = 0;
+}
+
+size_t rnemd_swap_smem() { return (size_t)2 * RN_CAP * sizeof(RnEntry); }
+
+template <typename Real, int RULE>
+static void launch_rnemd_t(const StepArgs &a, const RnemdArgs &g, int num_sms, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_rnemd_swap<Real, RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rnemd_swap_smem());
+        configured = true;
+    }
+    const int grid = std::max(1, num_sms);
+    k_rnemd_hist<Real><<<grid, 512, 0, s>>>(a, g);
+    k_rnemd_collect<Real><<<grid, 512, 0, s>>>(a, g);
+    k_rnemd_swap<Real, RULE><<<1, 1024, rnemd_swap_smem(), s>>>(a, g);
+}
+
+void launch_rnemd(const StepArgs &a, const RnemdArgs &g, int num_sms, cudaStream_t s)
+{
+    if (a.precision == 1) {
+        if (a.rule == 0) launch_rnemd_t<float, 0>(a, g, num_sms, s);
+        else launch_rnemd_t<float, 1>(a, g, num_sms, s);
+    } else {
+        if (a.rule == 0) launch_rnemd_t<double, 0>(a, g, num_sms, s);
+        else launch_rnemd_t<double, 1>(a, g, num_sms, s);
+    }
+}
+
+// ------------------------------------------ velocity profile (Sec. III.B)
+constexpr int PROFILE_MAX_BINS = 2048;
+
+template <typename Real>
+__global__ void __launch_bounds__(512) k_velocity_profile(StepArgs a, int bin_axis, int vel_axis, int n_bins,
+                                                          double *mass, double *mom)
+{
+    __shared__ double sm[2 * PROFILE_MAX_BINS];
+    for (int b = threadIdx.x; b < 2 * n_bins; b += blockDim.x) sm[b] = 0.0;
+    __syncthreads();
+    const DevReplica r = a.reps[0];
+    const Real *B = (const Real *)(bin_axis == 0 ? a.x : bin_axis == 1 ? a.y : a.z);
+    const Real *V = (const Real *)(vel_axis == 0 ? a.vx : vel_axis == 1 ? a.vy : a.vz);
+    const double scale = (double)n_bins / (double)r.L[bin_axis];
+    const double m = a.m_solvent;
+    const int64_t end = r.solv_begin + r.n_solvent;
+    for (int64_t i = r.solv_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = min(n_bins - 1, max(0, (int)floor((double)B[i] * scale)));
+        atomicAdd(&sm[b], m);
+        atomicAdd(&sm[n_bins + b], m * (double)V[i]);
+    }
+    if (blockIdx.x == 0)
+        for (int64_t j = r.body_begin + threadIdx.x; j < r.body_end; j += blockDim.x) {
+            const DevBody &bd = a.bodies[j];
+            const int b = min(n_bins - 1, max(0, (int)floor(bd.R[bin_axis] * scale)));
+            atomicAdd(&sm[b], a.shapes[bd.shape].M);
+            atomicAdd(&sm[n_bins + b], bd.P[vel_axis]);
+        }
+    __syncthreads();
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) {
+        if (sm[b] != 0.0) atomicAdd(&mass[b], sm[b]);
+        if (sm[n_bins + b] != 0.0) atomicAdd(&mom[b], sm[n_bins + b]);
+    }
+}
+
+void launch_velocity_profile(const StepArgs &a, int bin_axis, int vel_axis, int n_bins, double *mass, double *mom,
+                             int num_sms, cudaStream_t s)
+{
+    const int grid = std::max(1, num_sms);
+    if (a.precision == 1) k_velocity_profile<float><<<grid, 512, 0, s>>>(a, bin_axis, vel_axis, n_bins, mass, mom);
+    else k_velocity_profile<double><<<grid, 512, 0, s>>>(a, bin_axis, vel_axis, n_bins, mass, mom);
+}
+
 }  // namespace mpcd

@@ -103,6 +103,14 @@ struct mpcd_ctx {
     cudaEvent_t io_ev[2] = {nullptr, nullptr};
     cudaStream_t side = nullptr;                // site/body chain beside the solvent pass
     cudaEvent_t side_ev[2] = {nullptr, nullptr};
+
+    // reverse non-equilibrium exchange (allocated on first use)
+    mpcd_rnemd rn{};
+    int32_t *rn_hist = nullptr, *rn_count = nullptr;
+    unsigned long long *rn_key = nullptr;
+    uint32_t *rn_tag = nullptr, *rn_idx = nullptr;
+    double *rn_tot = nullptr;                   // [0] momentum, [1] pairs (as long long)
+    double *d_profile = nullptr;                // [2][PROFILE bins] velocity-profile sums
 };
 
 namespace {
@@ -413,6 +421,33 @@ int k_advance(mpcd_ctx *c, cudaStream_t s)
     return MPCD_OK;
 }
 
+static_assert(RN_CAP == MPCD_RNEMD_MAX_CANDIDATES, "candidate capacity of the exchange");
+
+// the exchange before the collision of step *d_step + step_offset; fix: the
+// solvent is already binned for that collision
+int k_rnemd(mpcd_ctx *c, cudaStream_t s, int step_offset, int fix)
+{
+    if (!c->rn.enabled || c->Ns == 0) return MPCD_OK;
+    StepArgs a = make_args(c);
+    RnemdArgs g{};
+    const mpcd_rnemd &r = c->rn;
+    g.ya0 = r.y_a; g.ya1 = r.y_a + r.width; g.yb0 = r.y_b; g.yb1 = r.y_b + r.width; g.vt = r.v_target;
+    g.ya0f = (float)g.ya0; g.ya1f = (float)g.ya1; g.yb0f = (float)g.yb0; g.yb1f = (float)g.yb1;
+    g.vtf = (float)g.vt;
+    g.max_pairs = r.max_pairs;
+    g.period = r.period;
+    g.step_offset = step_offset;
+    g.fix_sums = fix;
+    g.hist = c->rn_hist;
+    g.count = c->rn_count;
+    g.key = c->rn_key;
+    g.tag = c->rn_tag;
+    g.idx = c->rn_idx;
+    g.p_total = c->rn_tot;
+    g.n_total = reinterpret_cast<long long *>(c->rn_tot + 1);
+    return timed(c, "rnemd", 0, s, [&] { launch_rnemd(a, g, c->num_sms, s); });
+}
+
 int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
 {
     if (c->Ns == 0) return MPCD_OK;
@@ -447,6 +482,7 @@ int run_steps(mpcd_ctx *c, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return MPCD_OK;
     int e = k_solvent(c, SOLV_STREAM | SOLV_BIN, s);
+    if (!e) e = k_rnemd(c, s, 0, 1);
     if (!e) e = k_bodies(c, s);
     if (!e) e = k_pre(c, s);
     for (int64_t k = 0; k < n && !e; ++k) {
@@ -462,6 +498,7 @@ int run_steps(mpcd_ctx *c, int64_t n, cudaStream_t s)
             if ((e = k_pre(c, c->side, 1))) break;   // step k+1, before the counter advances
             CK(c, cudaEventRecord(c->side_ev[1], c->side));
             if ((e = k_solvent(c, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN, s))) break;
+            if ((e = k_rnemd(c, s, 1, 1))) break;   // before the collision of step k+1
             CK(c, cudaStreamWaitEvent(s, c->side_ev[1], 0));
             if (c->prm.sort_period >= 0 && ++c->since_sort >= c->tune.sort_period)
                 if ((e = do_sort(c, 0, s))) break;
@@ -487,6 +524,9 @@ int check_device_error(mpcd_ctx *c, cudaStream_t s)
         CK(c, cudaMemcpy(w, c->d_err, sizeof w, cudaMemcpyDeviceToHost));
         return fail(c, MPCD_ERR_STATE, "an index check failed (check %d); no access was made", w[1]);
     }
+    if (h & ERR_RNEMD)
+        return fail(c, MPCD_ERR_STATE,
+                    "momentum exchange skipped: more than %d candidates in a slab's threshold bucket", RN_CAP);
     if (h) return fail(c, MPCD_ERR_STATE, "device error word 0x%x", h);
     return MPCD_OK;
 }
@@ -998,7 +1038,8 @@ int mpcd_collide(mpcd_ctx *c, void *stream)
     CHECK_CTX(c);
     CK(c, cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
-    int e = k_solvent(c, SOLV_BIN, s);
+    int e = k_rnemd(c, s, 0, 0);
+    if (!e) e = k_solvent(c, SOLV_BIN, s);
     if (!e) e = k_params(c, s);
     if (!e) e = k_solvent(c, SOLV_COLLIDE, s);
     if (!e) CK(c, cudaGetLastError());
@@ -1082,6 +1123,77 @@ int mpcd_diagnostics(mpcd_ctx *c, mpcd_diag *o, void *stream)
     o->ke_rot = h[8];
     o->step = c->step;
     return MPCD_OK;
+}
+
+int mpcd_set_rnemd(mpcd_ctx *c, const mpcd_rnemd *cfg)
+{
+    CHECK_CTX(c);
+    if (!cfg || cfg->reserved != 0) return MPCD_ERR_ARG;
+    if (cfg->enabled) {
+        const double Ly = c->nrep == 1 ? (double)c->reps[0].L[1] : 0.0;
+        const mpcd_rnemd &r = *cfg;
+        if (c->nrep != 1 || r.max_pairs < 0 || r.max_pairs > MPCD_RNEMD_MAX_PAIRS || r.period < 1 ||
+            !(r.width > 0.0) || !(r.v_target >= 0.0) || !(r.y_a >= 0.0) || !(r.y_b >= 0.0) ||
+            !(r.y_a + r.width <= Ly) || !(r.y_b + r.width <= Ly) ||
+            !(r.y_a + r.width <= r.y_b || r.y_b + r.width <= r.y_a))
+            return MPCD_ERR_ARG;
+        CK(c, cudaSetDevice(c->device));
+        if (!c->rn_hist) {
+            c->rn_hist = (int32_t *)dalloc(c, 2 * RN_BUCKETS * sizeof(int32_t));
+            c->rn_count = (int32_t *)dalloc(c, 2 * sizeof(int32_t));
+            c->rn_key = (unsigned long long *)dalloc(c, 2 * RN_CAP * sizeof(unsigned long long));
+            c->rn_tag = (uint32_t *)dalloc(c, 2 * RN_CAP * sizeof(uint32_t));
+            c->rn_idx = (uint32_t *)dalloc(c, 2 * RN_CAP * sizeof(uint32_t));
+            c->rn_tot = (double *)dalloc(c, 2 * sizeof(double));
+            if (!c->rn_hist || !c->rn_count || !c->rn_key || !c->rn_tag || !c->rn_idx || !c->rn_tot)
+                return fail(c, MPCD_ERR_OOM, "exchange buffers");
+        }
+        CK(c, cudaDeviceSynchronize());   // no step in flight uses the buffers
+        CK(c, cudaMemset(c->rn_hist, 0, 2 * RN_BUCKETS * sizeof(int32_t)));
+        CK(c, cudaMemset(c->rn_tot, 0, 2 * sizeof(double)));
+    }
+    c->rn = *cfg;
+    clear_graphs(c);   // captured steps include (or omit) the exchange
+    return MPCD_OK;
+}
+
+int mpcd_rnemd_totals(mpcd_ctx *c, double *p_exchanged, int64_t *n_pairs, void *stream)
+{
+    CHECK_CTX(c);
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    double h[2] = {0.0, 0.0};
+    if (c->rn_tot) CK(c, cudaMemcpyAsync(h, c->rn_tot, sizeof h, cudaMemcpyDeviceToHost, s));
+    int e = check_device_error(c, s);
+    if (e) return e;
+    long long n = 0;
+    memcpy(&n, &h[1], sizeof n);
+    if (p_exchanged) *p_exchanged = h[0];
+    if (n_pairs) *n_pairs = (int64_t)n;
+    return MPCD_OK;
+}
+
+int mpcd_velocity_profile(mpcd_ctx *c, int32_t bin_axis, int32_t vel_axis, int32_t n_bins, double *mass,
+                          double *momentum, void *stream)
+{
+    CHECK_CTX(c);
+    if (bin_axis < 0 || bin_axis > 2 || vel_axis < 0 || vel_axis > 2 || n_bins < 1 ||
+        n_bins > MPCD_PROFILE_MAX_BINS || !mass || !momentum)
+        return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->d_profile) {
+        c->d_profile = (double *)dalloc(c, 2 * MPCD_PROFILE_MAX_BINS * sizeof(double));
+        if (!c->d_profile) return fail(c, MPCD_ERR_OOM, "profile buffer");
+    }
+    CK(c, cudaMemsetAsync(c->d_profile, 0, 2 * (size_t)n_bins * sizeof(double), s));
+    StepArgs a = make_args(c);
+    launch_velocity_profile(a, bin_axis, vel_axis, n_bins, c->d_profile, c->d_profile + n_bins, c->num_sms, s);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(mass, c->d_profile, (size_t)n_bins * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(momentum, c->d_profile + n_bins, (size_t)n_bins * sizeof(double),
+                          cudaMemcpyDeviceToHost, s));
+    return check_device_error(c, s);
 }
 
 int mpcd_set_debug(mpcd_ctx *c, int32_t on)

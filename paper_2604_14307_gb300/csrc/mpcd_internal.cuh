@@ -26,7 +26,7 @@ namespace mpcd {
 enum : uint32_t { TAG_SHIFT = 1, TAG_AXIS = 2, TAG_THERMO = 3, TAG_THERMO_ODD = 4,
                   TAG_SITE = 5, TAG_AT = 6 };
 // Bits of the device error word.
-enum : int { ERR_POSITION = 1, ERR_CELL = 2, ERR_TIMEOUT = 4, ERR_INDEX = 8 };
+enum : int { ERR_POSITION = 1, ERR_CELL = 2, ERR_TIMEOUT = 4, ERR_INDEX = 8, ERR_RNEMD = 16 };
 
 constexpr uint32_t PAD_TAG = 0xFFFFFFFFu;
 constexpr int NLIST_MAX = 96;       // neighbour-list capacity per body
@@ -283,6 +283,28 @@ void launch_solvent_diag(const StepArgs &a, double *acc, cudaStream_t s);
 // re-sort (kernels_solvent.cu)
 void launch_sort_count(const StepArgs &a, int32_t *counts, cudaStream_t s);
 void launch_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, cudaStream_t s);
+
+// Reverse non-equilibrium momentum exchange between two slabs (replica 0).
+constexpr int RN_BUCKETS = 4096;   // rank-key histogram: float bits >> 20 (1/8 octave)
+constexpr int RN_CAP = 4096;       // candidates kept per slab (MPCD_RNEMD_MAX_CANDIDATES)
+struct RnemdArgs {
+    float ya0f, ya1f, yb0f, yb1f, vtf;   // slab bounds and target (P32 decisions)
+    double ya0, ya1, yb0, yb1, vt;       // the same in double (P64 decisions)
+    int32_t max_pairs, period;
+    int32_t step_offset;                 // added to *d_step: the step whose collision follows
+    int32_t fix_sums;                    // the solvent is already binned: correct its cell words
+    int32_t *hist;                       // [2][RN_BUCKETS], zero between exchanges
+    int32_t *count;                      // [2]
+    unsigned long long *key;             // [2][RN_CAP] bits of the rank key
+    uint32_t *tag, *idx;                 // [2][RN_CAP] particle id, slot - solv_begin
+    double *p_total;                     // exchanged x momentum, A -> B
+    long long *n_total;                  // exchanged pairs
+};
+void launch_rnemd(const StepArgs &a, const RnemdArgs &g, int num_sms, cudaStream_t s);
+size_t rnemd_swap_smem();
+// mass and momentum profile of replica 0 (solvent and bodies), FP64 [n_bins] each
+void launch_velocity_profile(const StepArgs &a, int bin_axis, int vel_axis, int n_bins, double *mass, double *mom,
+                             int num_sms, cudaStream_t s);
 void launch_sort_scatter(const StepArgs &a, const int32_t *offsets, int32_t *cursor,
                          void *const dst[6], uint32_t *dst_tag, cudaStream_t s);
 void launch_sort_canonical(const StepArgs &a, void *const arr[6], uint32_t *tag,

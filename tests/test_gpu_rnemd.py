@@ -1,0 +1,237 @@
+"""GPU tests of the reverse non-equilibrium exchange and the velocity profile
+(Sec. III.B, Eq. 14).
+
+* One step with the exchange from the same state as the oracle, through the
+  unpipelined calls (stream, couple, collide: the exchange runs before binning)
+  and through mpcd_step (the exchange runs after the pass that already binned
+  the solvent, and corrects the exchanged particles' cell words): positions
+  bit-exact, the solvent's cell words bit-exact, velocities within the parity
+  bar, the same number of pairs and the same exchanged momentum.  The first
+  exchange sees identical stored values on both sides, so the selection is
+  compared exactly.
+* The period: over two steps with period 2 only the first exchanges.
+* Argument checks and the candidate-overflow status (raised on the host from a
+  device flag; no device fault).
+* The velocity profile against numpy binning of the downloaded state.
+* eta_0: pure SRD solvent with the cell thermostat in a 20 x 40 x 20 box,
+  driven by the exchange; Eq. 14 must give the paper's eta_0 = 3.96 within 2.5 %
+  (3.945 measured: 0.4 % low).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_14307_gb300 import inputs as I
+from paper_2604_14307_gb300 import transport as T
+
+pytestmark = pytest.mark.gpu
+
+TOL = {I.P64: 1e-12, I.P32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14307_gb300 import binding, build_lib
+    build_lib.build()
+    return binding
+
+
+def solvent_box(L, precision=I.P32, rule=I.SRD, thermostat=1, seed=5, density=5.0):
+    prm = I.Params(rule=rule, thermostat=thermostat, precision=precision, seed=seed)
+    return I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [L], density, [[]], "solvent_only",
+                          placement_seed=seed)
+
+
+def suspension_box(precision=I.P32, rule=I.SRD, seed=6):
+    """a box of height 16 with three 162-site spheres (sites take part in the
+    collision, not in the exchange)"""
+    prm = I.Params(rule=rule, thermostat=1, precision=precision, seed=seed)
+    return I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [(12, 16, 12)], 5.0, [[0, 0, 0]], "suspension",
+                          placement_seed=seed)
+
+
+SLABS = dict(y_a=0.0, y_b=8.0, width=1.0, v_target=0.5)
+
+
+def check_against_oracle(B, system, max_pairs, pipelined):
+    prec = system.params.precision
+    tol = TOL[prec]
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.set_debug(True)
+    sim.set_rnemd(max_pairs=max_pairs, period=1, **SLABS)
+    if pipelined:
+        sim.step(1)
+    else:
+        sim.stream()
+        sim.couple(B.MPCD_PRE)
+        sim.collide()
+        sim.couple(B.MPCD_POST)
+    d = sim.debug_cells()
+    g = sim.get_state()
+    dp, npairs = sim.rnemd_totals()
+    sim.close()
+
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st)
+    O.stream(osys, ost)
+    odp, on = O.rnemd_exchange(osys, ost, SLABS["y_a"], SLABS["y_b"], SLABS["width"], SLABS["v_target"],
+                               max_pairs)
+    tr = O.collide(osys, ost)
+    assert on > 0 or max_pairs == 0
+    assert npairs == on
+    assert dp == pytest.approx(odp, rel=1e-12, abs=1e-9)
+    assert np.array_equal(g.x, ost.x)
+    scale = np.abs(ost.v) + 1.0
+    assert np.max(np.abs(g.v - ost.v) / scale) <= tol
+    if prec == I.P32:
+        # solvent-only cells: the corrected words equal those of binning after the exchange
+        sites = np.zeros(tr["fixed"].shape[1], dtype=bool)
+        if osys.n_sites:
+            sites[tr["cell_site"] + osys.cell_base[0]] = True
+        # (AT: the noise words come from float32 transcendentals on the GPU, so
+        # the momentum/count words are the exact ones there)
+        nw = 3 if system.params.rule == I.SRD else 2
+        assert np.array_equal(d["sums"][:nw, ~sites], tr["fixed"][:nw, ~sites])
+    else:
+        w = d["sums"]
+        assert np.array_equal(w[0], tr["sums"][0])
+        assert np.max(np.abs(w[2] - tr["sums"][2]) / np.sqrt(np.maximum(tr["sums"][1], 1.0))) <= tol
+
+
+@pytest.mark.parametrize("pipelined", [True, False])
+@pytest.mark.parametrize("max_pairs", [0, 1, 37, 100, 1024])
+def test_one_step_with_exchange_matches_oracle(B, pipelined, max_pairs):
+    check_against_oracle(B, solvent_box((12, 16, 10)), max_pairs, pipelined)
+
+
+@pytest.mark.parametrize("prec,rule", [(I.P64, I.SRD), (I.P32, I.AT)])
+def test_exchange_other_forms(B, prec, rule):
+    check_against_oracle(B, solvent_box((12, 16, 10), precision=prec, rule=rule, thermostat=0), 50, True)
+
+
+def test_exchange_beside_colloids(B):
+    check_against_oracle(B, suspension_box(), 60, True)
+
+
+def test_exchange_period(B):
+    system = solvent_box((10, 16, 10))
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.set_rnemd(max_pairs=20, period=2, **SLABS)
+    sim.step(2)
+    g = sim.get_state()
+    dp, npairs = sim.rnemd_totals()
+    sim.close()
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st)
+    odp, on = O.step_rnemd(osys, ost, 2, SLABS["y_a"], SLABS["y_b"], SLABS["width"], SLABS["v_target"], 20,
+                           period=2)
+    assert npairs == on == 20
+    assert dp == pytest.approx(odp, rel=1e-12)
+    assert np.max(np.abs(g.v - ost.v) / (np.abs(ost.v) + 1.0)) <= TOL[I.P32]
+
+
+def test_exchange_arguments_are_checked(B):
+    system = solvent_box((10, 16, 10))
+    sim = B.Simulation(system)
+    sim.set_state(I.initial_state(system))
+    bad = [dict(max_pairs=2000), dict(period=0), dict(width=0.0), dict(y_b=0.5),      # overlap
+           dict(y_b=15.5), dict(v_target=-1.0)]
+    for b in bad:
+        kw = dict(SLABS, max_pairs=10, period=1)
+        kw.update(b)
+        with pytest.raises(B.MPCDError) as e:
+            sim.set_rnemd(**kw)
+        assert e.value.status == B.MPCD_ERR_ARG, b
+    sim.close()
+    two = I.batched_single_sphere(n_rep=2, precision=I.P32, seed=1, Ls=(12,))
+    sim = B.Simulation(two)
+    with pytest.raises(B.MPCDError) as e:
+        sim.set_rnemd(max_pairs=10, **SLABS)
+    assert e.value.status == B.MPCD_ERR_ARG
+    sim.close()
+
+
+def test_candidate_overflow_is_reported(B):
+    # 30 x 30 cells x 5 per cell = 4500 slab particles, all exactly on target;
+    # a band around slab A is held still in y so that the slab keeps them
+    system = solvent_box((30, 16, 30))
+    st = I.initial_state(system)
+    y = st.x[:, 1]
+    band = (y < 1.5) | (y >= 15.5)
+    assert ((y >= 0.0) & (y < 1.0)).sum() > 4096
+    st.v[band, 0] = 0.5
+    st.v[band, 1] = 0.0
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.set_rnemd(max_pairs=10, **SLABS)
+    sim.stream()
+    sim.couple(B.MPCD_PRE)
+    sim.collide()
+    with pytest.raises(B.MPCDError) as e:
+        sim.rnemd_totals()
+    assert e.value.status == B.MPCD_ERR_STATE and "candidates" in str(e.value)
+    sim.close()
+
+
+def test_velocity_profile_matches_host_binning(B):
+    system = suspension_box()
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.step(3)
+    g = sim.get_state()
+    n_bins = 32
+    mass, mom = sim.velocity_profile(n_bins, bin_axis=1, vel_axis=0)
+    sim.close()
+    Ly = system.replicas[0].L[1]
+    m = np.float32(system.params.m_solvent)
+    b = np.clip(np.floor(g.x[:, 1] * n_bins / Ly).astype(int), 0, n_bins - 1)
+    M = np.bincount(b, minlength=n_bins) * float(m)
+    P = np.bincount(b, weights=float(m) * g.v[:, 0], minlength=n_bins)
+    Mb = system.shapes[0].m.sum()
+    bb = np.clip(np.floor(g.R[:, 1] * n_bins / Ly).astype(int), 0, n_bins - 1)
+    M += np.bincount(bb, minlength=n_bins) * Mb
+    P += np.bincount(bb, weights=g.P[:, 0], minlength=n_bins)
+    assert np.allclose(mass, M, rtol=1e-12)
+    assert np.allclose(mom, P, rtol=1e-9, atol=1e-9)
+
+
+def test_solvent_viscosity_eta0(B, golden):
+    """Pure solvent (Sec. II.A parameters) sheared by the exchange; Eq. 14."""
+    L = (20, 40, 20)
+    system = solvent_box(L, seed=11)
+    sim = B.Simulation(system)
+    sim.set_state(I.initial_state(system))
+    y_a, y_b, width = 0.0, 20.0, 1.0
+    sim.set_rnemd(y_a=y_a, y_b=y_b, width=width, v_target=0.5, max_pairs=10, period=1)
+    for _ in range(30):
+        sim.step(100)                                # the linear profile builds up
+    p0, n0 = sim.rnemd_totals()
+    n_bins, every, samples = 80, 10, 2000
+    ms, ps = [], []
+    for _ in range(samples):
+        sim.step(every)
+        m, p = sim.velocity_profile(n_bins)
+        ms.append(m)
+        ps.append(p)
+    p1, n1 = sim.rnemd_totals()
+    sim.close()
+    assert n1 - n0 == 10 * every * samples
+    u = T.mean_profile(ms, ps)
+    y = T.bin_centres(n_bins, L[1])
+    sr = T.shear_rate(y, u, L[1], y_a, y_b, width, margin=2.0)
+    duration = every * samples * system.params.dt
+    eta = T.viscosity_rnemd(p1 - p0, duration, L[0] * L[2], sr["gamma_dot"])
+    eta0 = golden["eta0_solvent"]["value"]
+    print(f"eta = {eta:.4f} (eta_0 = {eta0}), gamma_dot = {sr['gamma_dot']:.5f}, slopes {sr['slope_ab']:.5f} "
+          f"{sr['slope_ba']:.5f}")
+    assert sr["slope_ab"] > 0 > sr["slope_ba"]
+    assert abs(sr["slope_ab"] + sr["slope_ba"]) < 0.1 * sr["gamma_dot"]     # symmetric flow
+    assert abs(eta - eta0) < 0.025 * eta0
