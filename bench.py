@@ -48,6 +48,8 @@ def args_():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
+    ap.add_argument("--no-protocols", action="store_true",
+                    help="skip the transport-protocol measurements (momentum exchange)")
     return ap.parse_args()
 
 
@@ -151,6 +153,67 @@ def cpu_baseline(steps: int = 8, L: int = 80):
             "sample": f"{steps} FP64-oracle step(s) of an L={L} box with the workload's density, "
                       f"phi, radius and sites ({n} particle-updates per step), median time",
             "seconds": float(sum(times))}
+
+
+def rnemd_protocol(Bd, I, stream, hbm, steps: int = 20):
+    """The viscosity protocol of Sec. III.B on the paper's box: L = 120 x 240 x
+    120 cells of pure solvent at 5 particles per cell (17.28M particles, P32,
+    SRD + cell thermostat), exchanging up to 100 pairs between the slabs at
+    y = 0 and y = 120 every step.  Reports the exchange kernels' time (CUDA
+    events inside mpcd_step), their algorithmic bytes (two passes reading y and
+    v_x of every particle) against the HBM peak, the step time with and without
+    the exchange, and the oracle's time for one exchange on the same state."""
+    import torch
+    import oracle as O
+    L = (120, 240, 120)
+    prm = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=7)
+    system = I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [L], 5.0, [[]], "rnemd_solvent",
+                            placement_seed=7)
+    st = I.initial_state(system)
+    n = system.n_solvent
+    sim = Bd.Simulation(system)
+    sim.set_state(st)
+
+    def timed_steps(k):
+        sim.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    base = timed_steps(steps)
+    sim.set_rnemd(y_a=0.0, y_b=120.0, width=1.0, v_target=0.5, max_pairs=100, period=1)
+    with_x = timed_steps(steps)
+    sim.set_profiling(True)
+    sim.reset_profile()
+    sim.step(steps)
+    prof = sim.profile()
+    sim.set_profiling(False)
+    p, npairs = sim.rnemd_totals()
+    sim.close()
+    pk = prof["rnemd"]
+    ms_x = pk["total_ms"] / max(pk["launches"], 1)
+    n_slab = 2 * L[0] * L[2] * 5
+    alg = 4.0 * n + n_slab * (4.0 + 16.0 + 16.0)   # the candidates (a few hundred entries) are not counted
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st, compute_forces=False)
+    t0 = time.perf_counter()
+    O.rnemd_exchange(osys, ost, 0.0, 120.0, 1.0, 0.5, 100)
+    t_cpu = time.perf_counter() - t0
+    return {"config": {"box": list(L), "n_solvent": n, "density": 5, "max_pairs": 100, "slab_width": 1.0,
+                       "v_target": 0.5, "period_steps": 1, "form": "P32", "rule": "SRD alpha=130 + cell thermostat"},
+            "ms_per_exchange": ms_x, "launches_per_exchange": 3,
+            "roofline": {"bound": "hbm", "achieved": alg / (ms_x / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (ms_x / 1e3) / 1e9 / hbm, "bytes_per_exchange": alg,
+                         "bytes_note": ("y of every particle (4 B); v_x of the slab members, their 16-B list "
+                                        "entries written and read back (36 B per member)")},
+            "ms_per_step_without": base, "ms_per_step_with": with_x,
+            "pairs_per_exchange": npairs / (2 * steps + 3),
+            "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "exchanges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one oracle exchange on the same {n}-particle state"}}
 
 
 def run_reference(a, ws, rank):
@@ -316,6 +379,10 @@ def main():
         sim64.close()
     del state
 
+    protocols = None
+    if rank == 0 and not a.no_protocols:
+        protocols = {"rnemd": rnemd_protocol(Bd, I, stream, peaks()[0])}
+
     cpu = None
     if rank == 0 and not a.no_cpu:
         cpu = cpu_baseline()
@@ -337,7 +404,8 @@ def main():
             "kernels_note": ("sites_post, body_impulse, body_md, body_force and the next step's sites_pre run "
                              "on a second stream beside solvent_fused; their event spans include shared time"),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "p64": p64, "diag_check": {"ke_solvent_per_particle": diag["ke_solvent"] / system.n_solvent},
+            "p64": p64, "protocols": protocols,
+            "diag_check": {"ke_solvent_per_particle": diag["ke_solvent"] / system.n_solvent},
         }
         print(json.dumps(out))
     if ws > 1:

@@ -228,6 +228,18 @@ int mpcd_set_profiling(mpcd_ctx *ctx, int32_t on);
 int mpcd_get_profile(mpcd_ctx *ctx, mpcd_kernel_time *out, int32_t max);
 int mpcd_reset_profile(mpcd_ctx *ctx);
 
+/* Constant force f on every body, the sedimentation protocol of Sec. III.B:
+ * it acts at the body's centre of mass (the centre site of the paper's spheres;
+ * no torque) and a balancing force -B f / N_s acts on every solvent particle,
+ * so that the box is force free.  The solvent then streams as
+ * v += a dt/2, x += v dt, v += a dt/2 with a = -B f / (N_s m) (exact for a
+ * constant force; in the P32 form a dt/2 is rounded to float once and every
+ * operation is a float operation in that order); the bodies' velocity-Verlet
+ * step includes f.  f = (0, 0, 0) turns it off.  Only contexts with one
+ * replica and at least one solvent particle (else MPCD_ERR_ARG).  The bodies'
+ * stored forces are recomputed on `stream`. */
+int mpcd_set_body_force(mpcd_ctx *ctx, const double f[3], void *stream);
+
 /* Reverse non-equilibrium momentum exchange (Mueller-Plathe), the shear-
  * viscosity protocol of Sec. III.B (Eq. 14).  While enabled, before the
  * collision of every step n with n % period == 0 (after the solvent has
@@ -242,9 +254,9 @@ int mpcd_reset_profile(mpcd_ctx *ctx);
  * Only contexts with one replica (else MPCD_ERR_ARG).  At most
  * MPCD_RNEMD_MAX_PAIRS pairs.  The candidates of a slab are the particles whose
  * rank key lies at or below the 1/8-octave bucket that holds the max_pairs-th
- * smallest key; if more than MPCD_RNEMD_MAX_CANDIDATES of them exist, that
- * exchange is skipped and the next synchronising call (e.g. mpcd_rnemd_totals)
- * returns MPCD_ERR_STATE.  enabled = 0 turns the exchange off.  Setting a
+ * smallest key (keys below 2^-40 share the lowest bucket); if a slab holds more than MPCD_RNEMD_MAX_SLAB particles or more
+ * than MPCD_RNEMD_MAX_CANDIDATES candidates, that exchange is skipped and the
+ * next synchronising call (e.g. mpcd_rnemd_totals) returns MPCD_ERR_STATE.  enabled = 0 turns the exchange off.  Setting a
  * configuration clears the totals and synchronises the device.  The exchange
  * conserves momentum and kinetic energy exactly.  In mpcd_step the exchange
  * runs after the solvent pass that streamed and binned for the collision, and
@@ -252,6 +264,7 @@ int mpcd_reset_profile(mpcd_ctx *ctx);
  * it before binning. */
 #define MPCD_RNEMD_MAX_PAIRS 1024
 #define MPCD_RNEMD_MAX_CANDIDATES 4096
+#define MPCD_RNEMD_MAX_SLAB 1048576
 typedef struct {
     int32_t enabled;
     int32_t max_pairs;     /* 0 .. MPCD_RNEMD_MAX_PAIRS */

@@ -49,7 +49,7 @@ class _Sys(C.Structure):
                 ("body_off", C.c_void_p), ("n_shapes", C.c_int32), ("site_off", C.c_void_p),
                 ("b", C.c_void_p), ("m", C.c_void_p), ("cent_off", C.c_void_p),
                 ("cent", C.c_void_p), ("wca_d", C.c_void_p), ("body_shape", C.c_void_p),
-                ("stream_id", C.c_void_p)]
+                ("stream_id", C.c_void_p), ("f_ext", C.c_void_p)]
 
 
 class _State(C.Structure):
@@ -125,7 +125,8 @@ class OracleSystem:
                       _ptr(self.solv_off), _ptr(self.body_off), len(system.shapes),
                       _ptr(self.site_off), _ptr(self.b), _ptr(self.m), _ptr(self.cent_off),
                       _ptr(self.cent), _ptr(self.wca_d), _ptr(self.body_shape),
-                      _ptr(self.stream_id))
+                      _ptr(self.stream_id), None)
+        self.f_ext = None
         self.n_solvent = int(self.solv_off[-1])
         self.n_bodies = int(self.body_off[-1])
         sizes = [int(so[s + 1] - so[s]) for s in self.body_shape[: self.n_bodies]]
@@ -133,6 +134,16 @@ class OracleSystem:
         self.n_sites = int(self.site_base[-1])
         self.cell_base = np.concatenate([[0], np.cumsum(np.prod(self.L, axis=1))]).astype(np.int64)
         self.n_cells = int(self.cell_base[-1])
+
+    def set_body_force(self, f):
+        """Constant force on every body at its centre of mass, balanced on the
+        solvent (Sec. III.B sedimentation); None or zeros: none."""
+        if f is None or not np.any(np.asarray(f, dtype=np.float64)):
+            self.f_ext = None
+            self.c.f_ext = None
+        else:
+            self.f_ext = np.ascontiguousarray(f, dtype=np.float64).reshape(3).copy()
+            self.c.f_ext = _ptr(self.f_ext)
 
 
 class OracleState:

@@ -32,7 +32,10 @@
  *   cells with fewer than two particles are left unchanged;
  *   sort order within a cell: solvent before sites, each by ascending id;
  *   the momentum change is an impulse at the collision; centre sites are
- *   massless and do not collide.
+ *   massless and do not collide;
+ *   sedimentation (Sec. III.B): the body force acts at the centre of mass (the
+ *   centre site of a sphere, so no torque) and is balanced by an equal share
+ *   on every solvent particle of the replica.
  */
 #include <math.h>
 #include <stdint.h>
@@ -65,6 +68,10 @@ typedef struct {
     const int32_t *body_shape; /* [bodies] */
     const int32_t *stream_id;  /* [n_rep] stream id of each replica (its index in the
                                   whole ensemble); NULL: the replica's position */
+    const double *f_ext;       /* [3] constant force on every body at its centre of
+                                  mass, balanced by -B f / N_s on every solvent
+                                  particle of its replica (Sec. III.B
+                                  sedimentation); NULL: none */
 } orc_sys;
 
 typedef struct {
@@ -375,6 +382,9 @@ int orc_forces(const orc_sys *s, orc_state *st, double *energy)
         }
     }
     if (energy) *energy = E;
+    if (s->f_ext)   /* external force at the centre of mass: no torque */
+        for (int64_t i = 0; i < s->body_off[s->n_rep]; ++i)
+            for (int a = 0; a < 3; ++a) st->F[3 * i + a] += s->f_ext[a];
     return 0;
 }
 
@@ -440,19 +450,36 @@ int orc_stream(const orc_sys *s, orc_state *st)
     const double dt = s->dt;
     for (int r = 0; r < s->n_rep; ++r) {
         const int32_t *L = s->L + 3 * r;
+        /* the solvent's share of the balancing force: acceleration
+         * g = -B f / (N_s m); streaming v += g dt/2, x += v dt, v += g dt/2 */
+        const int64_t nb = s->body_off[r + 1] - s->body_off[r], ns = s->solv_off[r + 1] - s->solv_off[r];
+        double half[3] = { 0.0, 0.0, 0.0 };
+        const int accel = s->f_ext && ns > 0 && (s->f_ext[0] != 0.0 || s->f_ext[1] != 0.0 || s->f_ext[2] != 0.0);
+        if (accel)
+            for (int a = 0; a < 3; ++a) {
+                const double g = -((double)nb * s->f_ext[a]) / ((double)ns * s->m_solvent);
+                half[a] = 0.5 * g * dt;
+            }
         for (int64_t i = s->solv_off[r]; i < s->solv_off[r + 1]; ++i) {
             for (int a = 0; a < 3; ++a) {
                 if (s->precision == ORC_P32) {
                     float x = (float)st->x[3 * i + a], v = (float)st->v[3 * i + a];
-                    float dtf = (float)dt;
+                    float dtf = (float)dt, h = (float)half[a];
+                    if (accel) v = v + h;
                     float step = v * dtf;
                     float y = x + step;
                     if (wrap_f(&y, (float)L[a])) return -1;
+                    if (accel) v = v + h;
                     st->x[3 * i + a] = (double)y;
+                    st->v[3 * i + a] = (double)v;
                 } else {
-                    double y = st->x[3 * i + a] + st->v[3 * i + a] * dt;
+                    double v = st->v[3 * i + a];
+                    if (accel) v = v + half[a];
+                    double y = st->x[3 * i + a] + v * dt;
                     if (wrap_d(&y, (double)L[a])) return -1;
+                    if (accel) v = v + half[a];
                     st->x[3 * i + a] = y;
+                    st->v[3 * i + a] = v;
                 }
             }
         }

@@ -32,7 +32,7 @@ EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "m
            "mpcd_sizes", "mpcd_last_error", "mpcd_set_debug", "mpcd_debug_cells",
            "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
            "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static", "mpcd_set_rnemd",
-           "mpcd_rnemd_totals", "mpcd_velocity_profile"]
+           "mpcd_rnemd_totals", "mpcd_velocity_profile", "mpcd_set_body_force"]
 
 
 class MPCDError(RuntimeError):
@@ -135,6 +135,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "mpcd_set_tuning": [vp, C.POINTER(Tuning)],
             "mpcd_autotune": [vp, i32, vp],
             "mpcd_set_rnemd": [vp, C.POINTER(Rnemd)],
+            "mpcd_set_body_force": [vp, C.POINTER(C.c_double * 3), vp],
             "mpcd_rnemd_totals": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), vp],
             "mpcd_velocity_profile": [vp, i32, i32, i32, vp, vp, vp],
             "mpcd_collide_solvent_static": [C.POINTER(Params), C.POINTER(C.c_int32 * 3), i64, vp, vp, vp,
@@ -336,6 +337,12 @@ class Simulation:
         cfg = Rnemd(int(enabled), int(max_pairs), int(period), 0, float(y_a), float(y_b), float(width),
                     float(v_target))
         self._check(self.lib.mpcd_set_rnemd(self.ctx, C.byref(cfg)))
+
+    def set_body_force(self, f, stream=None):
+        """Constant force on every body, balanced on the solvent (Sec. III.B
+        sedimentation); see mpcd_set_body_force."""
+        arr = (C.c_double * 3)(*[float(v) for v in f])
+        self._check(self.lib.mpcd_set_body_force(self.ctx, C.byref(arr), self._s(stream)))
 
     def rnemd_totals(self, stream=None):
         """(x momentum moved from slab A to slab B, number of exchanged pairs)."""

@@ -295,6 +295,7 @@ __global__ void k_body_force(StepArgs a, int kick)
         for (int64_t j = r.body_begin; j < r.body_end; ++j)
             if (j != i && may_interact(a, pi, a.bpos[j], r, reach)) pair_force(a, bi, si, Qi, j, r, F, T);
     }
+    for (int k = 0; k < 3; ++k) F[k] += a.fext[k];   // external force at the centre of mass (no torque)
     DevBody *o = a.bodies + i;
     double P[3] = {bi.P[0], bi.P[1], bi.P[2]}, L[3] = {bi.Lm[0], bi.Lm[1], bi.Lm[2]};
     for (int k = 0; k < 3; ++k) { o->F[k] = F[k]; o->T[k] = T[k]; }

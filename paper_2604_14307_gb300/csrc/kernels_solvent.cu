@@ -98,6 +98,11 @@ __device__ __forceinline__ double drift(double x, double v, double dt, double L,
     bad |= !(y >= 0.0 && y < L);
     return y;
 }
+// Streaming under a constant force (the solvent's share of the balancing
+// force of the sedimentation protocol): v += a dt/2, x += v dt, v += a dt/2,
+// exact for a constant force; with no force the plain drift.
+__device__ __forceinline__ float kick(float v, float h) { return __fadd_rn(v, h); }
+__device__ __forceinline__ double kick(double v, double h) { return __dadd_rn(v, h); }
 
 
 __device__ __forceinline__ void ld4(const float *p, float (&o)[4])
@@ -153,6 +158,7 @@ template <> struct Consts<float> {
     __device__ static float m(const StepArgs &a) { return a.m_solvent_f; }
     __device__ static float ca(const StepArgs &a) { return a.cos_af; }
     __device__ static float sa(const StepArgs &a) { return a.sin_af; }
+    __device__ static float ah(const StepArgs &a, int k) { return a.ahf[k]; }
 };
 template <> struct Consts<double> {
     __device__ static double kT(const StepArgs &a) { return a.kT; }
@@ -160,6 +166,7 @@ template <> struct Consts<double> {
     __device__ static double m(const StepArgs &a) { return a.m_solvent; }
     __device__ static double ca(const StepArgs &a) { return a.cos_a; }
     __device__ static double sa(const StepArgs &a) { return a.sin_a; }
+    __device__ static double ah(const StepArgs &a, int k) { return a.ah[k]; }
 };
 
 // SRD: v' = u + kappa R(n, alpha)(v - u)  (Rodrigues)
@@ -350,15 +357,25 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
                     }
                 }
                 if (STREAM) {
+                    if (a.accel) {
+                        vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                        vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                        vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                    }
                     x[j] = drift(x[j], vx[j], dt, Lx, bad);
                     y[j] = drift(y[j], vy[j], dt, Ly, bad);
                     z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                    if (a.accel) {
+                        vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                        vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                        vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                    }
                 }
             }
             if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (STREAM) { st4(X + i, x); st4(Y + i, y); st4(Z + i, z); }
-            if (COLLIDE) { st4(VX + i, vx); st4(VY + i, vy); st4(VZ + i, vz); }
+            if (COLLIDE || (STREAM && a.accel)) { st4(VX + i, vx); st4(VY + i, vy); st4(VZ + i, vz); }
         }
     }
     if (bad) atomicOr(a.d_err, ERR_POSITION);
@@ -581,16 +598,26 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (j < nv) {
+                        if (a.accel) {
+                            vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                            vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                            vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                        }
                         x[j] = drift(x[j], vx[j], dt, Lx, bad);
                         y[j] = drift(y[j], vy[j], dt, Ly, bad);
                         z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                        if (a.accel) {
+                            vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                            vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                            vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                        }
                     }
             }
             if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (nv > 0) {
                 if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
-                if (COLLIDE) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
+                if (COLLIDE || (STREAM && a.accel)) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
             }
         }
         fence_async_smem();
@@ -601,7 +628,7 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
             const uint32_t nb = (uint32_t)(((n + 3) & ~3) * sizeof(Real));
             if (STREAM)
                 for (int q = 0; q < 3; ++q) bulk_store(G[q] + beg, S[q], nb);
-            if (COLLIDE)
+            if (COLLIDE || (STREAM && a.accel))
                 for (int q = 3; q < 6; ++q) bulk_store(G[q] + beg, S[q], nb);
             bulk_commit();
         }
@@ -679,7 +706,7 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
                 unsigned char *base = smem + q * SB;
                 if (STREAM)
                     for (int c = 0; c < 3; ++c) bulk_store(G[c] + m.beg, base + (size_t)c * cap * sizeof(Real), nb);
-                if (COLLIDE)
+                if (COLLIDE || (STREAM && a.accel))
                     for (int c = 3; c < 6; ++c) bulk_store(G[c] + m.beg, base + (size_t)c * cap * sizeof(Real), nb);
             }
             bulk_commit();
@@ -786,16 +813,26 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (j < nv) {
+                        if (a.accel) {
+                            vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                            vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                            vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                        }
                         x[j] = drift(x[j], vx[j], dt, Lx, bad);
                         y[j] = drift(y[j], vy[j], dt, Ly, bad);
                         z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                        if (a.accel) {
+                            vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                            vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                            vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                        }
                     }
             }
             if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (nv > 0) {
                 if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
-                if (COLLIDE) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
+                if (COLLIDE || (STREAM && a.accel)) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
             }
         }
         fence_async_smem();   // results visible to the bulk stores
@@ -980,16 +1017,26 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (j < nv) {
+                        if (a.accel) {
+                            vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                            vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                            vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                        }
                         x[j] = drift(x[j], vx[j], dt, Lx, bad);
                         y[j] = drift(y[j], vy[j], dt, Ly, bad);
                         z[j] = drift(z[j], vz[j], dt, Lz, bad);
+                        if (a.accel) {
+                            vx[j] = kick(vx[j], Consts<Real>::ah(a, 0));
+                            vy[j] = kick(vy[j], Consts<Real>::ah(a, 1));
+                            vz[j] = kick(vz[j], Consts<Real>::ah(a, 2));
+                        }
                     }
             }
             if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (nv > 0) {
                 if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
-                if (COLLIDE) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
+                if (COLLIDE || (STREAM && a.accel)) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
             }
         }
         fence_async_smem();   // results visible to the bulk stores
@@ -1000,7 +1047,7 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
             const int64_t beg = mt.beg;
             if (STREAM)
                 for (int c = 0; c < 3; ++c) bulk_store(garr(c) + beg, sb + (size_t)c * cap * sizeof(Real), nb);
-            if (COLLIDE)
+            if (COLLIDE || (STREAM && a.accel))
                 for (int c = 3; c < 6; ++c) bulk_store(garr(c) + beg, sb + (size_t)c * cap * sizeof(Real), nb);
         }
         if (lane == 0) bulk_commit();
@@ -1710,17 +1757,36 @@ void launch_sort_canonical(const StepArgs &a, void *const d[6], uint32_t *tag, c
 // ------------------------------------------ RNEMD exchange (Sec. III.B)
 // Reverse non-equilibrium (Mueller-Plathe) exchange of v_x between the solvent
 // particles of slab A closest to +v_t and those of slab B closest to -v_t.
-// Three launches: a histogram of the rank keys per slab (1/8-octave buckets of
-// the non-negative key), a collection of the candidates up to the bucket that
-// holds the max_pairs-th smallest key, and one CTA that sorts the candidates
-// (key, then id) and exchanges the pairs.  When the solvent is already binned
-// for the coming collision, the exchanged particles' contributions to the cell
-// words are corrected exactly (the difference of their old and new terms).
-__device__ __forceinline__ int rn_bucket(float k) { return (int)(__float_as_uint(k) >> 20); }
+// Three launches.  k_rnemd_scan reads y of every particle (vector loads) and
+// v_x of the slab members only; it lists the members with their rank keys
+// (each CTA gathers its members in shared memory and reserves global space
+// once) and histograms the keys per slab in 1/8-octave buckets.
+// k_rnemd_filter finds, in every CTA, the bucket holding the max_pairs-th
+// smallest key of each slab and keeps the listed members up to it as
+// candidates.  k_rnemd_select, one CTA, sorts the candidates (key, then id) and
+// exchanges the pairs.  When the solvent is already binned for the coming collision the
+// exchanged particles' contributions to the cell words are corrected exactly
+// (the difference of their old and new terms).
+// 1/8-octave bucket of a non-negative key (float bits >> 20), clamped to the
+// RN_BUCKETS buckets that start at 2^-40: monotone in the key
+__device__ __forceinline__ int rn_bucket(float k)
+{
+    constexpr int lo = (127 - 40) << 3;   // bucket of 2^-40
+    return min(max((int)(__float_as_uint(k) >> 20) - lo, 0), RN_BUCKETS - 1);
+}
 __device__ __forceinline__ unsigned long long rn_bits(float k) { return (unsigned long long)__float_as_uint(k); }
 __device__ __forceinline__ unsigned long long rn_bits(double k)
 {
     return (unsigned long long)__double_as_longlong(k);
+}
+template <typename Real> __device__ __forceinline__ int rn_bucket_of_bits(unsigned long long b);
+template <> __device__ __forceinline__ int rn_bucket_of_bits<float>(unsigned long long b)
+{
+    return rn_bucket(__uint_as_float((uint32_t)b));
+}
+template <> __device__ __forceinline__ int rn_bucket_of_bits<double>(unsigned long long b)
+{
+    return rn_bucket((float)__longlong_as_double((long long)b));
 }
 __device__ __forceinline__ int rn_slab(const RnemdArgs &g, float y)
 {
@@ -1743,89 +1809,77 @@ __device__ __forceinline__ bool rn_due(const StepArgs &a, const RnemdArgs &g)
     return (*a.d_step + g.step_offset) % g.period == 0;
 }
 
+// members a CTA gathers in shared memory per slab; the launcher sizes the grid
+// so that a CTA's share of a slab fits (the rest would go one by one to the
+// global list through contended atomics)
+constexpr int RN_SBUF = 512;
+
 template <typename Real>
-__global__ void __launch_bounds__(512) k_rnemd_hist(StepArgs a, RnemdArgs g)
+__global__ void __launch_bounds__(512) k_rnemd_scan(StepArgs a, RnemdArgs g)
 {
     __shared__ int sh[2 * RN_BUCKETS];
+    __shared__ RnEntry sbuf[2][RN_SBUF];
+    __shared__ int scount[2], sbase[2];
     if (!rn_due(a, g)) return;
     for (int b = threadIdx.x; b < 2 * RN_BUCKETS; b += blockDim.x) sh[b] = 0;
-    if (blockIdx.x == 0 && threadIdx.x < 2) g.count[threadIdx.x] = 0;
+    if (threadIdx.x < 2) scount[threadIdx.x] = 0;
     __syncthreads();
     const DevReplica r = a.reps[0];
     const Real *Y = (const Real *)a.y, *VX = (const Real *)a.vx;
-    const int64_t end = r.solv_begin + r.n_solvent;
-    for (int64_t i = r.solv_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int sl = rn_slab(g, Y[i]);
-        if (sl >= 0) atomicAdd(&sh[sl * RN_BUCKETS + rn_bucket((float)rn_key(g, VX[i], sl))], 1);
+    const int64_t beg = r.solv_begin, n = r.n_solvent;
+    int bad = 0;
+    auto visit = [&](int64_t i, Real y) {
+        const int sl = rn_slab(g, y);
+        if (sl < 0) return;
+        const Real k = rn_key(g, VX[beg + i], sl);
+        atomicAdd(&sh[sl * RN_BUCKETS + rn_bucket((float)k)], 1);
+        const RnEntry e{rn_bits(k), a.tag[beg + i], (uint32_t)i};
+        const int pos = atomicAdd(&scount[sl], 1);
+        if (pos < RN_SBUF) {
+            sbuf[sl][pos] = e;
+        } else {   // a crowded CTA: straight to the global list
+            const int gp = atomicAdd(&g.count[sl], 1);
+            if (gp < RN_LIST) g.list[(int64_t)sl * RN_LIST + gp] = e;
+            else bad = 1;
+        }
+    };
+    // four consecutive particles per vector load of y (the replica's first
+    // slot is a multiple of 8), RN_LOADS loads in flight per thread: the pass
+    // is bound by how many bytes are in flight
+    constexpr int RN_LOADS = 4;
+    const int64_t n4 = n & ~(int64_t)3;
+    const int64_t stride = 4 * (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); i < n4; i += RN_LOADS * stride) {
+        Real y[RN_LOADS][4];
+#pragma unroll
+        for (int u = 0; u < RN_LOADS; ++u)
+            if (i + u * stride < n4) ld4(Y + beg + i + u * stride, y[u]);
+#pragma unroll
+        for (int u = 0; u < RN_LOADS; ++u)
+            if (i + u * stride < n4)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) visit(i + u * stride + j, y[u][j]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < n - n4) visit(n4 + threadIdx.x, Y[beg + n4 + threadIdx.x]);
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int m = min(scount[threadIdx.x], RN_SBUF);
+        sbase[threadIdx.x] = m ? atomicAdd(&g.count[threadIdx.x], m) : 0;
     }
     __syncthreads();
+    for (int sl = 0; sl < 2; ++sl) {
+        const int m = min(scount[sl], RN_SBUF);
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const int gp = sbase[sl] + j;
+            if (gp < RN_LIST) g.list[(int64_t)sl * RN_LIST + gp] = sbuf[sl][j];
+            else bad = 1;
+        }
+    }
     for (int b = threadIdx.x; b < 2 * RN_BUCKETS; b += blockDim.x)
         if (sh[b]) atomicAdd(&g.hist[b], sh[b]);
+    if (bad) atomicOr(a.d_err, ERR_RNEMD);
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(512) k_rnemd_collect(StepArgs a, RnemdArgs g)
-{
-    __shared__ int thr[2];
-    if (!rn_due(a, g)) return;
-    const unsigned FULL = 0xffffffffu;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int PER = RN_BUCKETS / 32;
-    if (warp < 2) {
-        // threshold of slab `warp`: the first bucket at which the running count
-        // reaches max_pairs (every bucket if the slab holds fewer)
-        const int *h = g.hist + warp * RN_BUCKETS;
-        int part = 0;
-        for (int j = 0; j < PER; ++j) part += h[lane * PER + j];
-        int incl = part;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const int before = incl - part, total = __shfl_sync(FULL, incl, 31);
-        int t = RN_BUCKETS - 1;
-        if (g.max_pairs == 0) {
-            t = -1;
-        } else if (total > g.max_pairs) {
-            const unsigned hit = __ballot_sync(FULL, before < g.max_pairs && incl >= g.max_pairs);
-            const int owner = __ffs(hit) - 1;
-            int tb = 0;
-            if (lane == owner) {
-                int cum = before;
-                for (int j = 0; j < PER; ++j) {
-                    cum += h[lane * PER + j];
-                    if (cum >= g.max_pairs) { tb = lane * PER + j; break; }
-                }
-            }
-            t = __shfl_sync(FULL, tb, owner);
-        }
-        if (lane == 0) thr[warp] = t;
-    }
-    __syncthreads();
-    const DevReplica r = a.reps[0];
-    const Real *Y = (const Real *)a.y, *VX = (const Real *)a.vx;
-    const int64_t end = r.solv_begin + r.n_solvent;
-    for (int64_t i = r.solv_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int sl = rn_slab(g, Y[i]);
-        if (sl < 0) continue;
-        const Real k = rn_key(g, VX[i], sl);
-        if (rn_bucket((float)k) > thr[sl]) continue;
-        const int pos = atomicAdd(&g.count[sl], 1);
-        if (pos < RN_CAP) {
-            g.key[sl * RN_CAP + pos] = rn_bits(k);
-            g.tag[sl * RN_CAP + pos] = a.tag[i];
-            g.idx[sl * RN_CAP + pos] = (uint32_t)(i - r.solv_begin);
-        }
-    }
-}
-
-struct RnEntry {
-    unsigned long long key;
-    uint32_t tag, idx;
-};
 __device__ __forceinline__ bool rn_less(const RnEntry &p, const RnEntry &q)
 {
     return p.key < q.key || (p.key == q.key && p.tag < q.tag);
@@ -1859,23 +1913,85 @@ __device__ __forceinline__ void rn_fix(const StepArgs &a, int c, double v0, doub
         if (w1[k] != w0[k]) red_add(sums + k * a.n_cells + c, w1[k] - w0[k]);
 }
 
+// threshold bucket of slab w (computed by warp w of the CTA): the first bucket
+// at which the running count reaches max_pairs (every bucket if the slab holds
+// fewer; none for max_pairs = 0)
+__device__ __forceinline__ int rn_threshold(const RnemdArgs &g, int w)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    constexpr int PER = RN_BUCKETS / 32;
+    const int *h = g.hist + w * RN_BUCKETS;
+    int part = 0;
+    for (int j = 0; j < PER; ++j) part += h[lane * PER + j];
+    int incl = part;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int before = incl - part, total = __shfl_sync(FULL, incl, 31);
+    if (g.max_pairs == 0) return -1;
+    if (total <= g.max_pairs) return RN_BUCKETS - 1;
+    const unsigned hit = __ballot_sync(FULL, before < g.max_pairs && incl >= g.max_pairs);
+    const int owner = __ffs(hit) - 1;
+    int tb = 0;
+    if (lane == owner) {
+        int cum = before;
+        for (int j = 0; j < PER; ++j) {
+            cum += h[lane * PER + j];
+            if (cum >= g.max_pairs) { tb = lane * PER + j; break; }
+        }
+    }
+    return __shfl_sync(FULL, tb, owner);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(512) k_rnemd_filter(StepArgs a, RnemdArgs g)
+{
+    __shared__ int thr[2];
+    if (!rn_due(a, g)) return;
+    const int warp = threadIdx.x >> 5;
+    if (warp < 2) {
+        const int t = rn_threshold(g, warp);
+        if ((threadIdx.x & 31) == 0) thr[warp] = t;
+    }
+    __syncthreads();
+    for (int sl = 0; sl < 2; ++sl) {
+        const int n = min(g.count[sl], RN_LIST);
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+            const RnEntry e = g.list[(int64_t)sl * RN_LIST + j];
+            if (rn_bucket_of_bits<Real>(e.key) > thr[sl]) continue;
+            const int pos = atomicAdd(&g.ncand[sl], 1);
+            if (pos < RN_CAP) g.cand[sl * RN_CAP + pos] = e;
+        }
+    }
+}
+
 template <typename Real, int RULE>
-__global__ void __launch_bounds__(1024) k_rnemd_swap(StepArgs a, RnemdArgs g)
+__global__ void __launch_bounds__(1024) k_rnemd_select(StepArgs a, RnemdArgs g)
 {
     extern __shared__ __align__(16) unsigned char rn_smem[];
     RnEntry *E = reinterpret_cast<RnEntry *>(rn_smem);   // [2][RN_CAP]
     __shared__ double red[32];
     if (!rn_due(a, g)) return;
-    const int nA = g.count[0], nB = g.count[1];
-    if (nA > RN_CAP || nB > RN_CAP) {
+    const unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool listed = g.count[0] <= RN_LIST && g.count[1] <= RN_LIST;
+    const int nA = g.ncand[0], nB = g.ncand[1];
+    if (listed && nA <= RN_CAP && nB <= RN_CAP) {
+        for (int t = threadIdx.x; t < nA; t += blockDim.x) E[t] = g.cand[t];
+        for (int t = threadIdx.x; t < nB; t += blockDim.x) E[RN_CAP + t] = g.cand[RN_CAP + t];
+    }
+    if (!listed || nA > RN_CAP || nB > RN_CAP) {
         if (threadIdx.x == 0) atomicOr(a.d_err, ERR_RNEMD);
     } else {
         int P = 2;
         while (P < nA || P < nB) P <<= 1;
         const RnEntry pad{~0ull, ~0u, 0u};
         for (int t = threadIdx.x; t < P; t += blockDim.x) {
-            E[t] = t < nA ? RnEntry{g.key[t], g.tag[t], g.idx[t]} : pad;
-            E[RN_CAP + t] = t < nB ? RnEntry{g.key[RN_CAP + t], g.tag[RN_CAP + t], g.idx[RN_CAP + t]} : pad;
+            if (t >= nA) E[t] = pad;
+            if (t >= nB) E[RN_CAP + t] = pad;
         }
         __syncthreads();
         // bitonic sort of both lists, ascending by (key, id)
@@ -1919,47 +2035,54 @@ __global__ void __launch_bounds__(1024) k_rnemd_swap(StepArgs a, RnemdArgs g)
         }
         // deterministic block sum of the exchanged momentum
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dp += __shfl_down_sync(0xffffffffu, dp, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dp;
+        for (int o = 16; o > 0; o >>= 1) dp += __shfl_down_sync(FULL, dp, o);
+        if (lane == 0) red[warp] = dp;
         __syncthreads();
-        if (threadIdx.x < 32) {
-            double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        if (warp == 0) {
+            double v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (threadIdx.x == 0) {
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+            if (lane == 0) {
                 *g.p_total += v;
                 *g.n_total += np;
             }
         }
     }
+    // ready for the next exchange
     for (int b = threadIdx.x; b < 2 * RN_BUCKETS; b += blockDim.x) g.hist[b] = 0;
+    if (threadIdx.x < 2) {
+        g.count[threadIdx.x] = 0;
+        g.ncand[threadIdx.x] = 0;
+    }
 }
 
 size_t rnemd_swap_smem() { return (size_t)2 * RN_CAP * sizeof(RnEntry); }
 
 template <typename Real, int RULE>
-static void launch_rnemd_t(const StepArgs &a, const RnemdArgs &g, int num_sms, cudaStream_t s)
+static void launch_rnemd_t(const StepArgs &a, const RnemdArgs &g, int num_sms, int64_t slab_members,
+                           cudaStream_t s)
 {
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_rnemd_swap<Real, RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_rnemd_select<Real, RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rnemd_swap_smem());
         configured = true;
     }
-    const int grid = std::max(1, num_sms);
-    k_rnemd_hist<Real><<<grid, 512, 0, s>>>(a, g);
-    k_rnemd_collect<Real><<<grid, 512, 0, s>>>(a, g);
-    k_rnemd_swap<Real, RULE><<<1, 1024, rnemd_swap_smem(), s>>>(a, g);
+    const int64_t want = (3 * slab_members / 2 + RN_SBUF - 1) / RN_SBUF;   // 50 % margin
+    const int grid = (int)std::min<int64_t>(std::max<int64_t>(3 * (int64_t)num_sms, want), 1 << 20);
+    k_rnemd_scan<Real><<<grid, 512, 0, s>>>(a, g);
+    k_rnemd_filter<Real><<<std::max(1, num_sms), 512, 0, s>>>(a, g);
+    k_rnemd_select<Real, RULE><<<1, 1024, rnemd_swap_smem(), s>>>(a, g);
 }
 
-void launch_rnemd(const StepArgs &a, const RnemdArgs &g, int num_sms, cudaStream_t s)
+void launch_rnemd(const StepArgs &a, const RnemdArgs &g, int num_sms, int64_t slab_members, cudaStream_t s)
 {
     if (a.precision == 1) {
-        if (a.rule == 0) launch_rnemd_t<float, 0>(a, g, num_sms, s);
-        else launch_rnemd_t<float, 1>(a, g, num_sms, s);
+        if (a.rule == 0) launch_rnemd_t<float, 0>(a, g, num_sms, slab_members, s);
+        else launch_rnemd_t<float, 1>(a, g, num_sms, slab_members, s);
     } else {
-        if (a.rule == 0) launch_rnemd_t<double, 0>(a, g, num_sms, s);
-        else launch_rnemd_t<double, 1>(a, g, num_sms, s);
+        if (a.rule == 0) launch_rnemd_t<double, 0>(a, g, num_sms, slab_members, s);
+        else launch_rnemd_t<double, 1>(a, g, num_sms, slab_members, s);
     }
 }
 

@@ -107,10 +107,12 @@ struct mpcd_ctx {
     // reverse non-equilibrium exchange (allocated on first use)
     mpcd_rnemd rn{};
     int32_t *rn_hist = nullptr, *rn_count = nullptr;
-    unsigned long long *rn_key = nullptr;
-    uint32_t *rn_tag = nullptr, *rn_idx = nullptr;
+    RnEntry *rn_list = nullptr, *rn_cand = nullptr;
+    int32_t *rn_ncand = nullptr;
     double *rn_tot = nullptr;                   // [0] momentum, [1] pairs (as long long)
     double *d_profile = nullptr;                // [2][PROFILE bins] velocity-profile sums
+    double f_ext[3] = {0.0, 0.0, 0.0};          // constant force on every body (one replica)
+    bool have_state = false;                    // mpcd_set_state has run
 };
 
 namespace {
@@ -222,6 +224,17 @@ StepArgs make_args(const mpcd_ctx *c)
     a.n_sites = c->Nsite;
     a.d_step = c->d_step;
     a.d_err = c->d_err;
+    // constant body force, balanced by a uniform force on the solvent of the
+    // (single) replica: each particle gets -B f / N_s, i.e. acceleration g
+    if (c->f_ext[0] != 0.0 || c->f_ext[1] != 0.0 || c->f_ext[2] != 0.0) {
+        for (int k = 0; k < 3; ++k) {
+            a.fext[k] = c->f_ext[k];
+            const double g = -((double)c->B * c->f_ext[k]) / ((double)c->Ns * p.m_solvent);
+            a.ah[k] = 0.5 * g * p.dt;
+            a.ahf[k] = (float)a.ah[k];
+        }
+        a.accel = 1;
+    }
     return a;
 }
 
@@ -422,6 +435,7 @@ int k_advance(mpcd_ctx *c, cudaStream_t s)
 }
 
 static_assert(RN_CAP == MPCD_RNEMD_MAX_CANDIDATES, "candidate capacity of the exchange");
+static_assert(RN_LIST == MPCD_RNEMD_MAX_SLAB, "slab capacity of the exchange");
 
 // the exchange before the collision of step *d_step + step_offset; fix: the
 // solvent is already binned for that collision
@@ -440,12 +454,13 @@ int k_rnemd(mpcd_ctx *c, cudaStream_t s, int step_offset, int fix)
     g.fix_sums = fix;
     g.hist = c->rn_hist;
     g.count = c->rn_count;
-    g.key = c->rn_key;
-    g.tag = c->rn_tag;
-    g.idx = c->rn_idx;
+    g.list = c->rn_list;
+    g.ncand = c->rn_ncand;
+    g.cand = c->rn_cand;
     g.p_total = c->rn_tot;
     g.n_total = reinterpret_cast<long long *>(c->rn_tot + 1);
-    return timed(c, "rnemd", 0, s, [&] { launch_rnemd(a, g, c->num_sms, s); });
+    const int64_t members = (int64_t)std::ceil((double)c->Ns * r.width / (double)c->reps[0].L[1]);
+    return timed(c, "rnemd", 0, s, [&] { launch_rnemd(a, g, c->num_sms, members, s); });
 }
 
 int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
@@ -526,7 +541,8 @@ int check_device_error(mpcd_ctx *c, cudaStream_t s)
     }
     if (h & ERR_RNEMD)
         return fail(c, MPCD_ERR_STATE,
-                    "momentum exchange skipped: more than %d candidates in a slab's threshold bucket", RN_CAP);
+                    "momentum exchange skipped: more than %d particles in a slab or more than %d candidates "
+                    "up to a slab's threshold bucket", RN_LIST, RN_CAP);
     if (h) return fail(c, MPCD_ERR_STATE, "device error word 0x%x", h);
     return MPCD_OK;
 }
@@ -964,6 +980,7 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
     c->step = h->step;
     c->since_sort = 0;
     c->last_key = -1;
+    c->have_state = true;
     return MPCD_OK;
 }
 
@@ -1125,6 +1142,23 @@ int mpcd_diagnostics(mpcd_ctx *c, mpcd_diag *o, void *stream)
     return MPCD_OK;
 }
 
+int mpcd_set_body_force(mpcd_ctx *c, const double f[3], void *stream)
+{
+    CHECK_CTX(c);
+    if (!f || !std::isfinite(f[0]) || !std::isfinite(f[1]) || !std::isfinite(f[2])) return MPCD_ERR_ARG;
+    const bool on = f[0] != 0.0 || f[1] != 0.0 || f[2] != 0.0;
+    if (on && (c->nrep != 1 || c->Ns == 0)) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    for (int k = 0; k < 3; ++k) c->f_ext[k] = f[k];
+    clear_graphs(c);   // captured steps carry the force in their arguments
+    // the stored body forces enter the next half kick: recompute them
+    cudaStream_t s = (cudaStream_t)stream;
+    StepArgs a = make_args(c);
+    if (c->have_state) launch_body_force(a, 0, s);   // else mpcd_set_state computes them
+    CK(c, cudaGetLastError());
+    return MPCD_OK;
+}
+
 int mpcd_set_rnemd(mpcd_ctx *c, const mpcd_rnemd *cfg)
 {
     CHECK_CTX(c);
@@ -1141,15 +1175,17 @@ int mpcd_set_rnemd(mpcd_ctx *c, const mpcd_rnemd *cfg)
         if (!c->rn_hist) {
             c->rn_hist = (int32_t *)dalloc(c, 2 * RN_BUCKETS * sizeof(int32_t));
             c->rn_count = (int32_t *)dalloc(c, 2 * sizeof(int32_t));
-            c->rn_key = (unsigned long long *)dalloc(c, 2 * RN_CAP * sizeof(unsigned long long));
-            c->rn_tag = (uint32_t *)dalloc(c, 2 * RN_CAP * sizeof(uint32_t));
-            c->rn_idx = (uint32_t *)dalloc(c, 2 * RN_CAP * sizeof(uint32_t));
+            c->rn_list = (RnEntry *)dalloc(c, (size_t)2 * RN_LIST * sizeof(RnEntry));
+            c->rn_ncand = (int32_t *)dalloc(c, 2 * sizeof(int32_t));
+            c->rn_cand = (RnEntry *)dalloc(c, (size_t)2 * RN_CAP * sizeof(RnEntry));
             c->rn_tot = (double *)dalloc(c, 2 * sizeof(double));
-            if (!c->rn_hist || !c->rn_count || !c->rn_key || !c->rn_tag || !c->rn_idx || !c->rn_tot)
+            if (!c->rn_hist || !c->rn_count || !c->rn_list || !c->rn_ncand || !c->rn_cand || !c->rn_tot)
                 return fail(c, MPCD_ERR_OOM, "exchange buffers");
         }
         CK(c, cudaDeviceSynchronize());   // no step in flight uses the buffers
         CK(c, cudaMemset(c->rn_hist, 0, 2 * RN_BUCKETS * sizeof(int32_t)));
+        CK(c, cudaMemset(c->rn_count, 0, 2 * sizeof(int32_t)));
+        CK(c, cudaMemset(c->rn_ncand, 0, 2 * sizeof(int32_t)));
         CK(c, cudaMemset(c->rn_tot, 0, 2 * sizeof(double)));
     }
     c->rn = *cfg;

@@ -113,6 +113,10 @@ struct StepArgs {
     void *site_v;                   // [3][n_sites] SoA
     int32_t *site_cell;             // replica-local cell of each site
     int64_t n_sites;
+    int32_t accel;                  // constant-force streaming of the solvent (below)
+    double ah[3];                   // its half-step velocity change a dt / 2 (P64)
+    float ahf[3];                   // the same rounded to float (P32)
+    double fext[3];                 // constant force on every body at its centre of mass
     const int64_t *d_step;          // completed steps (device)
     int32_t step_offset;            // added to *d_step by the site PRE pass (1 when it runs
                                     // for the next step before the counter advances)
@@ -285,8 +289,14 @@ void launch_sort_count(const StepArgs &a, int32_t *counts, cudaStream_t s);
 void launch_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, cudaStream_t s);
 
 // Reverse non-equilibrium momentum exchange between two slabs (replica 0).
-constexpr int RN_BUCKETS = 4096;   // rank-key histogram: float bits >> 20 (1/8 octave)
+constexpr int RN_BUCKETS = 512;    // rank-key histogram: 1/8-octave buckets from 2^-40 to 2^24,
+                                   // smaller keys in the first, larger in the last
 constexpr int RN_CAP = 4096;       // candidates kept per slab (MPCD_RNEMD_MAX_CANDIDATES)
+constexpr int RN_LIST = 1 << 20;   // slab members listed per slab (MPCD_RNEMD_MAX_SLAB)
+struct RnEntry {
+    unsigned long long key;          // bits of the non-negative rank key (float or double)
+    uint32_t tag, idx;               // particle id, slot - solv_begin
+};
 struct RnemdArgs {
     float ya0f, ya1f, yb0f, yb1f, vtf;   // slab bounds and target (P32 decisions)
     double ya0, ya1, yb0, yb1, vt;       // the same in double (P64 decisions)
@@ -294,13 +304,15 @@ struct RnemdArgs {
     int32_t step_offset;                 // added to *d_step: the step whose collision follows
     int32_t fix_sums;                    // the solvent is already binned: correct its cell words
     int32_t *hist;                       // [2][RN_BUCKETS], zero between exchanges
-    int32_t *count;                      // [2]
-    unsigned long long *key;             // [2][RN_CAP] bits of the rank key
-    uint32_t *tag, *idx;                 // [2][RN_CAP] particle id, slot - solv_begin
+    int32_t *count;                      // [2] slab members listed, zero between exchanges
+    RnEntry *list;                       // [2][RN_LIST] slab members
+    int32_t *ncand;                      // [2] candidates kept, zero between exchanges
+    RnEntry *cand;                       // [2][RN_CAP] candidates
     double *p_total;                     // exchanged x momentum, A -> B
     long long *n_total;                  // exchanged pairs
 };
-void launch_rnemd(const StepArgs &a, const RnemdArgs &g, int num_sms, cudaStream_t s);
+// slab_members: the expected members of one slab (sizes the scan grid)
+void launch_rnemd(const StepArgs &a, const RnemdArgs &g, int num_sms, int64_t slab_members, cudaStream_t s);
 size_t rnemd_swap_smem();
 // mass and momentum profile of replica 0 (solvent and bodies), FP64 [n_bins] each
 void launch_velocity_profile(const StepArgs &a, int bin_axis, int vel_axis, int n_bins, double *mass, double *mom,

@@ -1,0 +1,93 @@
+"""GPU tests of the sedimentation forcing (Sec. III.B): a constant force on
+every body, balanced on the solvent.
+
+* One step with the force from the same state as the oracle, through mpcd_step
+  (the solvent pass kicks, drifts and kicks inside the fused pass) and through
+  stream, couple, collide: solvent positions bit-exact, solvent velocities,
+  body momenta and positions within the parity bars.
+* Many steps keep the box force free: solvent plus body momentum stays at its
+  initial value to float rounding, while the bodies gain momentum along f.
+* A force on a context with several replicas, or without solvent, is refused.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_14307_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {I.P64: 1e-12, I.P32: 1e-5}
+F = np.array([0.5, 0.0, 0.0])
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14307_gb300 import binding, build_lib
+    build_lib.build()
+    return binding
+
+
+def box(precision, rule=I.SRD, n_bodies=3, seed=8):
+    prm = I.Params(rule=rule, thermostat=1, precision=precision, seed=seed)
+    return I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [(14, 14, 14)], 5.0, [[0] * n_bodies],
+                          "sediment", placement_seed=seed)
+
+
+@pytest.mark.parametrize("pipelined", [True, False])
+@pytest.mark.parametrize("precision,rule", [(I.P32, I.SRD), (I.P64, I.SRD), (I.P32, I.AT)])
+def test_one_forced_step_matches_oracle(B, pipelined, precision, rule):
+    system = box(precision, rule)
+    tol = TOL[precision]
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.set_body_force(F)
+    if pipelined:
+        sim.step(1)
+    else:
+        sim.stream()
+        sim.couple(B.MPCD_PRE)
+        sim.collide()
+        sim.couple(B.MPCD_POST)
+    g = sim.get_state()
+    sim.close()
+    osys = O.OracleSystem(system)
+    osys.set_body_force(F)
+    ost = O.OracleState(osys, st)
+    O.step(osys, ost, 1)
+    assert np.array_equal(g.x, ost.x)
+    assert np.max(np.abs(g.v - ost.v) / (np.abs(ost.v) + 1.0)) <= tol
+    M = system.shapes[0].m.sum()
+    assert np.max(np.abs(g.P - ost.P)) <= tol * np.sqrt(M) * 10
+    assert np.max(np.abs(g.R - ost.R)) <= 1e-12
+    assert np.all(g.P[:, 0] != st.P[:, 0])
+
+
+def test_forced_box_stays_force_free(B):
+    system = box(I.P32, n_bodies=4, seed=9)
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.set_body_force(10 * F)      # strong enough to beat the bodies' thermal momentum
+    d0 = sim.diagnostics()
+    p0 = np.asarray(d0["p_solvent"]) + np.asarray(d0["p_bodies"])
+    sim.step(400)
+    d1 = sim.diagnostics()
+    p1 = np.asarray(d1["p_solvent"]) + np.asarray(d1["p_bodies"])
+    sim.close()
+    assert np.all(np.abs(p1 - p0) < 1e-2 * np.sqrt(system.n_solvent + system.n_sites))
+    assert d1["p_bodies"][0] - d0["p_bodies"][0] > 0.0
+
+
+def test_force_needs_one_replica_with_solvent(B):
+    two = I.batched_single_sphere(n_rep=2, precision=I.P32, seed=1, Ls=(12,))
+    sim = B.Simulation(two)
+    with pytest.raises(B.MPCDError) as e:
+        sim.set_body_force(F)
+    assert e.value.status == B.MPCD_ERR_ARG
+    sim.set_body_force([0.0, 0.0, 0.0])       # turning it off is always allowed
+    sim.close()
