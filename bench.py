@@ -271,7 +271,7 @@ def main():
 
     sim = Bd.Simulation(system, device=local)
     sim.set_state(state)
-    tuning = sim.tuning() if a.no_tune else sim.autotune(steps_per_trial=6)
+    tuning = sim.tuning() if a.no_tune else sim.autotune(steps_per_trial=10)
     sim.step(a.warmup)
     torch.cuda.synchronize()
     sim.set_profiling(True)

@@ -228,6 +228,13 @@ int mpcd_set_profiling(mpcd_ctx *ctx, int32_t on);
 int mpcd_get_profile(mpcd_ctx *ctx, mpcd_kernel_time *out, int32_t max);
 int mpcd_reset_profile(mpcd_ctx *ctx);
 
+/* Displacement of every body since the last mpcd_set_state, not wrapped into
+ * the box: the sum of the drifts dt P/M of its velocity-Verlet steps (FP64).
+ * The long-time self-diffusion coefficient of Sec. III.B (Eq. 15) follows from
+ * its mean squared change.  D is a host array of [n_bodies][3] doubles.
+ * Synchronises the stream. */
+int mpcd_body_displacements(mpcd_ctx *ctx, double *D, void *stream);
+
 /* Constant force f on every body, the sedimentation protocol of Sec. III.B:
  * it acts at the body's centre of mass (the centre site of the paper's spheres;
  * no torque) and a balancing force -B f / N_s acts on every solvent particle,
@@ -292,7 +299,9 @@ int mpcd_velocity_profile(mpcd_ctx *ctx, int32_t bin_axis, int32_t vel_axis, int
 
 /* Launch configuration of the solvent pass and the re-sort period.  The
  * autotuner times candidate configurations on the current state (which it
- * restores afterwards) and keeps the fastest; set_tuning fixes one directly.
+ * restores afterwards) and keeps the fastest: each candidate runs
+ * mpcd_step(steps_per_trial) twice from that state, the first run recording its
+ * CUDA graph, the second, timed, replaying it.  set_tuning fixes one directly.
  * Any field <= 0 keeps its current value. */
 typedef struct {
     int32_t block;          /* threads per CTA of the solvent pass */

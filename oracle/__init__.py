@@ -55,7 +55,7 @@ class _Sys(C.Structure):
 class _State(C.Structure):
     _fields_ = [("x", C.c_void_p), ("v", C.c_void_p), ("R", C.c_void_p), ("q", C.c_void_p),
                 ("P", C.c_void_p), ("Lm", C.c_void_p), ("F", C.c_void_p), ("T", C.c_void_p),
-                ("step", C.c_int64)]
+                ("step", C.c_int64), ("D", C.c_void_p)]
 
 
 _TRACE_FIELDS = ["shift", "cell_solvent", "cell_site", "site_r", "site_v", "site_vpost",
@@ -159,6 +159,7 @@ class OracleState:
         nb = max(1, self.R.shape[0])
         self.F = np.zeros((nb, 3))
         self.T = np.zeros((nb, 3))
+        self.D = np.zeros((nb, 3))      # unwrapped body displacement since construction
         self.step = int(st.step)
         self.osys = osys
         if compute_forces:
@@ -174,7 +175,7 @@ class OracleState:
             self._keep.append(z)
             return _ptr(z)
         self._c = _State(pp(self.x), pp(self.v), pp(self.R), pp(self.q), pp(self.P),
-                         pp(self.Lm), pp(self.F), pp(self.T), self.step)
+                         pp(self.Lm), pp(self.F), pp(self.T), self.step, pp(self.D))
         return self._c
 
     def sync(self):

@@ -80,6 +80,7 @@ typedef struct {
     double *P, *Lm;     /* [B][3] linear and space-frame angular momentum */
     double *F, *T;      /* [B][3] WCA force and torque */
     int64_t step;
+    double *D;          /* [B][3] unwrapped displacement (sum of the drifts); NULL: not kept */
 } orc_state;
 
 /* Optional per-collision outputs; every pointer may be NULL. */
@@ -494,9 +495,11 @@ int orc_stream(const orc_sys *s, orc_state *st)
             for (int a = 0; a < 3; ++a) st->P[3 * i + a] += 0.5 * dt * st->F[3 * i + a];
             torque_kick(q, p, st->T + 3 * i, 0.5 * dt);
             for (int a = 0; a < 3; ++a) {
-                double y = st->R[3 * i + a] + dt * (st->P[3 * i + a] / bp.M);
+                const double d = dt * (st->P[3 * i + a] / bp.M);
+                double y = st->R[3 * i + a] + d;
                 if (wrap_d(&y, (double)L[a])) return -1;
                 st->R[3 * i + a] = y;
+                if (st->D) st->D[3 * i + a] += d;
             }
             rotor(q, p, 3, 0.5 * dt, bp.Ihat);
             rotor(q, p, 2, 0.5 * dt, bp.Ihat);

@@ -32,7 +32,8 @@ EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "m
            "mpcd_sizes", "mpcd_last_error", "mpcd_set_debug", "mpcd_debug_cells",
            "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
            "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static", "mpcd_set_rnemd",
-           "mpcd_rnemd_totals", "mpcd_velocity_profile", "mpcd_set_body_force"]
+           "mpcd_rnemd_totals", "mpcd_velocity_profile", "mpcd_set_body_force",
+           "mpcd_body_displacements"]
 
 
 class MPCDError(RuntimeError):
@@ -136,6 +137,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "mpcd_autotune": [vp, i32, vp],
             "mpcd_set_rnemd": [vp, C.POINTER(Rnemd)],
             "mpcd_set_body_force": [vp, C.POINTER(C.c_double * 3), vp],
+            "mpcd_body_displacements": [vp, vp, vp],
             "mpcd_rnemd_totals": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), vp],
             "mpcd_velocity_profile": [vp, i32, i32, i32, vp, vp, vp],
             "mpcd_collide_solvent_static": [C.POINTER(Params), C.POINTER(C.c_int32 * 3), i64, vp, vp, vp,
@@ -343,6 +345,12 @@ class Simulation:
         sedimentation); see mpcd_set_body_force."""
         arr = (C.c_double * 3)(*[float(v) for v in f])
         self._check(self.lib.mpcd_set_body_force(self.ctx, C.byref(arr), self._s(stream)))
+
+    def body_displacements(self, stream=None) -> np.ndarray:
+        """Unwrapped displacement of every body since set_state, [n_bodies, 3]."""
+        D = np.zeros((max(1, self.sizes.n_bodies), 3))
+        self._check(self.lib.mpcd_body_displacements(self.ctx, D.ctypes.data, self._s(stream)))
+        return D[: self.sizes.n_bodies]
 
     def rnemd_totals(self, stream=None):
         """(x momentum moved from slab A to slab B, number of exchanged pairs)."""

@@ -144,7 +144,11 @@ __global__ void k_body_md(StepArgs a)
     L_to_p(b.q, b.Lm, p);
     for (int k = 0; k < 3; ++k) b.P[k] += 0.5 * dt * b.F[k];
     torque_kick(b.q, p, b.T, 0.5 * dt);
-    for (int k = 0; k < 3; ++k) b.R[k] = wrapd(b.R[k] + dt * (b.P[k] / sh.M), (double)r.L[k], bad);
+    for (int k = 0; k < 3; ++k) {
+        const double d = dt * (b.P[k] / sh.M);
+        b.D[k] += d;
+        b.R[k] = wrapd(b.R[k] + d, (double)r.L[k], bad);
+    }
     rotor(b.q, p, 3, 0.5 * dt, sh.Ihat);
     rotor(b.q, p, 2, 0.5 * dt, sh.Ihat);
     rotor(b.q, p, 1, dt, sh.Ihat);
@@ -154,7 +158,7 @@ __global__ void k_body_md(StepArgs a)
     for (int k = 0; k < 4; ++k) b.q[k] /= nq;
     p_to_L(b.q, p, b.Lm);
     DevBody *o = a.bodies + i;
-    for (int k = 0; k < 3; ++k) { o->R[k] = b.R[k]; o->P[k] = b.P[k]; o->Lm[k] = b.Lm[k]; }
+    for (int k = 0; k < 3; ++k) { o->R[k] = b.R[k]; o->P[k] = b.P[k]; o->Lm[k] = b.Lm[k]; o->D[k] = b.D[k]; }
     for (int k = 0; k < 4; ++k) o->q[k] = b.q[k];
     a.bpos[i] = make_float4((float)b.R[0], (float)b.R[1], (float)b.R[2], (float)sh.bound);
     // neighbour lists stay valid while every body is within half the skin of

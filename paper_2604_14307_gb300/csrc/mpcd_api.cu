@@ -925,6 +925,7 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
             b.R[k] = x;
             b.P[k] = h->P[3 * i + k];
             b.F[k] = b.T[k] = 0.0;
+            b.D[k] = 0.0;
         }
         for (int k = 0; k < 4; ++k) b.q[k] = h->q[4 * i + k];
         for (int k = 0; k < 3; ++k) b.Lm[k] = h->Lm[3 * i + k];
@@ -1159,6 +1160,19 @@ int mpcd_set_body_force(mpcd_ctx *c, const double f[3], void *stream)
     return MPCD_OK;
 }
 
+int mpcd_body_displacements(mpcd_ctx *c, double *D, void *stream)
+{
+    CHECK_CTX(c);
+    if (!D && c->B) return MPCD_ERR_ARG;
+    if (c->B == 0) return MPCD_OK;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the D field of every body record: a strided copy, three doubles per body
+    CK(c, cudaMemcpy2DAsync(D, 3 * sizeof(double), &c->d_bodies[0].D[0], sizeof(DevBody), 3 * sizeof(double),
+                            (size_t)c->B, cudaMemcpyDeviceToHost, s));
+    return check_device_error(c, s);
+}
+
 int mpcd_set_rnemd(mpcd_ctx *c, const mpcd_rnemd *cfg)
 {
     CHECK_CTX(c);
@@ -1389,13 +1403,18 @@ int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
     const bool prof = c->profiling;
     c->profiling = false;
     int st = MPCD_OK;
+    // Each candidate runs the same steps from the same state twice through
+    // mpcd_step, as a caller would: the first run records (and runs) its CUDA
+    // graph, the second, timed, replays it.
     for (const mpcd_tuning &t : cand) {
         c->tune = t;
         build_tiles(c);
         if ((st = upload_tiles(c))) goto out;
-        if ((st = run_steps(c, 1, s))) goto out;   // warm-up
+        clear_graphs(c);
+        if ((st = mpcd_step(c, steps_per_trial, s))) goto out;   // graph capture + warm-up
+        if ((st = restore())) goto out;
         CK(c, cudaEventRecord(e0, s));
-        if ((st = run_steps(c, steps_per_trial, s))) goto out;
+        if ((st = mpcd_step(c, steps_per_trial, s))) goto out;
         CK(c, cudaEventRecord(e1, s));
         CK(c, cudaEventSynchronize(e1));
         {

@@ -69,6 +69,7 @@ struct DevBody {
     double Lm[3];           // space-frame angular momentum (Eq. 4)
     double F[3];
     double T[3];
+    double D[3];            // displacement since mpcd_set_state, unwrapped (diffusion)
     int32_t shape, rep;
     int64_t site_begin;     // global index of the body's first site
 };

@@ -1,6 +1,6 @@
 """Host-side analysis of the transport protocols of Sec. III.B.
 
-The shear viscosity comes from reverse non-equilibrium simulation: the device
+Shear viscosity.  It comes from reverse non-equilibrium simulation: the device
 exchanges v_x between two slabs (mpcd_set_rnemd), which drives a bidirectional
 linear shear flow, and Eq. 14 relates the rate of exchanged momentum to the
 shear rate of the mass-averaged velocity profile (mpcd_velocity_profile):
@@ -9,6 +9,12 @@ shear rate of the mass-averaged velocity profile (mpcd_velocity_profile):
 
 with A the area of a slab (L^2 for the paper's square cross-section) and the
 factor 2 because the momentum leaves the exchange slabs through two planes.
+
+Self-diffusion.  The long-time self-diffusion coefficient follows from the
+mean squared displacement of the bodies (Eq. 15, Einstein relation), with every
+sample as a time origin, and the finite-size correction of the periodic box,
+Delta D = xi kT / (6 pi eta L), xi = 2.837297, is added.
+
 This module only post-processes host arrays; every per-particle operation runs
 on the device.
 """
@@ -71,3 +77,31 @@ def mean_profile(mass: Sequence[np.ndarray], momentum: Sequence[np.ndarray]) -> 
     M = np.sum(np.asarray(mass, dtype=np.float64), axis=0)
     P = np.sum(np.asarray(momentum, dtype=np.float64), axis=0)
     return np.where(M > 0, P / np.where(M > 0, M, 1.0), 0.0)
+
+
+XI_CUBIC = 2.837297     # periodic-lattice constant of the finite-size corrections (Sec. III.B)
+
+
+def mean_squared_displacement(D: np.ndarray, max_lag: int) -> np.ndarray:
+    """MSD(k) for lags k = 0..max_lag samples from unwrapped displacements D
+    [n_samples, n_bodies, 3], averaged over every time origin and body."""
+    D = np.asarray(D, dtype=np.float64)
+    n = D.shape[0]
+    out = np.zeros(max_lag + 1)
+    for k in range(1, min(max_lag, n - 1) + 1):
+        d = D[k:] - D[:-k]
+        out[k] = np.mean(np.sum(d * d, axis=-1))
+    return out
+
+
+def diffusion_coefficient(msd: np.ndarray, dt_sample: float, lag_lo: int, lag_hi: int) -> float:
+    """Eq. 15: D = (1/6) d MSD / dt, the least-squares slope over lags
+    [lag_lo, lag_hi] (the long-time regime)."""
+    k = np.arange(lag_lo, lag_hi + 1)
+    slope = np.polyfit(k * dt_sample, msd[lag_lo: lag_hi + 1], 1)[0]
+    return float(slope / 6.0)
+
+
+def finite_size_correction(kT: float, eta: float, L: float) -> float:
+    """Delta D = xi kT / (6 pi eta L) for a cubic periodic box of edge L."""
+    return XI_CUBIC * kT / (6.0 * np.pi * eta * L)

@@ -65,7 +65,7 @@ def check_full_step(B, system, n_sample=2000, seed=0):
     st = I.initial_state(system)
     sim = B.Simulation(system)
     sim.set_state(st)
-    sim.autotune(steps_per_trial=6)          # the launch configuration bench.py times
+    sim.autotune(steps_per_trial=10)          # the launch configuration bench.py times
     sim.set_state(st)
     sim.set_debug(True)
     p_before = sim.diagnostics()

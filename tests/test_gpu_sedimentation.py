@@ -8,6 +8,8 @@ every body, balanced on the solvent.
 * Many steps keep the box force free: solvent plus body momentum stays at its
   initial value to float rounding, while the bodies gain momentum along f.
 * A force on a context with several replicas, or without solvent, is refused.
+* The unwrapped body displacements (mpcd_body_displacements, the input of the
+  diffusion coefficient of Eq. 15) match the oracle and the wrapped positions.
 """
 import numpy as np
 import pytest
@@ -91,3 +93,24 @@ def test_force_needs_one_replica_with_solvent(B):
     assert e.value.status == B.MPCD_ERR_ARG
     sim.set_body_force([0.0, 0.0, 0.0])       # turning it off is always allowed
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [I.P32, I.P64])
+def test_body_displacements_match_oracle(B, precision):
+    """Unwrapped displacement (the input of Eq. 15): the oracle's value, and the
+    wrapped position equals start + displacement modulo the box."""
+    system = I.suspension(14, 5.0, 0.1, 2.0, 2, 5.0, I.SRD, 1, precision, seed=3)
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.step(6)
+    D = sim.body_displacements()
+    g = sim.get_state()
+    sim.close()
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st)
+    O.step(osys, ost, 6)
+    assert np.allclose(D, ost.D[: system.n_bodies], rtol=1e-4, atol=1e-9)
+    L = np.array(system.replicas[0].L, dtype=np.float64)
+    d = np.mod(st.R + D - g.R, L)
+    assert np.all(np.minimum(d, L - d) < 1e-9)
