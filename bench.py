@@ -49,7 +49,7 @@ def args_():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
     ap.add_argument("--no-protocols", action="store_true",
-                    help="skip the transport-protocol measurements (momentum exchange)")
+                    help="skip the transport-protocol measurements (momentum exchange, sedimentation)")
     return ap.parse_args()
 
 
@@ -153,6 +153,31 @@ def cpu_baseline(steps: int = 8, L: int = 80):
             "sample": f"{steps} FP64-oracle step(s) of an L={L} box with the workload's density, "
                       f"phi, radius and sites ({n} particle-updates per step), median time",
             "seconds": float(sum(times))}
+
+
+def sedimentation_protocol(sim, stream, steps: int = 20):
+    """The sedimentation protocol of Sec. III.B on the benchmark suspension: a
+    force of 0.5 along x on every colloid, balanced on the solvent (the solvent
+    then streams under a constant force).  Step time with and without it."""
+    import torch
+
+    def timed_steps(k):
+        sim.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    base = timed_steps(steps)
+    sim.set_body_force([0.5, 0.0, 0.0])
+    forced = timed_steps(steps)
+    D = sim.body_displacements()
+    sim.set_body_force([0.0, 0.0, 0.0])
+    return {"force": [0.5, 0.0, 0.0], "steps": steps, "ms_per_step_without": base, "ms_per_step_with": forced,
+            "mean_body_displacement_x": float(np.mean(D[:, 0]))}
 
 
 def rnemd_protocol(Bd, I, stream, hbm, steps: int = 20):
@@ -355,6 +380,7 @@ def main():
            "h2d_bytes_per_step": state_bytes / a.steps, "d2h_bytes_per_step": (state_bytes + 80) / a.steps,
            "how": "mpcd_set_state from pinned host + mpcd_step(steps) + mpcd_get_state to pinned host "
                   "+ mpcd_diagnostics, wall clock", "parts": e2e_parts}
+    sed = sedimentation_protocol(sim, stream) if (rank == 0 and not a.no_protocols) else None
     sim.close()
     del hb
 
@@ -381,7 +407,7 @@ def main():
 
     protocols = None
     if rank == 0 and not a.no_protocols:
-        protocols = {"rnemd": rnemd_protocol(Bd, I, stream, peaks()[0])}
+        protocols = {"rnemd": rnemd_protocol(Bd, I, stream, peaks()[0]), "sedimentation": sed}
 
     cpu = None
     if rank == 0 and not a.no_cpu:

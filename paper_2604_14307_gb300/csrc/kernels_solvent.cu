@@ -16,6 +16,10 @@
 // re-sort     counting sort of the solvent by cell (histogram, scan, scatter,
 //             optional per-cell order by tag) for memory locality; it changes
 //             no result.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "mpcd_internal.cuh"
 
 namespace mpcd {
@@ -1057,43 +1061,43 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
     if (bad) atomicOr(a.d_err, ERR_POSITION);
 }
 
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device,
+// once per (kernel, device) and size; safe from several host threads.
+static void smem_opt_in(const void *func, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;   // the launch reports the error
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = done[{func, dev}];
+    if (bytes > have &&
+        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+        have = bytes;
+}
+
 template <typename Real, int RULE, int FLAGS>
 static void launch_wt(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
-    static bool configured = false;
     const int warps = cfg.block / 32;
     const size_t bytes = (size_t)warps * WT_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
-    if (!configured) {
-        cudaFuncSetAttribute(k_solvent_wt<Real, RULE, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             220 * 1024);
-        configured = true;
-    }
+    smem_opt_in((const void *)k_solvent_wt<Real, RULE, FLAGS>, bytes);
     k_solvent_wt<Real, RULE, FLAGS><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
 }
 
 template <typename Real, int RULE, int FLAGS>
 static void launch_ws(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
-    static size_t configured = 0;   // dynamic shared memory the kernel is opted in for
     const size_t bytes = (size_t)WS_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
-    if (bytes > configured) {
-        cudaFuncSetAttribute(k_solvent_ws<Real, RULE, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bytes);
-        configured = bytes;
-    }
+    smem_opt_in((const void *)k_solvent_ws<Real, RULE, FLAGS>, bytes);
     k_solvent_ws<Real, RULE, FLAGS><<<cfg.grid, cfg.block + 32, bytes, s>>>(a, cfg.cap);
 }
 
 template <typename Real, int RULE, int FLAGS>
 static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
-    static bool configured = false;   // opt in to large dynamic shared memory once
     const size_t bytes = solvent_smem_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap, cfg.block);
-    if (!configured) {
-        cudaFuncSetAttribute(k_solvent_staged<Real, RULE, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        configured = true;
-    }
+    smem_opt_in((const void *)k_solvent_staged<Real, RULE, FLAGS>, bytes);
     k_solvent_staged<Real, RULE, FLAGS><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
 }
 
@@ -2062,12 +2066,7 @@ template <typename Real, int RULE>
 static void launch_rnemd_t(const StepArgs &a, const RnemdArgs &g, int num_sms, int64_t slab_members,
                            cudaStream_t s)
 {
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_rnemd_select<Real, RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)rnemd_swap_smem());
-        configured = true;
-    }
+    smem_opt_in((const void *)k_rnemd_select<Real, RULE>, rnemd_swap_smem());
     const int64_t want = (3 * slab_members / 2 + RN_SBUF - 1) / RN_SBUF;   // 50 % margin
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(3 * (int64_t)num_sms, want), 1 << 20);
     k_rnemd_scan<Real><<<grid, 512, 0, s>>>(a, g);
