@@ -228,6 +228,21 @@ int mpcd_set_profiling(mpcd_ctx *ctx, int32_t on);
 int mpcd_get_profile(mpcd_ctx *ctx, mpcd_kernel_time *out, int32_t max);
 int mpcd_reset_profile(mpcd_ctx *ctx);
 
+/* Per-body velocity autocorrelations (Sec. III.A): C_T(k) = sum over time
+ * origins t of V(t).V(t + k) and C_R(k) the same for the space-frame angular
+ * velocity omega = Q Ihat^-1 Q^T L, for lags of k = 0 .. n_lags-1 samples, with
+ * one sample after every `every`-th step (every sample is a time origin).
+ * mpcd_set_vacf(ctx, n_lags, every) clears the sums and starts sampling from the
+ * current step; n_lags = 0 stops it.  It synchronises the device.  FP64 on the
+ * device, one thread per body, after the POST coupling of each sampled step.
+ * mpcd_get_vacf copies the sums, [n_bodies][n_lags] each, and the number of
+ * origins summed per lag, [n_lags] (divide to get the averages); any pointer
+ * may be NULL; it synchronises the stream and returns MPCD_ERR_ARG while
+ * sampling is off. */
+#define MPCD_VACF_MAX_LAGS 100000
+int mpcd_set_vacf(mpcd_ctx *ctx, int32_t n_lags, int32_t every);
+int mpcd_get_vacf(mpcd_ctx *ctx, double *ct, double *cr, int64_t *counts, void *stream);
+
 /* Displacement of every body since the last mpcd_set_state, not wrapped into
  * the box: the sum of the drifts dt P/M of its velocity-Verlet steps (FP64).
  * The long-time self-diffusion coefficient of Sec. III.B (Eq. 15) follows from

@@ -33,7 +33,7 @@ EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "m
            "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
            "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static", "mpcd_set_rnemd",
            "mpcd_rnemd_totals", "mpcd_velocity_profile", "mpcd_set_body_force",
-           "mpcd_body_displacements"]
+           "mpcd_body_displacements", "mpcd_set_vacf", "mpcd_get_vacf"]
 
 
 class MPCDError(RuntimeError):
@@ -138,6 +138,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "mpcd_set_rnemd": [vp, C.POINTER(Rnemd)],
             "mpcd_set_body_force": [vp, C.POINTER(C.c_double * 3), vp],
             "mpcd_body_displacements": [vp, vp, vp],
+            "mpcd_set_vacf": [vp, i32, i32],
+            "mpcd_get_vacf": [vp, vp, vp, vp, vp],
             "mpcd_rnemd_totals": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), vp],
             "mpcd_velocity_profile": [vp, i32, i32, i32, vp, vp, vp],
             "mpcd_collide_solvent_static": [C.POINTER(Params), C.POINTER(C.c_int32 * 3), i64, vp, vp, vp,
@@ -351,6 +353,23 @@ class Simulation:
         D = np.zeros((max(1, self.sizes.n_bodies), 3))
         self._check(self.lib.mpcd_body_displacements(self.ctx, D.ctypes.data, self._s(stream)))
         return D[: self.sizes.n_bodies]
+
+    def set_vacf(self, n_lags: int, every: int = 1):
+        """Start (or with n_lags = 0 stop) the per-body velocity autocorrelations
+        of Sec. III.A; see mpcd_set_vacf."""
+        self._vacf_lags = int(n_lags)
+        self._check(self.lib.mpcd_set_vacf(self.ctx, int(n_lags), int(every)))
+
+    def vacf(self, stream=None):
+        """(C_T, C_R) per body and lag, averaged over the origins: [n_bodies, n_lags]."""
+        nl, nb = getattr(self, "_vacf_lags", 0), self.sizes.n_bodies
+        ct = np.zeros((max(1, nb), nl))
+        cr = np.zeros((max(1, nb), nl))
+        cnt = np.zeros(nl, dtype=np.int64)
+        self._check(self.lib.mpcd_get_vacf(self.ctx, ct.ctypes.data, cr.ctypes.data, cnt.ctypes.data,
+                                           self._s(stream)))
+        den = np.maximum(cnt, 1)[None, :]
+        return ct[:nb] / den, cr[:nb] / den, cnt
 
     def rnemd_totals(self, stream=None):
         """(x momentum moved from slab A to slab B, number of exchanged pairs)."""

@@ -720,4 +720,58 @@ void launch_body_diag(const StepArgs &a, double *acc, cudaStream_t s)
     k_body_diag<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a, acc);
 }
 
+
+// ------------------------------------------- velocity autocorrelation
+// Sec. III.A: C_T(t) = <V(0).V(t)> and C_R(t) = <omega(0).omega(t)>, every
+// sample a time origin.  After every `every`-th completed step each body adds
+// V(t).V(t - k) and omega(t).omega(t - k) for the lags k it has samples for;
+// the last n_lags samples stay in a per-body ring.  omega is the space-frame
+// angular velocity Q Ihat^-1 Q^T L.  FP64, one thread per body.
+__global__ void k_vacf_sample(StepArgs a, VacfArgs g)
+{
+    const int64_t done = *a.d_step + 1 - g.start;   // steps completed since the start
+    if (done <= 0 || done % g.every != 0) return;
+    const int64_t smp = done / g.every - 1;          // this sample's index
+    const int nk = (int)(smp + 1 < g.n_lags ? smp + 1 : g.n_lags);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0)
+        for (int k = 0; k < nk; ++k) g.count[k] += 1;
+    if (i >= a.n_bodies) return;
+    const DevBody b = a.bodies[i];
+    const DevShape sh = a.shapes[b.shape];
+    double Q[9], Lb[3], wb[3], V[3], W[3];
+    rotmat(b.q, Q);
+    mtv(Q, b.Lm, Lb);
+    for (int k = 0; k < 3; ++k) {
+        V[k] = b.P[k] / sh.M;
+        wb[k] = sh.Ihat[k] > 0.0 ? Lb[k] / sh.Ihat[k] : 0.0;
+    }
+    mv(Q, wb, W);
+    const int64_t base = (int64_t)i * g.n_lags;
+    for (int k = 0; k < nk; ++k) {
+        double cv, cw;
+        if (k == 0) {
+            cv = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+            cw = W[0] * W[0] + W[1] * W[1] + W[2] * W[2];
+        } else {
+            const int64_t r = 3 * (base + (smp - k) % g.n_lags);
+            cv = V[0] * g.ring_v[r] + V[1] * g.ring_v[r + 1] + V[2] * g.ring_v[r + 2];
+            cw = W[0] * g.ring_w[r] + W[1] * g.ring_w[r + 1] + W[2] * g.ring_w[r + 2];
+        }
+        g.ct[base + k] += cv;
+        g.cr[base + k] += cw;
+    }
+    const int64_t r = 3 * (base + smp % g.n_lags);
+    for (int k = 0; k < 3; ++k) {
+        g.ring_v[r + k] = V[k];
+        g.ring_w[r + k] = W[k];
+    }
+}
+
+void launch_vacf_sample(const StepArgs &a, const VacfArgs &g, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    k_vacf_sample<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a, g);
+}
+
 }  // namespace mpcd

@@ -112,6 +112,7 @@ struct mpcd_ctx {
     double *rn_tot = nullptr;                   // [0] momentum, [1] pairs (as long long)
     double *d_profile = nullptr;                // [2][PROFILE bins] velocity-profile sums
     double f_ext[3] = {0.0, 0.0, 0.0};          // constant force on every body (one replica)
+    VacfArgs vacf{};                            // velocity autocorrelations (n_lags 0: off)
     bool have_state = false;                    // mpcd_set_state has run
 };
 
@@ -413,6 +414,14 @@ int k_post(mpcd_ctx *c, cudaStream_t s)
     return timed(c, "body_impulse", 0, s, [&] { launch_body_impulse(a, s); });
 }
 
+// velocity-autocorrelation sample after the POST coupling of a step
+int k_vacf(mpcd_ctx *c, cudaStream_t s)
+{
+    if (c->vacf.n_lags == 0 || c->B == 0) return MPCD_OK;
+    StepArgs a = make_args(c);
+    return timed(c, "vacf", 0, s, [&] { launch_vacf_sample(a, c->vacf, s); });
+}
+
 int k_solvent(mpcd_ctx *c, int flags, cudaStream_t s)
 {
     StepArgs a = make_args(c);
@@ -504,11 +513,13 @@ int run_steps(mpcd_ctx *c, int64_t n, cudaStream_t s)
         if ((e = k_params(c, s))) break;
         if (k == n - 1) {
             if ((e = k_post(c, s))) break;
+            if ((e = k_vacf(c, s))) break;
             if ((e = k_solvent(c, SOLV_COLLIDE, s))) break;
         } else {
             CK(c, cudaEventRecord(c->side_ev[0], s));
             CK(c, cudaStreamWaitEvent(c->side, c->side_ev[0], 0));
             if ((e = k_post(c, c->side))) break;
+            if ((e = k_vacf(c, c->side))) break;
             if ((e = k_bodies(c, c->side))) break;
             if ((e = k_pre(c, c->side, 1))) break;   // step k+1, before the counter advances
             CK(c, cudaEventRecord(c->side_ev[1], c->side));
@@ -1046,6 +1057,7 @@ int mpcd_couple(mpcd_ctx *c, int32_t phase, void *stream)
     CK(c, cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
     int e = phase == MPCD_PRE ? k_pre(c, s) : k_post(c, s);
+    if (!e && phase == MPCD_POST) e = k_vacf(c, s);
     if (!e && phase == MPCD_POST) e = k_advance(c, s);
     if (!e) CK(c, cudaGetLastError());
     return e;
@@ -1170,6 +1182,51 @@ int mpcd_body_displacements(mpcd_ctx *c, double *D, void *stream)
     // the D field of every body record: a strided copy, three doubles per body
     CK(c, cudaMemcpy2DAsync(D, 3 * sizeof(double), &c->d_bodies[0].D[0], sizeof(DevBody), 3 * sizeof(double),
                             (size_t)c->B, cudaMemcpyDeviceToHost, s));
+    return check_device_error(c, s);
+}
+
+int mpcd_set_vacf(mpcd_ctx *c, int32_t n_lags, int32_t every)
+{
+    CHECK_CTX(c);
+    if (n_lags < 0 || n_lags > MPCD_VACF_MAX_LAGS || (n_lags > 0 && every < 1)) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaDeviceSynchronize());   // no step in flight uses the buffers
+    VacfArgs &g = c->vacf;
+    if (n_lags > 0 && c->B > 0 && n_lags > g.n_lags) {
+        // grown buffers (the old ones stay with the context until it is destroyed)
+        const size_t nb = (size_t)c->B * n_lags;
+        g.ring_v = (double *)dalloc(c, nb * 3 * sizeof(double));
+        g.ring_w = (double *)dalloc(c, nb * 3 * sizeof(double));
+        g.ct = (double *)dalloc(c, nb * sizeof(double));
+        g.cr = (double *)dalloc(c, nb * sizeof(double));
+        g.count = (long long *)dalloc(c, (size_t)n_lags * sizeof(long long));
+        if (!g.ring_v || !g.ring_w || !g.ct || !g.cr || !g.count) return fail(c, MPCD_ERR_OOM, "vacf buffers");
+    }
+    if (n_lags > 0 && c->B > 0) {
+        const size_t nb = (size_t)c->B * n_lags;
+        CK(c, cudaMemset(g.ct, 0, nb * sizeof(double)));
+        CK(c, cudaMemset(g.cr, 0, nb * sizeof(double)));
+        CK(c, cudaMemset(g.count, 0, (size_t)n_lags * sizeof(long long)));
+    }
+    g.n_lags = n_lags;
+    g.every = every;
+    g.start = c->step;
+    clear_graphs(c);   // captured steps include (or omit) the sampling
+    return MPCD_OK;
+}
+
+int mpcd_get_vacf(mpcd_ctx *c, double *ct, double *cr, int64_t *counts, void *stream)
+{
+    CHECK_CTX(c);
+    const VacfArgs &g = c->vacf;
+    if (g.n_lags == 0) return MPCD_ERR_ARG;
+    if (c->B == 0) return MPCD_OK;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = (size_t)c->B * g.n_lags;
+    if (ct) CK(c, cudaMemcpyAsync(ct, g.ct, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (cr) CK(c, cudaMemcpyAsync(cr, g.cr, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (counts) CK(c, cudaMemcpyAsync(counts, g.count, (size_t)g.n_lags * sizeof(long long), cudaMemcpyDeviceToHost, s));
     return check_device_error(c, s);
 }
 

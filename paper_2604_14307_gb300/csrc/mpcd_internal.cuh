@@ -289,6 +289,17 @@ void launch_solvent_diag(const StepArgs &a, double *acc, cudaStream_t s);
 void launch_sort_count(const StepArgs &a, int32_t *counts, cudaStream_t s);
 void launch_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, cudaStream_t s);
 
+// Per-body velocity autocorrelation accumulators (translational and angular).
+struct VacfArgs {
+    int32_t n_lags, every;
+    int64_t start;                       // completed steps when the accumulation began
+    double *ring_v, *ring_w;             // [n_bodies][n_lags][3] last samples of V and omega
+    double *ct, *cr;                     // [n_bodies][n_lags] sums of V(t).V(t+k), omega(t).omega(t+k)
+    long long *count;                    // [n_lags] origins summed per lag
+};
+// after the POST coupling of a step, before the counter advances
+void launch_vacf_sample(const StepArgs &a, const VacfArgs &g, cudaStream_t s);
+
 // Reverse non-equilibrium momentum exchange between two slabs (replica 0).
 constexpr int RN_BUCKETS = 512;    // rank-key histogram: 1/8-octave buckets from 2^-40 to 2^24,
                                    // smaller keys in the first, larger in the last

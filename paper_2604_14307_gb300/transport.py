@@ -10,6 +10,11 @@ shear rate of the mass-averaged velocity profile (mpcd_velocity_profile):
 with A the area of a slab (L^2 for the paper's square cross-section) and the
 factor 2 because the momentum leaves the exchange slabs through two planes.
 
+Velocity autocorrelations.  C_T(t) = <V(0).V(t)> and C_R(t) = <omega(0).omega(t)>
+(Sec. III.A) with every sample as a time origin; the device accumulates them
+per body (mpcd_set_vacf); `velocity_autocorrelation` is the same average over
+host samples.
+
 Self-diffusion.  The long-time self-diffusion coefficient follows from the
 mean squared displacement of the bodies (Eq. 15, Einstein relation), with every
 sample as a time origin, and the finite-size correction of the periodic box,
@@ -105,3 +110,31 @@ def diffusion_coefficient(msd: np.ndarray, dt_sample: float, lag_lo: int, lag_hi
 def finite_size_correction(kT: float, eta: float, L: float) -> float:
     """Delta D = xi kT / (6 pi eta L) for a cubic periodic box of edge L."""
     return XI_CUBIC * kT / (6.0 * np.pi * eta * L)
+
+
+def rotation_matrix(q: np.ndarray) -> np.ndarray:
+    """Body-to-space rotation of unit quaternions (w, x, y, z), [..., 3, 3]."""
+    q = np.asarray(q, dtype=np.float64)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], axis=-1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], axis=-1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], axis=-1)], axis=-2)
+
+
+def angular_velocity(q: np.ndarray, L: np.ndarray, Ihat: np.ndarray) -> np.ndarray:
+    """Space-frame omega = Q Ihat^-1 Q^T L of bodies with principal moments Ihat."""
+    Q = rotation_matrix(q)
+    Lb = np.einsum("...ji,...j->...i", Q, np.asarray(L, dtype=np.float64))
+    return np.einsum("...ij,...j->...i", Q, Lb / np.asarray(Ihat, dtype=np.float64))
+
+
+def velocity_autocorrelation(X: np.ndarray, n_lags: int) -> np.ndarray:
+    """<X(t).X(t + k)> per body for k = 0..n_lags-1 over every time origin, from
+    samples X [n_samples, n_bodies, 3]; returns [n_bodies, n_lags]."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    out = np.zeros((X.shape[1], n_lags))
+    for k in range(min(n_lags, n)):
+        out[:, k] = np.mean(np.sum(X[k:] * X[: n - k], axis=-1), axis=0)
+    return out

@@ -1,0 +1,114 @@
+"""GPU tests of the per-body velocity autocorrelations (Sec. III.A; the
+batched single-colloid workload's per-replica observable).
+
+* The device sums equal the host average of V(t).V(t + k) and
+  omega(t).omega(t + k) over the same samples of the GPU's own trajectory
+  (downloaded with mpcd_get_state after every sampled step).
+* Against the oracle: the same ensemble stepped by the oracle from the same
+  state gives the same C_T and C_R per replica and lag for every replica whose
+  two trajectories stayed together (see the test).
+* Arguments are checked; reading before sampling starts is refused.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_14307_gb300 import inputs as I
+from paper_2604_14307_gb300 import transport as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14307_gb300 import binding, build_lib
+    build_lib.build()
+    return binding
+
+
+def moments(system):
+    return np.array([np.sum(system.shapes[s].m[:, None] * (np.sum(system.shapes[s].b ** 2, axis=1)[:, None]
+                                                           - system.shapes[s].b ** 2), axis=0)
+                     for s in system.body_shape_array()])
+
+
+def samples(system, states):
+    M = np.array([system.shapes[s].m.sum() for s in system.body_shape_array()])
+    Ih = moments(system)
+    V = np.stack([st.P / M[:, None] for st in states])
+    W = np.stack([T.angular_velocity(st.q, st.Lm, Ih) for st in states])
+    return V, W
+
+
+def test_device_sums_equal_the_host_average(B):
+    system = I.batched_single_sphere(n_rep=8, precision=I.P32, seed=3, Ls=(12, 16))
+    sim = B.Simulation(system)
+    sim.set_state(I.initial_state(system))
+    n_lags, every, n = 6, 2, 15
+    sim.set_vacf(n_lags, every)
+    states = []
+    for _ in range(n):
+        sim.step(every)
+        states.append(sim.get_state())
+    ct, cr, cnt = sim.vacf()
+    sim.close()
+    V, W = samples(system, states)
+    assert np.array_equal(cnt, n - np.arange(n_lags))
+    assert np.allclose(ct, T.velocity_autocorrelation(V, n_lags), rtol=1e-12, atol=1e-18)
+    assert np.allclose(cr, T.velocity_autocorrelation(W, n_lags), rtol=1e-12, atol=1e-18)
+
+
+def test_vacf_matches_the_oracle_ensemble(B):
+    """The GPU and the oracle step the same ensemble from the same state.  Their
+    body velocities agree to ~1e-6 until, in some replica, the rounding of the
+    FP32 velocities moves a solvent particle across a cell boundary differently;
+    from then on that replica's trajectories part (chaotic, a few % within tens
+    of steps).  Replicas whose trajectories stayed together must give the same
+    autocorrelations; at least a quarter of them do over 24 steps."""
+    system = I.batched_single_sphere(n_rep=16, precision=I.P32, seed=5, Ls=(12,))
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    n_lags, n = 6, 24
+    sim.set_vacf(n_lags, 1)
+    gst = []
+    for _ in range(n):
+        sim.step(1)
+        gst.append(sim.get_state())
+    ct, cr, cnt = sim.vacf()
+    sim.close()
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st)
+    states = []
+    for _ in range(n):
+        O.step(osys, ost, 1)
+        states.append(I.State(x=ost.x, v=ost.v, R=ost.R.copy(), q=ost.q.copy(), P=ost.P.copy(),
+                              Lm=ost.Lm.copy(), step=ost.step))
+    V, W = samples(system, states)
+    Vg, Wg = samples(system, gst)
+    dv = np.max(np.abs(Vg - V), axis=(0, 2)) / np.max(np.abs(V))
+    dw = np.max(np.abs(Wg - W), axis=(0, 2)) / np.max(np.abs(W))
+    close = (dv < 1e-5) & (dw < 1e-5)
+    assert close.sum() >= 4, (dv, dw)
+    oct_, ocr = T.velocity_autocorrelation(V, n_lags), T.velocity_autocorrelation(W, n_lags)
+    assert np.array_equal(cnt, n - np.arange(n_lags))
+    sv, sw = np.max(np.abs(oct_)), np.max(np.abs(ocr))
+    assert np.allclose(ct[close], oct_[close], rtol=1e-4, atol=1e-4 * sv)
+    assert np.allclose(cr[close], ocr[close], rtol=1e-4, atol=1e-4 * sw)
+
+
+def test_vacf_arguments(B):
+    system = I.batched_single_sphere(n_rep=2, precision=I.P32, seed=1, Ls=(12,))
+    sim = B.Simulation(system)
+    sim.set_state(I.initial_state(system))
+    with pytest.raises(B.MPCDError) as e:
+        sim.vacf()
+    assert e.value.status == B.MPCD_ERR_ARG
+    for bad in [(-1, 1), (4, 0)]:
+        with pytest.raises(B.MPCDError) as e:
+            sim.set_vacf(*bad)
+        assert e.value.status == B.MPCD_ERR_ARG
+    sim.close()
