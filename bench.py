@@ -49,7 +49,7 @@ def args_():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
     ap.add_argument("--no-protocols", action="store_true",
-                    help="skip the transport-protocol measurements (momentum exchange, sedimentation)")
+                    help="skip the transport-protocol measurements (momentum exchange, sedimentation, VACF)")
     return ap.parse_args()
 
 
@@ -155,10 +155,11 @@ def cpu_baseline(steps: int = 8, L: int = 80):
             "seconds": float(sum(times))}
 
 
-def sedimentation_protocol(sim, stream, steps: int = 20):
-    """The sedimentation protocol of Sec. III.B on the benchmark suspension: a
-    force of 0.5 along x on every colloid, balanced on the solvent (the solvent
-    then streams under a constant force).  Step time with and without it."""
+def body_protocols(sim, stream, steps: int = 20):
+    """On the benchmark suspension: the sedimentation protocol of Sec. III.B (a
+    force of 0.5 along x on every colloid, balanced on the solvent, which then
+    streams under a constant force) and the per-body velocity autocorrelations
+    of Sec. III.A; step time with and without each."""
     import torch
 
     def timed_steps(k):
@@ -176,8 +177,15 @@ def sedimentation_protocol(sim, stream, steps: int = 20):
     forced = timed_steps(steps)
     D = sim.body_displacements()
     sim.set_body_force([0.0, 0.0, 0.0])
-    return {"force": [0.5, 0.0, 0.0], "steps": steps, "ms_per_step_without": base, "ms_per_step_with": forced,
-            "mean_body_displacement_x": float(np.mean(D[:, 0]))}
+    # per-body velocity autocorrelations (Sec. III.A), 50 lags, every step
+    sim.set_vacf(50, 1)
+    with_vacf = timed_steps(steps)
+    ct, cr, cnt = sim.vacf()
+    sim.set_vacf(0, 1)
+    return {"sedimentation": {"force": [0.5, 0.0, 0.0], "steps": steps, "ms_per_step_without": base,
+                              "ms_per_step_with": forced, "mean_body_displacement_x": float(np.mean(D[:, 0]))},
+            "vacf": {"n_lags": 50, "every": 1, "steps": steps, "ms_per_step_without": base,
+                     "ms_per_step_with": with_vacf, "mean_C_T0": float(np.mean(ct[:, 0]))}}
 
 
 def rnemd_protocol(Bd, I, stream, hbm, steps: int = 20):
@@ -380,7 +388,7 @@ def main():
            "h2d_bytes_per_step": state_bytes / a.steps, "d2h_bytes_per_step": (state_bytes + 80) / a.steps,
            "how": "mpcd_set_state from pinned host + mpcd_step(steps) + mpcd_get_state to pinned host "
                   "+ mpcd_diagnostics, wall clock", "parts": e2e_parts}
-    sed = sedimentation_protocol(sim, stream) if (rank == 0 and not a.no_protocols) else None
+    bodyp = body_protocols(sim, stream) if (rank == 0 and not a.no_protocols) else {}
     sim.close()
     del hb
 
@@ -407,7 +415,7 @@ def main():
 
     protocols = None
     if rank == 0 and not a.no_protocols:
-        protocols = {"rnemd": rnemd_protocol(Bd, I, stream, peaks()[0]), "sedimentation": sed}
+        protocols = {"rnemd": rnemd_protocol(Bd, I, stream, peaks()[0]), **bodyp}
 
     cpu = None
     if rank == 0 and not a.no_cpu:
