@@ -316,7 +316,8 @@ int mpcd_velocity_profile(mpcd_ctx *ctx, int32_t bin_axis, int32_t vel_axis, int
  * autotuner times candidate configurations on the current state (which it
  * restores afterwards) and keeps the fastest: each candidate runs
  * mpcd_step(steps_per_trial) twice from that state, the first run recording its
- * CUDA graph, the second, timed, replaying it.  set_tuning fixes one directly.
+ * CUDA graph, the second, timed, replaying it; the trials leave the exchange
+ * totals and the autocorrelation sums as they were.  set_tuning fixes one directly.
  * Any field <= 0 keeps its current value. */
 typedef struct {
     int32_t block;          /* threads per CTA of the solvent pass */

@@ -1424,7 +1424,17 @@ int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
     CK(c, cudaMemcpyAsync(sbody, c->d_bodies, std::max<int64_t>(1, c->B) * sizeof(DevBody), cudaMemcpyDeviceToDevice, s));
     const int64_t step0 = c->step, since0 = c->since_sort, key0 = c->last_key;
     const int cur0 = c->cur;
+    // the trials must not add to the observables: the exchange totals are
+    // restored after every trial, the autocorrelation sampling is paused
+    double rn_tot0[2] = {0.0, 0.0};
+    if (c->rn_tot) {
+        CK(c, cudaMemcpyAsync(rn_tot0, c->rn_tot, sizeof rn_tot0, cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+    }
+    const int32_t vacf_lags0 = c->vacf.n_lags;
+    c->vacf.n_lags = 0;
     auto restore = [&]() -> int {
+        if (c->rn_tot) CK(c, cudaMemcpyAsync(c->rn_tot, rn_tot0, sizeof rn_tot0, cudaMemcpyHostToDevice, s));
         c->cur = cur0;
         for (int k = 0; k < 6; ++k) CK(c, cudaMemcpyAsync(c->sol[cur0][k], save[k], sb, cudaMemcpyDeviceToDevice, s));
         CK(c, cudaMemcpyAsync(c->tag[cur0], stag, c->Nslots * 4, cudaMemcpyDeviceToDevice, s));
@@ -1488,6 +1498,7 @@ out:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->profiling = prof;
+    c->vacf.n_lags = vacf_lags0;
     if (st) return st;
     c->tune = best;
     build_tiles(c);

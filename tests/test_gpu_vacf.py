@@ -112,3 +112,27 @@ def test_vacf_arguments(B):
             sim.set_vacf(*bad)
         assert e.value.status == B.MPCD_ERR_ARG
     sim.close()
+
+
+def test_autotune_leaves_the_observables_alone(B):
+    """The autotuner's trial steps add neither to the exchange totals nor to
+    the autocorrelation sums."""
+    prm = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=9)
+    system = I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [(14, 16, 14)], 5.0, [[0, 0]], "tune",
+                            placement_seed=9)
+    sim = B.Simulation(system)
+    sim.set_state(I.initial_state(system))
+    sim.set_rnemd(y_a=0.0, y_b=8.0, width=1.0, v_target=0.5, max_pairs=20)
+    sim.set_vacf(4, 1)
+    sim.step(5)
+    t1 = sim.rnemd_totals()
+    c1 = sim.vacf()
+    sim.autotune(steps_per_trial=2)
+    assert sim.rnemd_totals() == t1
+    c2 = sim.vacf()
+    for u, w in zip(c1, c2):
+        assert np.array_equal(u, w)
+    sim.step(3)                        # sampling and exchanging resume
+    assert sim.rnemd_totals()[1] == t1[1] + 3 * 20
+    assert sim.vacf()[2][0] == c1[2][0] + 3
+    sim.close()
