@@ -48,6 +48,9 @@ def args_():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
+    ap.add_argument("--rule", default="srd", choices=["srd", "at"],
+                    help="collision rule of the workload: SRD with the cell thermostat (the benchmark) or "
+                         "MPCD-AT (for the ALU-side measurement of the Philox/Box-Muller path)")
     ap.add_argument("--no-protocols", action="store_true",
                     help="skip the transport-protocol measurements (momentum exchange, sedimentation, VACF)")
     return ap.parse_args()
@@ -297,8 +300,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     L = a.L
-    system = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1 + rank,
-                          name=WORKLOAD)
+    rule, thermo = (I.SRD, 1) if a.rule == "srd" else (I.AT, 0)
+    workload = WORKLOAD if a.rule == "srd" else WORKLOAD.replace("SRD130_thermostat", "MPCD-AT")
+    system = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, rule, thermo, I.P32, seed=1 + rank, name=workload)
     state = I.initial_state(system)
     n_upd = system.n_solvent + system.n_sites
 
@@ -340,7 +344,7 @@ def main():
     pk = prof[name]
     per_launch_ms = pk["total_ms"] / max(pk["launches"], 1)
     achieved = pk["bytes_per_launch"] / (per_launch_ms / 1e3) / 1e9
-    tr = recorded_traffic(name)
+    tr = recorded_traffic(name) if a.rule == "srd" else None   # the record is of the SRD pass
     traffic = None
     if tr is not None:
         traffic = float(tr["bytes_per_launch_per_particle"]) * system.n_solvent
@@ -395,7 +399,7 @@ def main():
     # ------------------------------------------------------ plain FP64 form
     p64 = None
     if not a.no_p64:
-        s64 = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P64, seed=1 + rank, name=WORKLOAD)
+        s64 = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, rule, thermo, I.P64, seed=1 + rank, name=workload)
         sim64 = Bd.Simulation(s64, device=local)
         sim64.set_state(state)
         k64 = max(3, a.steps // 5)
@@ -427,11 +431,12 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L, "density": 10, "phi": 0.3, "colloid_radius": 4.0,
+            "config": {"workload": workload, "L": L, "density": 10, "phi": 0.3, "colloid_radius": 4.0,
                        "n_solvent": system.n_solvent, "n_bodies": system.n_bodies,
                        "n_sites": system.n_sites, "n_cells": system.n_cells,
                        "form": "P32: FP32 state, int64 fixed-point cell sums, FP64 bodies",
-                       "rule": "SRD alpha=130 + cell-level thermostat", "dt": 0.1,
+                       "rule": ("SRD alpha=130 + cell-level thermostat" if a.rule == "srd"
+                                else "MPCD-AT (Andersen thermostat rule)"), "dt": 0.1,
                        "l2": "no flush: state per GPU (2.1 GB) is larger than L2 (129 MB)",
                        "tuning": tuning, "parallelism": f"replicas x{ws} (one box per GPU)"},
             "roofline": roof, "hbm_effective": hbm_eff, "kernels": kernels,

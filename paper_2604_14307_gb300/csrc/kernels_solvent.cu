@@ -253,7 +253,7 @@ __device__ __forceinline__ void bin4(const StepArgs &a, const Real (&x)[4], cons
     for (int j = 0; j < 4; ++j) {
         cc[j] = base + cell_axis(x[j], S[0], L0) + L0 * (cell_axis(y[j], S[1], L1) + L1 * cell_axis(z[j], S[2], L2));
         xi[j][0] = xi[j][1] = xi[j][2] = Real(0);
-        if (RULE == 1 && j < nv) {
+        if (RULE == 1) {   // for every slot, so that the four draws interleave; runs past nv are dropped
             normals3(draw(rr, step + (COLLIDE ? 1 : 0), tg[j], TAG_AT, 0u), xi[j]);
             xi[j][0] *= sc; xi[j][1] *= sc; xi[j][2] *= sc;
         }
@@ -583,17 +583,23 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
                     c = j < nv ? c : base;
                     p[j] = get_params<Real>(a.params, c);
                 }
+                Real nn[4][3];
+                if (RULE == 1) {
+                    // the four particles' Philox blocks are independent: draw
+                    // them all (a lane past the tile end draws for id 0), so
+                    // that their dependent rounds interleave
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn[j]);
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (j < nv && p[j].kappa >= Real(0)) {
                         if (RULE == 0) {
                             srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
                         } else {
-                            Real nn[3];
-                            normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn);
-                            vx[j] = p[j].ux + sc * nn[0] - p[j].ax;
-                            vy[j] = p[j].uy + sc * nn[1] - p[j].ay;
-                            vz[j] = p[j].uz + sc * nn[2] - p[j].az;
+                            vx[j] = p[j].ux + sc * nn[j][0] - p[j].ax;
+                            vy[j] = p[j].uy + sc * nn[j][1] - p[j].ay;
+                            vz[j] = p[j].uz + sc * nn[j][2] - p[j].az;
                         }
                     }
                 }
@@ -798,17 +804,23 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
                     c = j < nv ? c : base;
                     p[j] = get_params<Real>(a.params, c);
                 }
+                Real nn[4][3];
+                if (RULE == 1) {
+                    // the four particles' Philox blocks are independent: draw
+                    // them all (a lane past the tile end draws for id 0), so
+                    // that their dependent rounds interleave
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn[j]);
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (j < nv && p[j].kappa >= Real(0)) {
                         if (RULE == 0) {
                             srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
                         } else {
-                            Real nn[3];
-                            normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn);
-                            vx[j] = p[j].ux + sc * nn[0] - p[j].ax;
-                            vy[j] = p[j].uy + sc * nn[1] - p[j].ay;
-                            vz[j] = p[j].uz + sc * nn[2] - p[j].az;
+                            vx[j] = p[j].ux + sc * nn[j][0] - p[j].ax;
+                            vy[j] = p[j].uy + sc * nn[j][1] - p[j].ay;
+                            vz[j] = p[j].uz + sc * nn[j][2] - p[j].az;
                         }
                     }
                 }
@@ -860,9 +872,11 @@ constexpr int WT_STAGES = 3, WT_MAX_WARPS = 16;
 // registers leave 24 K of the SM's 64 K registers to the site/body kernels
 // that run beside this pass on the second stream (a cap of 96 left room for
 // one of their CTAs per SM, none without a cap; 72 and below spill in the
-// loop).  The AT form, with its Philox normals, keeps 96.
+// loop).  The AT form draws two Philox normals per particle and is latency-
+// bound on their rounds: it gains more from registers (ILP) than from the
+// overlap (L=200: 2.40 ms with 128, 2.69 with 112, 3.01 with 96).
 template <typename Real, int RULE> struct WtRegs {
-    static constexpr int n = sizeof(Real) == 4 ? (RULE == 0 ? 80 : 96) : 128;
+    static constexpr int n = sizeof(Real) == 4 && RULE == 0 ? 80 : 128;
 };
 
 template <typename Real, int RULE, int FLAGS>
@@ -1002,17 +1016,23 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
                     c = j < nv ? c : base;
                     p[j] = get_params<Real>(a.params, c);
                 }
+                Real nn[4][3];
+                if (RULE == 1) {
+                    // the four particles' Philox blocks are independent: draw
+                    // them all (a lane past the tile end draws for id 0), so
+                    // that their dependent rounds interleave
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn[j]);
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (j < nv && p[j].kappa >= Real(0)) {
                         if (RULE == 0) {
                             srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
                         } else {
-                            Real nn[3];
-                            normals3(draw(rr, step, tg[j], TAG_AT, 0u), nn);
-                            vx[j] = p[j].ux + sc * nn[0] - p[j].ax;
-                            vy[j] = p[j].uy + sc * nn[1] - p[j].ay;
-                            vz[j] = p[j].uz + sc * nn[2] - p[j].az;
+                            vx[j] = p[j].ux + sc * nn[j][0] - p[j].ax;
+                            vy[j] = p[j].uy + sc * nn[j][1] - p[j].ay;
+                            vz[j] = p[j].uz + sc * nn[j][2] - p[j].az;
                         }
                     }
                 }
