@@ -48,6 +48,13 @@ def args_():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
+    ap.add_argument("--workload", default="suspension",
+                    choices=["suspension", "single_sphere_L10", "suspension_L50", "batched_single_sphere",
+                             "batched_mixed_shapes", "phi_sweep_L120"],
+                    help="suspension: the benchmark (box --L, rule --rule); the others are the smaller and "
+                         "batched workloads and the paper-shaped phi sweep (--phi), for the record")
+    ap.add_argument("--phi", type=float, default=0.3, help="volume fraction of phi_sweep_L120")
+    ap.add_argument("--n-rep", type=int, default=0, help="replicas of the batched workloads (0: their default)")
     ap.add_argument("--rule", default="srd", choices=["srd", "at"],
                     help="collision rule of the workload: SRD with the cell thermostat (the benchmark) or "
                          "MPCD-AT (for the ALU-side measurement of the Philox/Box-Muller path)")
@@ -301,8 +308,30 @@ def main():
 
     L = a.L
     rule, thermo = (I.SRD, 1) if a.rule == "srd" else (I.AT, 0)
-    workload = WORKLOAD if a.rule == "srd" else WORKLOAD.replace("SRD130_thermostat", "MPCD-AT")
-    system = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, rule, thermo, I.P32, seed=1 + rank, name=workload)
+
+    def make_system(precision):
+        """The workload in the given arithmetic form (seeded per rank)."""
+        seed = 1 + rank
+        if a.workload == "single_sphere_L10":
+            return I.single_sphere_L10(precision, seed=seed), "single_sphere_L10_162sites_density5_SRD130"
+        if a.workload == "suspension_L50":
+            return I.suspension_L50(precision, seed=seed), "suspension_L50_phi0.2_r3_642sites_density5_MPCD-AT"
+        if a.workload == "batched_single_sphere":
+            n = a.n_rep or 4096
+            return (I.batched_single_sphere(n_rep=n, precision=precision, seed=seed),
+                    f"batched_{n}x_single_sphere_L12-24_162sites_density5_SRD130")
+        if a.workload == "batched_mixed_shapes":
+            n = a.n_rep or 256
+            return (I.batched_mixed_shapes(n_rep=n, precision=precision, seed=seed),
+                    f"batched_{n}x_mixed_shapes_L20-40_MPCD-AT")
+        if a.workload == "phi_sweep_L120":
+            name = f"suspension_L120_phi{a.phi:g}_d6_162sites_density5_SRD130_thermostat"
+            return I.suspension(120, 5.0, a.phi, 3.0, 2, 5.0, I.SRD, 1, precision, seed=seed, name=name), name
+        w = WORKLOAD if a.rule == "srd" else WORKLOAD.replace("SRD130_thermostat", "MPCD-AT")
+        return I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, rule, thermo, precision, seed=seed, name=w), w
+
+    system, workload = make_system(I.P32)
+    default_workload = a.workload == "suspension"
     state = I.initial_state(system)
     n_upd = system.n_solvent + system.n_sites
 
@@ -344,7 +373,7 @@ def main():
     pk = prof[name]
     per_launch_ms = pk["total_ms"] / max(pk["launches"], 1)
     achieved = pk["bytes_per_launch"] / (per_launch_ms / 1e3) / 1e9
-    tr = recorded_traffic(name) if a.rule == "srd" else None   # the record is of the SRD pass
+    tr = recorded_traffic(name) if (a.rule == "srd" and default_workload) else None   # the record is of the benchmark
     traffic = None
     if tr is not None:
         traffic = float(tr["bytes_per_launch_per_particle"]) * system.n_solvent
@@ -392,14 +421,15 @@ def main():
            "h2d_bytes_per_step": state_bytes / a.steps, "d2h_bytes_per_step": (state_bytes + 80) / a.steps,
            "how": "mpcd_set_state from pinned host + mpcd_step(steps) + mpcd_get_state to pinned host "
                   "+ mpcd_diagnostics, wall clock", "parts": e2e_parts}
-    bodyp = body_protocols(sim, stream) if (rank == 0 and not a.no_protocols) else {}
+    protocols_on = rank == 0 and not a.no_protocols and default_workload
+    bodyp = body_protocols(sim, stream) if protocols_on else {}
     sim.close()
     del hb
 
     # ------------------------------------------------------ plain FP64 form
     p64 = None
     if not a.no_p64:
-        s64 = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, rule, thermo, I.P64, seed=1 + rank, name=workload)
+        s64, _ = make_system(I.P64)
         sim64 = Bd.Simulation(s64, device=local)
         sim64.set_state(state)
         k64 = max(3, a.steps // 5)
@@ -418,27 +448,36 @@ def main():
     del state
 
     protocols = None
-    if rank == 0 and not a.no_protocols:
+    if protocols_on:
         protocols = {"rnemd": rnemd_protocol(Bd, I, stream, peaks()[0]), **bodyp}
 
     cpu = None
-    if rank == 0 and not a.no_cpu:
+    if rank == 0 and not a.no_cpu and default_workload:   # the oracle sample is of the benchmark composition
         cpu = cpu_baseline()
         cpu.pop("seconds", None)
 
+    state_bytes_dev = system.n_solvent * 28 + system.n_cells * 56
+    l2_note = ("no flush: state per GPU (%.1f GB) is larger than L2 (129 MB)" % (state_bytes_dev / 1e9)
+               if state_bytes_dev > 129e6 else
+               "no flush: the state fits in L2 (129 MB), so the bandwidth fraction is not meaningful")
+    rule_note = ("SRD alpha=130" + (" + cell-level thermostat" if system.params.thermostat else "")
+                 if system.params.rule == I.SRD else "MPCD-AT (Andersen thermostat rule)")
+    if default_workload:
+        config = {"workload": workload, "L": L, "density": 10, "phi": 0.3, "colloid_radius": 4.0}
+    else:
+        config = {"workload": workload, "n_replicas": system.n_rep}
+        if a.workload == "phi_sweep_L120":
+            config.update({"L": 120, "density": 5, "phi": a.phi, "colloid_radius": 3.0})
+    config.update({"n_solvent": system.n_solvent, "n_bodies": system.n_bodies, "n_sites": system.n_sites,
+                   "n_cells": system.n_cells, "form": "P32: FP32 state, int64 fixed-point cell sums, FP64 bodies",
+                   "rule": rule_note, "dt": 0.1, "l2": l2_note, "tuning": tuning,
+                   "parallelism": f"replicas x{ws} (one box per GPU)"})
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload, "L": L, "density": 10, "phi": 0.3, "colloid_radius": 4.0,
-                       "n_solvent": system.n_solvent, "n_bodies": system.n_bodies,
-                       "n_sites": system.n_sites, "n_cells": system.n_cells,
-                       "form": "P32: FP32 state, int64 fixed-point cell sums, FP64 bodies",
-                       "rule": ("SRD alpha=130 + cell-level thermostat" if a.rule == "srd"
-                                else "MPCD-AT (Andersen thermostat rule)"), "dt": 0.1,
-                       "l2": "no flush: state per GPU (2.1 GB) is larger than L2 (129 MB)",
-                       "tuning": tuning, "parallelism": f"replicas x{ws} (one box per GPU)"},
+            "config": config,
             "roofline": roof, "hbm_effective": hbm_eff, "kernels": kernels,
             "kernels_note": ("sites_post, body_impulse, body_md, body_force and the next step's sites_pre run "
                              "on a second stream beside solvent_fused; their event spans include shared time"),

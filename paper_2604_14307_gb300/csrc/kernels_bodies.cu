@@ -199,40 +199,72 @@ __device__ __forceinline__ void min_image(double d[3], const int32_t L[3])
     }
 }
 
-// Forces on body i are summed by lane (j - first) mod 32 in ascending j, then
-// by a fixed shuffle tree, whichever path enumerates the candidates, so the
-// result depends only on the set of interacting pairs.
-__device__ __forceinline__ void pair_force(const StepArgs &a, const DevBody &bi, const DevShape &si,
-                                           const double Qi[9], int64_t j, const DevReplica &r,
-                                           double F[3], double T[3])
+// Rotated WCA centres of every body, Q c in the space frame, once per pose (in
+// FP64 and rounded to float), so that the pair loop below only adds offsets.
+__global__ void k_body_centres(StepArgs a)
 {
-    const double rc_extra = 1.122462048309373;   // 2^(1/6) sigma
-    const DevBody bj = a.bodies[j];
-    const DevShape sj = a.shapes[bj.shape];
-    const double dij = 0.5 * (si.wca_d + sj.wca_d);
-    const double delta = dij - 1.0, rcut = delta + rc_extra;
-    double Qj[9];
-    rotmat(bj.q, Qj);
-    for (int ca = 0; ca < si.n_cent; ++ca) {
-        double c_a[3];
-        mv(Qi, a.tcent + 3 * (si.cent_begin + ca), c_a);
-        for (int cc = 0; cc < sj.n_cent; ++cc) {
-            double c_c[3], dv[3];
-            mv(Qj, a.tcent + 3 * (sj.cent_begin + cc), c_c);
-            for (int k = 0; k < 3; ++k) dv[k] = (bi.R[k] + c_a[k]) - (bj.R[k] + c_c[k]);
-            min_image(dv, r.L);
-            double rr = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-            if (rr > rcut) continue;
-            double s = 1.0 / (rr - delta);
-            double s6 = s * s * s * s * s * s;
-            double fm = 4.0 * (12.0 * s6 * s6 - 6.0 * s6) / (rr - delta);
-            double f[3] = {fm * dv[0] / rr, fm * dv[1] / rr, fm * dv[2] / rr};
-            F[0] += f[0]; F[1] += f[1]; F[2] += f[2];
-            T[0] += c_a[1] * f[2] - c_a[2] * f[1];
-            T[1] += c_a[2] * f[0] - c_a[0] * f[2];
-            T[2] += c_a[0] * f[1] - c_a[1] * f[0];
-        }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bodies) return;
+    const DevBody &b = a.bodies[i];
+    const DevShape &sh = a.shapes[b.shape];
+    double Q[9];
+    rotmat(b.q, Q);
+    for (int c = 0; c < sh.n_cent; ++c) {
+        double d[3];
+        mv(Q, a.tcent + 3 * (sh.cent_begin + c), d);
+        const int64_t g = b.cent_begin + c;
+        for (int k = 0; k < 3; ++k) a.cent64[3 * g + k] = d[k];
+        a.cent32[g] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.0f);
     }
+}
+
+template <typename Real> struct CentreOf;
+template <> struct CentreOf<float> {
+    __device__ static void get(const StepArgs &a, int64_t g, float c[3])
+    {
+        const float4 v = a.cent32[g];
+        c[0] = v.x; c[1] = v.y; c[2] = v.z;
+    }
+};
+template <> struct CentreOf<double> {
+    __device__ static void get(const StepArgs &a, int64_t g, double c[3])
+    {
+        c[0] = a.cent64[3 * g]; c[1] = a.cent64[3 * g + 1]; c[2] = a.cent64[3 * g + 2];
+    }
+};
+
+// WCA force (Eq. 1) between centre ca of body i and centre cc of body j, added
+// to F and the torque c_a x f to T.  The centre-pair vector
+// (R_i + c_a) - (R_j + c_c) takes its own minimum image.  Real = float for the
+// P32 form (R_i - R_j formed in FP64, then the pair arithmetic in FP32), double
+// for the P64 form; F and T accumulate in FP64.
+template <typename Real>
+__device__ __forceinline__ void centre_pair(const StepArgs &a, const DevBody &bi, const DevShape &si, int ca,
+                                            const DevBody &bj, const DevShape &sj, int cc, const DevReplica &r,
+                                            double F[3], double T[3])
+{
+    const Real rc_extra = Real(1.122462048309373);   // 2^(1/6) sigma
+    const Real dij = Real(0.5 * (si.wca_d + sj.wca_d));
+    const Real delta = dij - Real(1), rcut = delta + rc_extra;
+    Real c_a[3], c_c[3], dv[3];
+    CentreOf<Real>::get(a, bi.cent_begin + ca, c_a);
+    CentreOf<Real>::get(a, bj.cent_begin + cc, c_c);
+    for (int k = 0; k < 3; ++k) {
+        dv[k] = (Real)(bi.R[k] - bj.R[k]) + (c_a[k] - c_c[k]);
+        const Real L = (Real)r.L[k], h = Real(0.5) * L;
+        if (dv[k] > h) dv[k] -= L;
+        else if (dv[k] < -h) dv[k] += L;
+    }
+    const Real rr = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    if (!(rr <= rcut)) return;
+    const Real sdl = Real(1) / (rr - delta);
+    const Real s6 = sdl * sdl * sdl * sdl * sdl * sdl;
+    const Real fm = Real(4) * (Real(12) * s6 * s6 - Real(6) * s6) / (rr - delta);
+    const double f[3] = {(double)(fm * dv[0] / rr), (double)(fm * dv[1] / rr), (double)(fm * dv[2] / rr)};
+    F[0] += f[0]; F[1] += f[1]; F[2] += f[2];
+    T[0] += (double)c_a[1] * f[2] - (double)c_a[2] * f[1];
+    T[1] += (double)c_a[2] * f[0] - (double)c_a[0] * f[2];
+    T[2] += (double)c_a[0] * f[1] - (double)c_a[1] * f[0];
 }
 
 __device__ __forceinline__ bool may_interact(const StepArgs &a, const float4 &pi, const float4 &pj,
@@ -274,32 +306,56 @@ __global__ void k_nlist_build(StepArgs a)
     }
 }
 
-// One thread per body: FP64 forces summed over the candidates in ascending j
-// (the list, or every body when the list overflowed - the same result), the
-// second half kick, and the pose record the site kernels read.
-__global__ void k_body_force(StepArgs a, int kick)
+// One warp per body: the lanes take the (neighbour, centre, centre) triples
+// of the body's candidates in turn, each lane summing its triples in order,
+// and a fixed shuffle tree adds the lanes, so the result depends only on the
+// candidate list.  Then the second half kick and the pose record the site
+// kernels read (lane 0, FP64).
+template <typename Real>
+__global__ void __launch_bounds__(128) k_body_force(StepArgs a, int kick)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_bodies) return;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= a.n_bodies) return;   // uniform over the warp
     const DevBody bi = a.bodies[i];
     const DevShape si = a.shapes[bi.shape];
     const DevReplica r = a.reps[bi.rep];
-    double Qi[9];
-    rotmat(bi.q, Qi);
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
     const int n = a.ncount[i];
+    const int nci = si.n_cent, maxc = max(a.max_cent, 1);
     if (n >= 0 && n <= NLIST_MAX) {
-        for (int e = 0; e < n; ++e) {
-            const int64_t j = a.nlist[(int64_t)i * NLIST_MAX + e];
-            if (j >= r.body_begin && j < r.body_end) pair_force(a, bi, si, Qi, j, r, F, T);
+        const int per = nci * maxc;
+        for (int t = lane; t < n * per; t += 32) {
+            const int e = t / per, rem = t - e * per, ca = rem / maxc, cc = rem - ca * maxc;
+            const int64_t j = a.nlist[i * NLIST_MAX + e];
+            if (j < r.body_begin || j >= r.body_end) continue;
+            const DevBody &bj = a.bodies[j];
+            const DevShape &sj = a.shapes[bj.shape];
+            if (cc < sj.n_cent) centre_pair<Real>(a, bi, si, ca, bj, sj, cc, r, F, T);
         }
     } else {
+        // the list overflowed: every body of the replica, prefiltered
         const float4 pi = a.bpos[i];
         const float reach = (float)(0.5 * (si.wca_d + a.max_wca_d) - 1.0 + 1.122462048309373) + 1e-2f;
-        for (int64_t j = r.body_begin; j < r.body_end; ++j)
-            if (j != i && may_interact(a, pi, a.bpos[j], r, reach)) pair_force(a, bi, si, Qi, j, r, F, T);
+        for (int64_t j = r.body_begin + lane; j < r.body_end; j += 32) {
+            if (j == i || !may_interact(a, pi, a.bpos[j], r, reach)) continue;
+            const DevBody &bj = a.bodies[j];
+            const DevShape &sj = a.shapes[bj.shape];
+            for (int ca = 0; ca < nci; ++ca)
+                for (int cc = 0; cc < sj.n_cent; ++cc) centre_pair<Real>(a, bi, si, ca, bj, sj, cc, r, F, T);
+        }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            F[k] += __shfl_down_sync(0xffffffffu, F[k], o);
+            T[k] += __shfl_down_sync(0xffffffffu, T[k], o);
+        }
+    if (lane != 0) return;
     for (int k = 0; k < 3; ++k) F[k] += a.fext[k];   // external force at the centre of mass (no torque)
+    double Qi[9];
+    rotmat(bi.q, Qi);
     DevBody *o = a.bodies + i;
     double P[3] = {bi.P[0], bi.P[1], bi.P[2]}, L[3] = {bi.Lm[0], bi.Lm[1], bi.Lm[2]};
     for (int k = 0; k < 3; ++k) { o->F[k] = F[k]; o->T[k] = T[k]; }
@@ -317,8 +373,8 @@ __global__ void k_body_force(StepArgs a, int kick)
     mtv(Qi, L, Lb);
     for (int k = 0; k < 3; ++k) wb[k] = si.Ihat[k] > 0.0 ? Lb[k] / si.Ihat[k] : 0.0;
     mv(Qi, wb, W);
-    double *p64 = a.pose64 + (int64_t)i * POSE_W;
-    float *p32 = a.pose32 + (int64_t)i * POSE_W;
+    double *p64 = a.pose64 + i * POSE_W;
+    float *p32 = a.pose32 + i * POSE_W;
     for (int k = 0; k < 9; ++k) { p64[k] = Qi[k]; p32[k] = (float)Qi[k]; }
     for (int k = 0; k < 3; ++k) {
         p64[9 + k] = bi.R[k]; p32[9 + k] = (float)bi.R[k];
@@ -332,9 +388,12 @@ void launch_body_force(const StepArgs &a, int kick, cudaStream_t s)
 {
     if (a.n_bodies == 0) return;
     if (!kick) k_body_pos<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
+    k_body_centres<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
     const int wpb = 4;
     k_nlist_build<<<(a.n_bodies + wpb - 1) / wpb, 32 * wpb, 0, s>>>(a);
-    k_body_force<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a, kick);
+    const unsigned grid = (unsigned)((a.n_bodies + wpb - 1) / wpb);
+    if (a.precision == 1) k_body_force<float><<<grid, 32 * wpb, 0, s>>>(a, kick);
+    else k_body_force<double><<<grid, 32 * wpb, 0, s>>>(a, kick);
 }
 
 // ---------------------------------------------------------------- sites

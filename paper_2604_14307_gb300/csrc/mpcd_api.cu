@@ -71,6 +71,10 @@ struct mpcd_ctx {
     double *d_pose64 = nullptr;
     void *d_partial = nullptr;
     double *d_tb = nullptr, *d_tm = nullptr, *d_tcent = nullptr;
+    double *d_cent64 = nullptr;                 // rotated WCA centres of every body
+    float4 *d_cent32 = nullptr;
+    int64_t n_cent_bodies = 0;                  // WCA centres over all bodies
+    int max_cent = 0;                           // most centres of any shape
     float *d_tbf = nullptr, *d_tmf = nullptr;
     void *sol[2][6] = {};
     uint32_t *tag[2] = {nullptr, nullptr};
@@ -220,6 +224,9 @@ StepArgs make_args(const mpcd_ctx *c)
     a.tmf = c->d_tmf;
     a.tcent = c->d_tcent;
     a.max_wca_d = c->max_wca_d;
+    a.max_cent = c->max_cent;
+    a.cent64 = c->d_cent64;
+    a.cent32 = c->d_cent32;
     a.site_v = c->site_v;
     a.site_cell = c->site_cell;
     a.n_sites = c->Nsite;
@@ -666,6 +673,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
         S.bound = bound;
         c->max_sites = std::max(c->max_sites, d.n_sites);
         c->max_wca_d = std::max(c->max_wca_d, d.wca_d);
+        c->max_cent = std::max(c->max_cent, d.n_centres);
         c->shapes.push_back(S);
     }
 
@@ -764,6 +772,12 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     ok &= (c->d_tm = (double *)A(std::max<size_t>(1, tm.size()) * 8)) != nullptr;
     ok &= (c->d_tmf = (float *)A(std::max<size_t>(1, tm.size()) * 4)) != nullptr;
     ok &= (c->d_tcent = (double *)A(std::max<size_t>(1, tcent.size()) * 8)) != nullptr;
+    {
+        int64_t nc = 0;
+        for (int64_t b = 0; b < c->B; ++b) nc += c->shapes[body_shape[b]].n_cent;
+        ok &= (c->d_cent64 = (double *)A((size_t)std::max<int64_t>(1, nc) * 3 * 8)) != nullptr;
+        ok &= (c->d_cent32 = (float4 *)A((size_t)std::max<int64_t>(1, nc) * sizeof(float4))) != nullptr;
+    }
     ok &= (c->site_v = A(std::max<int64_t>(1, c->Nsite) * 3 * c->realsz)) != nullptr;
     ok &= (c->site_cell = (int32_t *)A(std::max<int64_t>(1, c->Nsite) * 4)) != nullptr;
     ok &= (c->d_step = (int64_t *)A(8)) != nullptr;
@@ -785,7 +799,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     std::vector<float> tbf(tb.begin(), tb.end()), tmf(tm.begin(), tm.end());
     std::vector<DevBody> hb(std::max<int64_t>(1, c->B));
     {
-        int64_t site = 0, bi = 0;
+        int64_t site = 0, cent = 0, bi = 0;
         for (int r = 0; r < n_replicas; ++r)
             for (int b = 0; b < replicas[r].n_bodies; ++b, ++bi) {
                 DevBody &B = hb[bi];
@@ -794,8 +808,11 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
                 B.shape = body_shape[bi];
                 B.rep = r;
                 B.site_begin = site;
+                B.cent_begin = cent;
                 site += c->shapes[B.shape].n_sites;
+                cent += c->shapes[B.shape].n_cent;
             }
+        c->n_cent_bodies = cent;
     }
     int st = MPCD_OK;
     auto H2D = [&](void *d, const void *h, size_t n) {

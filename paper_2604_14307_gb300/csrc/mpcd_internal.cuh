@@ -72,6 +72,7 @@ struct DevBody {
     double D[3];            // displacement since mpcd_set_state, unwrapped (diffusion)
     int32_t shape, rep;
     int64_t site_begin;     // global index of the body's first site
+    int64_t cent_begin;     // global index of the body's first WCA centre (rotated-centre buffers)
 };
 
 // Arguments shared by every kernel of a step (passed by value).
@@ -111,6 +112,9 @@ struct StepArgs {
     const float *tmf;
     const double *tcent;            // WCA centres [centres][3]
     double max_wca_d;               // largest centre diameter of any shape
+    int32_t max_cent;               // most WCA centres of any shape
+    double *cent64;                 // per body centre: Q c in the space frame [n][3] (this step's pose)
+    float4 *cent32;                 // the same rounded to float
     void *site_v;                   // [3][n_sites] SoA
     int32_t *site_cell;             // replica-local cell of each site
     int64_t n_sites;
