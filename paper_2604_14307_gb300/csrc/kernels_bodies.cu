@@ -306,13 +306,83 @@ __global__ void k_nlist_build(StepArgs a)
     }
 }
 
-// One warp per body: the lanes take the (neighbour, centre, centre) triples
-// of the body's candidates in turn, each lane summing its triples in order,
-// and a fixed shuffle tree adds the lanes, so the result depends only on the
-// candidate list.  Then the second half kick and the pose record the site
-// kernels read (lane 0, FP64).
+// Forces done: external force, stored F and T, the second half kick (kick)
+// and the pose record the site kernels read (FP64).
+__device__ __forceinline__ void body_force_finish(const StepArgs &a, int64_t i, const DevBody &bi, const DevShape &si,
+                                                  double F[3], const double T[3], int kick)
+{
+    for (int k = 0; k < 3; ++k) F[k] += a.fext[k];   // external force at the centre of mass (no torque)
+    double Qi[9];
+    rotmat(bi.q, Qi);
+    DevBody *o = a.bodies + i;
+    double P[3] = {bi.P[0], bi.P[1], bi.P[2]}, L[3] = {bi.Lm[0], bi.Lm[1], bi.Lm[2]};
+    for (int k = 0; k < 3; ++k) { o->F[k] = F[k]; o->T[k] = T[k]; }
+    if (kick) {
+        double p[4];
+        L_to_p(bi.q, L, p);
+        for (int k = 0; k < 3; ++k) P[k] = bi.P[k] + 0.5 * a.dt * F[k];
+        torque_kick(bi.q, p, T, 0.5 * a.dt);
+        p_to_L(bi.q, p, L);
+        for (int k = 0; k < 3; ++k) { o->P[k] = P[k]; o->Lm[k] = L[k]; }
+    }
+    // pose: Q, R, V = P/M, omega = Q Ihat^-1 Q^T L (Eq. 5)
+    double V[3], Lb[3], wb[3], W[3];
+    for (int k = 0; k < 3; ++k) V[k] = P[k] / si.M;
+    mtv(Qi, L, Lb);
+    for (int k = 0; k < 3; ++k) wb[k] = si.Ihat[k] > 0.0 ? Lb[k] / si.Ihat[k] : 0.0;
+    mv(Qi, wb, W);
+    double *p64 = a.pose64 + i * POSE_W;
+    float *p32 = a.pose32 + i * POSE_W;
+    for (int k = 0; k < 9; ++k) { p64[k] = Qi[k]; p32[k] = (float)Qi[k]; }
+    for (int k = 0; k < 3; ++k) {
+        p64[9 + k] = bi.R[k]; p32[9 + k] = (float)bi.R[k];
+        p64[12 + k] = V[k]; p32[12 + k] = (float)V[k];
+        p64[15 + k] = W[k]; p32[15 + k] = (float)W[k];
+    }
+    if (i == 0) *a.nl_dirty = 0;   // the lists used by this step are fresh
+}
+
+// One thread per body (shapes of one or two centres): the candidates in
+// ascending order, each centre pair in turn.
 template <typename Real>
 __global__ void __launch_bounds__(128) k_body_force(StepArgs a, int kick)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_bodies) return;
+    const DevBody bi = a.bodies[i];
+    const DevShape si = a.shapes[bi.shape];
+    const DevReplica r = a.reps[bi.rep];
+    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    const int n = a.ncount[i];
+    if (n >= 0 && n <= NLIST_MAX) {
+        for (int e = 0; e < n; ++e) {
+            const int64_t j = a.nlist[i * NLIST_MAX + e];
+            if (j < r.body_begin || j >= r.body_end) continue;
+            const DevBody &bj = a.bodies[j];
+            const DevShape &sj = a.shapes[bj.shape];
+            for (int ca = 0; ca < si.n_cent; ++ca)
+                for (int cc = 0; cc < sj.n_cent; ++cc) centre_pair<Real>(a, bi, si, ca, bj, sj, cc, r, F, T);
+        }
+    } else {
+        const float4 pi = a.bpos[i];
+        const float reach = (float)(0.5 * (si.wca_d + a.max_wca_d) - 1.0 + 1.122462048309373) + 1e-2f;
+        for (int64_t j = r.body_begin; j < r.body_end; ++j) {
+            if (j == i || !may_interact(a, pi, a.bpos[j], r, reach)) continue;
+            const DevBody &bj = a.bodies[j];
+            const DevShape &sj = a.shapes[bj.shape];
+            for (int ca = 0; ca < si.n_cent; ++ca)
+                for (int cc = 0; cc < sj.n_cent; ++cc) centre_pair<Real>(a, bi, si, ca, bj, sj, cc, r, F, T);
+        }
+    }
+    body_force_finish(a, i, bi, si, F, T, kick);
+}
+
+// One warp per body (shapes with many centres, e.g. rods): the lanes take the
+// (neighbour, centre, centre) triples of the body's candidates in turn, each
+// lane summing its triples in order, and a fixed shuffle tree adds the lanes,
+// so the result depends only on the candidate list.
+template <typename Real>
+__global__ void __launch_bounds__(128) k_body_force_warp(StepArgs a, int kick)
 {
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -352,36 +422,7 @@ __global__ void __launch_bounds__(128) k_body_force(StepArgs a, int kick)
             F[k] += __shfl_down_sync(0xffffffffu, F[k], o);
             T[k] += __shfl_down_sync(0xffffffffu, T[k], o);
         }
-    if (lane != 0) return;
-    for (int k = 0; k < 3; ++k) F[k] += a.fext[k];   // external force at the centre of mass (no torque)
-    double Qi[9];
-    rotmat(bi.q, Qi);
-    DevBody *o = a.bodies + i;
-    double P[3] = {bi.P[0], bi.P[1], bi.P[2]}, L[3] = {bi.Lm[0], bi.Lm[1], bi.Lm[2]};
-    for (int k = 0; k < 3; ++k) { o->F[k] = F[k]; o->T[k] = T[k]; }
-    if (kick) {
-        double p[4];
-        L_to_p(bi.q, L, p);
-        for (int k = 0; k < 3; ++k) P[k] = bi.P[k] + 0.5 * a.dt * F[k];
-        torque_kick(bi.q, p, T, 0.5 * a.dt);
-        p_to_L(bi.q, p, L);
-        for (int k = 0; k < 3; ++k) { o->P[k] = P[k]; o->Lm[k] = L[k]; }
-    }
-    // pose: Q, R, V = P/M, omega = Q Ihat^-1 Q^T L (Eq. 5)
-    double V[3], Lb[3], wb[3], W[3];
-    for (int k = 0; k < 3; ++k) V[k] = P[k] / si.M;
-    mtv(Qi, L, Lb);
-    for (int k = 0; k < 3; ++k) wb[k] = si.Ihat[k] > 0.0 ? Lb[k] / si.Ihat[k] : 0.0;
-    mv(Qi, wb, W);
-    double *p64 = a.pose64 + i * POSE_W;
-    float *p32 = a.pose32 + i * POSE_W;
-    for (int k = 0; k < 9; ++k) { p64[k] = Qi[k]; p32[k] = (float)Qi[k]; }
-    for (int k = 0; k < 3; ++k) {
-        p64[9 + k] = bi.R[k]; p32[9 + k] = (float)bi.R[k];
-        p64[12 + k] = V[k]; p32[12 + k] = (float)V[k];
-        p64[15 + k] = W[k]; p32[15 + k] = (float)W[k];
-    }
-    if (i == 0) *a.nl_dirty = 0;   // the lists used by this step are fresh
+    if (lane == 0) body_force_finish(a, i, bi, si, F, T, kick);
 }
 
 void launch_body_force(const StepArgs &a, int kick, cudaStream_t s)
@@ -391,9 +432,15 @@ void launch_body_force(const StepArgs &a, int kick, cudaStream_t s)
     k_body_centres<<<(a.n_bodies + 127) / 128, 128, 0, s>>>(a);
     const int wpb = 4;
     k_nlist_build<<<(a.n_bodies + wpb - 1) / wpb, 32 * wpb, 0, s>>>(a);
-    const unsigned grid = (unsigned)((a.n_bodies + wpb - 1) / wpb);
-    if (a.precision == 1) k_body_force<float><<<grid, 32 * wpb, 0, s>>>(a, kick);
-    else k_body_force<double><<<grid, 32 * wpb, 0, s>>>(a, kick);
+    if (a.max_cent <= 2) {   // spheres, dumbbells: one thread per body
+        const unsigned grid = (unsigned)((a.n_bodies + 127) / 128);
+        if (a.precision == 1) k_body_force<float><<<grid, 128, 0, s>>>(a, kick);
+        else k_body_force<double><<<grid, 128, 0, s>>>(a, kick);
+    } else {                 // many centres: one warp per body
+        const unsigned grid = (unsigned)((a.n_bodies + wpb - 1) / wpb);
+        if (a.precision == 1) k_body_force_warp<float><<<grid, 32 * wpb, 0, s>>>(a, kick);
+        else k_body_force_warp<double><<<grid, 32 * wpb, 0, s>>>(a, kick);
+    }
 }
 
 // ---------------------------------------------------------------- sites
