@@ -4,9 +4,14 @@
 //               al. NO_SQUISH free-rotor sequence 3-2-1-2-3 for q and its
 //               conjugate momentum p = 2 q (x) (0, L_body), formed from the
 //               stored space-frame L and converted back; one thread per body.
+// k_body_centres the space-frame offsets Q c of every WCA centre, once per pose.
 // k_body_force  core-shifted WCA (Eq. 1) between the centres of different
-//               bodies of a replica, with torques; one warp per body, FP32
-//               bounding-sphere prefilter, FP64 forces; optional second kick.
+//               bodies of a replica, with torques, over Verlet neighbour lists
+//               (FP32 bounding-sphere prefilter); one thread per body for
+//               shapes of one or two centres, one warp per body otherwise;
+//               the pair arithmetic in the form's precision (FP32 for P32),
+//               forces and torques summed in FP64; optional second kick.
+// k_vacf_sample per-body velocity autocorrelation sums (Sec. III.A).
 // k_sites_pre   one CTA per body: site positions from the pose, Maxwell-
 //               Boltzmann draws, per-body mean velocity and angular velocity of
 //               the draws, thermalised site velocity of Eq. 7, binning of the
@@ -17,7 +22,7 @@
 //               the sites are reset to rigid motion (Eq. 5) implicitly, since
 //               the next step recomputes them from P and L.
 // This file is compiled without fused multiply-add so that the FP64 body and
-// site-position arithmetic rounds the same way as the reference oracle.
+// site-position arithmetic rounds the same way as the oracle.
 #include "mpcd_internal.cuh"
 
 namespace mpcd {
