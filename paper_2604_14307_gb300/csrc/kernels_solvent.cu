@@ -16,6 +16,13 @@
 // re-sort     counting sort of the solvent by cell (histogram, scan, scatter,
 //             optional per-cell order by tag) for memory locality; it changes
 //             no result.
+// The solvent pass has four launch forms that give bit-identical results:
+// direct loads (k_solvent), a CTA-wide two-stage bulk-copy ring
+// (k_solvent_staged), a warp-specialised three-stage ring (k_solvent_ws) and a
+// three-stage ring per warp (k_solvent_wt).  Streaming takes an optional
+// constant force (the balancing force of the sedimentation protocol).
+// Transport protocols of Sec. III.B: the reverse non-equilibrium exchange
+// (k_rnemd_scan, k_rnemd_filter, k_rnemd_select) and the velocity profile.
 #include <map>
 #include <mutex>
 #include <utility>

@@ -12,9 +12,14 @@
 //             `params`: one record per cell (32 B for P32, 64 B for P64):
 //                       u, kappa (< 0 marks a cell that does not collide),
 //                       and the SRD axis or the AT mean noise.
-//   bodies    one FP64 record per body (R, q, P, L, F, T).
+//   bodies    one FP64 record per body (R, q, P, L, F, T, unwrapped
+//             displacement D); the space-frame offsets of every WCA centre
+//             (FP64 and float copies), recomputed once per pose.
 //   sites     thermalised velocity (3 x Real SoA) and cell of every site,
 //             written by the PRE coupling and read by the POST coupling.
+//   protocols (allocated on first use) the exchange's key histogram, member
+//             lists and candidates; the velocity-profile sums; the per-body
+//             autocorrelation rings and sums.
 #pragma once
 
 #include <cuda_runtime.h>
