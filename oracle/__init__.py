@@ -49,7 +49,7 @@ class _Sys(C.Structure):
                 ("body_off", C.c_void_p), ("n_shapes", C.c_int32), ("site_off", C.c_void_p),
                 ("b", C.c_void_p), ("m", C.c_void_p), ("cent_off", C.c_void_p),
                 ("cent", C.c_void_p), ("wca_d", C.c_void_p), ("body_shape", C.c_void_p),
-                ("stream_id", C.c_void_p), ("f_ext", C.c_void_p)]
+                ("stream_id", C.c_void_p), ("f_ext", C.c_void_p), ("angular", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -60,7 +60,7 @@ class _State(C.Structure):
 
 _TRACE_FIELDS = ["shift", "cell_solvent", "cell_site", "site_r", "site_v", "site_vpost",
                  "fixed", "sums", "cell_u", "cell_axis", "cell_kappa", "cell_xibar",
-                 "order", "cell_start", "dP", "dL"]
+                 "order", "cell_start", "dP", "dL", "cell_omega"]
 
 
 class _Trace(C.Structure):
@@ -116,7 +116,7 @@ class OracleSystem:
             self.body_shape = np.zeros(1, dtype=np.int32)
         vals = dict(kT=p.kT, dt=p.dt, alpha_deg=p.alpha_deg, m_solvent=p.m_solvent,
                     rule=p.rule, thermostat=p.thermostat, precision=p.precision,
-                    naive_transfer=p.naive_transfer, seed=p.seed)
+                    naive_transfer=p.naive_transfer, seed=p.seed, angular=getattr(p, "angular", 0))
         vals.update(overrides)
         self.params = vals
         self.c = _Sys(vals["kT"], vals["dt"], vals["alpha_deg"], vals["m_solvent"],
@@ -125,7 +125,7 @@ class OracleSystem:
                       _ptr(self.solv_off), _ptr(self.body_off), len(system.shapes),
                       _ptr(self.site_off), _ptr(self.b), _ptr(self.m), _ptr(self.cent_off),
                       _ptr(self.cent), _ptr(self.wca_d), _ptr(self.body_shape),
-                      _ptr(self.stream_id), None)
+                      _ptr(self.stream_id), None, vals["angular"])
         self.f_ext = None
         self.n_solvent = int(self.solv_off[-1])
         self.n_bodies = int(self.body_off[-1])
@@ -210,7 +210,8 @@ def collide(osys: OracleSystem, st: OracleState, trace: bool = True) -> dict:
                       cell_u=((Ct, 3), np.float64), cell_axis=((Ct, 3), np.float64),
                       cell_kappa=((Ct,), np.float64), cell_xibar=((Ct, 3), np.float64),
                       order=((Ns + Nsite,), np.int64), cell_start=((Ct + 1,), np.int64),
-                      dP=((max(B, 1), 3), np.float64), dL=((max(B, 1), 3), np.float64))
+                      dP=((max(B, 1), 3), np.float64), dL=((max(B, 1), 3), np.float64),
+                      cell_omega=((Ct, 3), np.float64))
         for k, (shp, dt) in shapes.items():
             a = np.zeros(shp, dtype=dt)
             if a.size == 0:

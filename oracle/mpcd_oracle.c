@@ -35,7 +35,16 @@
  *   massless and do not collide;
  *   sedimentation (Sec. III.B): the body force acts at the centre of mass (the
  *   centre site of a sphere, so no torque) and is balanced by an equal share
- *   on every solvent particle of the replica.
+ *   on every solvent particle of the replica;
+ *   angular-momentum-conserving variants (SRD+a, MPCD-AT+a; the modification
+ *   Sec. II.A cites from Noguchi and Gompper): after the rule has produced v*,
+ *   every colliding cell gets the rigid rotation v' = v* + w x r_c that gives
+ *   back the angular momentum about the cell's centre of mass, with
+ *   Pi w = sum m r_c x (v - v*) and Pi the cell's inertia tensor about that
+ *   centre (its pseudo-inverse when the members are collinear, e.g. two
+ *   particles); r_c is measured on the 2^-20 lattice of the binning rule
+ *   (the fractional part of (X - S) 2^-20), and the thermostat, if any, acts
+ *   in the rule before the correction.
  */
 #include <math.h>
 #include <stdint.h>
@@ -72,6 +81,7 @@ typedef struct {
                                   mass, balanced by -B f / N_s on every solvent
                                   particle of its replica (Sec. III.B
                                   sedimentation); NULL: none */
+    int32_t angular;           /* 1: angular-momentum-conserving variant of the rule */
 } orc_sys;
 
 typedef struct {
@@ -101,6 +111,7 @@ typedef struct {
     int64_t *cell_start;   /* [Ctot + 1] */
     double *dP;            /* [B][3] momentum transferred to each body */
     double *dL;            /* [B][3] angular momentum transferred */
+    double *cell_omega;    /* [Ctot][3] angular-momentum correction w (+a variants) */
 } orc_trace;
 
 /* ------------------------------------------------------------------ */
@@ -240,6 +251,96 @@ static int64_t local_cell(const double r[3], const int32_t S[3], const int32_t L
     int64_t cy = orc_cell_axis(r[1], S[1], L[1]);
     int64_t cz = orc_cell_axis(r[2], S[2], L[2]);
     return cx + (int64_t)L[0] * (cy + (int64_t)L[1] * cz);
+}
+
+/* position of a stored coordinate x inside its shifted cell, in [0, 1): the
+ * fractional part of (X - S) 2^-20 with X = floor(x 2^20) (the binning rule) */
+static double cell_offset(double x, int32_t S)
+{
+    const int64_t D = 1048576; /* 2^20 */
+    int64_t t = (int64_t)floor(x * 1048576.0) - (int64_t)S;
+    int64_t c = t / D;
+    if (t % D != 0 && t < 0) c -= 1;
+    return (double)(t - c * D) * 0x1p-20;
+}
+
+/* eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
+ * (Golub and Van Loan, Sec. 8.5): A = V diag(lam) V^T, columns of V */
+static void sym_eig3(const double A0[3][3], double lam[3], double V[3][3])
+{
+    double A[3][3];
+    memcpy(A, A0, sizeof A);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) V[a][b] = (a == b);
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+        double scale = fabs(A[0][0]) + fabs(A[1][1]) + fabs(A[2][2]);
+        if (off <= 1e-300 || off <= 1e-18 * scale) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0) continue;
+                /* rotation in the (p, q) plane that zeroes A[p][q] */
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 3; ++k) {      /* A <- A J */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {      /* A <- J^T A */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {      /* V <- V J */
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int a = 0; a < 3; ++a) lam[a] = A[a][a];
+}
+
+/* The +a correction of one cell of n members (masses m, lattice positions q
+ * inside the cell, velocities v before and o after the rule): o += w x r_c
+ * with w the least-norm solution of Pi w = sum m r_c x (v - o).  Eigenvalues
+ * of Pi below 1e-12 of the largest count as zero (collinear members). */
+static void angular_correction(int64_t n, const double *m, const double *q, const double *v, double *o,
+                               double w_out[3])
+{
+    double M = 0, Qc[3] = { 0, 0, 0 };
+    for (int64_t i = 0; i < n; ++i) {
+        M += m[i];
+        for (int a = 0; a < 3; ++a) Qc[a] += m[i] * q[3 * i + a];
+    }
+    for (int a = 0; a < 3; ++a) Qc[a] /= M;
+    double Pi[3][3] = { { 0 } }, dL[3] = { 0, 0, 0 };
+    for (int64_t i = 0; i < n; ++i) {
+        double rc[3], dv[3], t[3];
+        for (int a = 0; a < 3; ++a) { rc[a] = q[3 * i + a] - Qc[a]; dv[a] = v[3 * i + a] - o[3 * i + a]; }
+        double r2 = rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Pi[a][b] += m[i] * ((a == b) * r2 - rc[a] * rc[b]);
+        cross(rc, dv, t);
+        for (int a = 0; a < 3; ++a) dL[a] += m[i] * t[a];
+    }
+    double lam[3], V[3][3], w[3] = { 0, 0, 0 };
+    sym_eig3(Pi, lam, V);
+    double lmax = fmax(fmax(lam[0], lam[1]), lam[2]);
+    for (int k = 0; k < 3; ++k) {
+        if (!(lam[k] > 1e-12 * lmax)) continue;
+        double c = (V[0][k] * dL[0] + V[1][k] * dL[1] + V[2][k] * dL[2]) / lam[k];
+        for (int a = 0; a < 3; ++a) w[a] += c * V[a][k];
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double rc[3], t[3];
+        for (int a = 0; a < 3; ++a) rc[a] = q[3 * i + a] - Qc[a];
+        cross(w, rc, t);
+        for (int a = 0; a < 3; ++a) o[3 * i + a] += t[a];
+    }
+    if (w_out) memcpy(w_out, w, sizeof w);
 }
 
 void orc_grid_shift(const orc_sys *s, int rep, int64_t step, int32_t S[3])
@@ -598,12 +699,15 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
     int64_t *start = (int64_t *)calloc(Ctot + 1, sizeof(int64_t));
     int64_t *order = (int64_t *)malloc((Ns + Nsite + 1) * sizeof(int64_t));
     double *vnew = (double *)malloc(3 * (Ns + Nsite + 1) * sizeof(double));
+    double *spos = (double *)malloc(3 * (Nsite ? Nsite : 1) * sizeof(double)); /* stored site r */
+    int32_t *shifts = (int32_t *)malloc(3 * (s->n_rep + 1) * sizeof(int32_t));
     int status = 0;
 
     for (int r = 0; r < s->n_rep; ++r) {
         const int32_t *L = s->L + 3 * r;
         int32_t S[3];
         orc_grid_shift(s, r, st->step, S);                              /* a2 */
+        memcpy(shifts + 3 * r, S, sizeof S);
         if (tr && tr->shift) memcpy(tr->shift + 3 * r, S, sizeof S);
         const int64_t ns_r = s->solv_off[r + 1] - s->solv_off[r];
 
@@ -648,6 +752,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                         rr[a] = y;
                     }
                 }
+                memcpy(spos + 3 * g, rr, sizeof rr);
                 if (tr && tr->site_r) memcpy(tr->site_r + 3 * g, rr, sizeof rr);
                 cell_of[Ns + g] = cbase[r] + local_cell(rr, S, L);
                 if (!s->naive_transfer) {
@@ -816,6 +921,35 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                 }
             }
             free(xi);
+            if (s->angular && collide) {
+                /* +a: restore the cell's angular momentum about its centre of mass */
+                double *mm = (double *)malloc(n * sizeof(double));
+                double *qq = (double *)malloc(3 * n * sizeof(double));
+                double *vv = (double *)malloc(3 * n * sizeof(double));
+                double *oo = (double *)malloc(3 * n * sizeof(double));
+                double w[3];
+                for (int64_t k = start[c]; k < start[c + 1]; ++k) {
+                    int64_t id = order[k], j = k - start[c];
+                    const double *x, *v;
+                    if (id < Ns) { mm[j] = s->m_solvent; x = st->x + 3 * id; v = st->v + 3 * id; }
+                    else {
+                        int64_t g = id - Ns, b = site_body[g];
+                        mm[j] = s->m[s->site_off[s->body_shape[b]] + (g - site_base[b])];
+                        x = spos + 3 * g;
+                        v = sv + 3 * g;
+                    }
+                    for (int a = 0; a < 3; ++a) {
+                        qq[3 * j + a] = cell_offset(x[a], shifts[3 * r + a]);
+                        vv[3 * j + a] = v[a];
+                        oo[3 * j + a] = vnew[3 * id + a];
+                    }
+                }
+                angular_correction(n, mm, qq, vv, oo, w);
+                for (int64_t k = start[c]; k < start[c + 1]; ++k)
+                    for (int a = 0; a < 3; ++a) vnew[3 * order[k] + a] = oo[3 * (k - start[c]) + a];
+                if (tr && tr->cell_omega) memcpy(tr->cell_omega + 3 * c, w, sizeof w);
+                free(mm); free(qq); free(vv); free(oo);
+            }
         }
     }
 
@@ -860,7 +994,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
     }
 done:
     free(site_base); free(site_body); free(body_rep); free(cbase); free(sv); free(svp); free(sd);
-    free(cell_of); free(start); free(order); free(vnew);
+    free(cell_of); free(start); free(order); free(vnew); free(spos); free(shifts);
     return status;
 }
 

@@ -212,6 +212,7 @@ class Params:
     precision: int = P64
     naive_transfer: int = 0
     seed: int = 1
+    angular: int = 0              # 1: angular-momentum-conserving variant of the rule (SRD+a, MPCD-AT+a)
 
 
 @dataclasses.dataclass
