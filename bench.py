@@ -50,7 +50,7 @@ def args_():
     ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
     ap.add_argument("--workload", default="suspension",
                     choices=["suspension", "single_sphere_L10", "suspension_L50", "batched_single_sphere",
-                             "batched_mixed_shapes", "phi_sweep_L120"],
+                             "batched_mixed_shapes", "phi_sweep_L120", "solvent_L200"],
                     help="suspension: the benchmark (box --L, rule --rule); the others are the smaller and "
                          "batched workloads and the paper-shaped phi sweep (--phi), for the record")
     ap.add_argument("--phi", type=float, default=0.3, help="volume fraction of phi_sweep_L120")
@@ -58,6 +58,9 @@ def args_():
     ap.add_argument("--rule", default="srd", choices=["srd", "at"],
                     help="collision rule of the workload: SRD with the cell thermostat (the benchmark) or "
                          "MPCD-AT (for the ALU-side measurement of the Philox/Box-Muller path)")
+    ap.add_argument("--angular", action="store_true",
+                    help="angular-momentum-conserving variant of the rule (SRD+a / MPCD-AT+a); pure solvent "
+                         "only (--workload solvent_L200)")
     ap.add_argument("--no-protocols", action="store_true",
                     help="skip the transport-protocol measurements (momentum exchange, sedimentation, VACF)")
     return ap.parse_args()
@@ -324,6 +327,12 @@ def main():
             n = a.n_rep or 256
             return (I.batched_mixed_shapes(n_rep=n, precision=precision, seed=seed),
                     f"batched_{n}x_mixed_shapes_L20-40_MPCD-AT")
+        if a.workload == "solvent_L200":
+            prm = I.Params(rule=rule, thermostat=thermo, precision=precision, seed=seed, angular=int(a.angular))
+            name = "solvent_L200_density10_" + ("SRD130_thermostat" if rule == I.SRD else "MPCD-AT") + \
+                ("+a" if a.angular else "")
+            return I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [(L, L, L)], 10.0, [[]], name,
+                                  placement_seed=seed), name
         if a.workload == "phi_sweep_L120":
             name = f"suspension_L120_phi{a.phi:g}_d6_162sites_density5_SRD130_thermostat"
             return I.suspension(120, 5.0, a.phi, 3.0, 2, 5.0, I.SRD, 1, precision, seed=seed, name=name), name
@@ -462,12 +471,16 @@ def main():
                "no flush: the state fits in L2 (129 MB), so the bandwidth fraction is not meaningful")
     rule_note = ("SRD alpha=130" + (" + cell-level thermostat" if system.params.thermostat else "")
                  if system.params.rule == I.SRD else "MPCD-AT (Andersen thermostat rule)")
+    if getattr(system.params, "angular", 0):
+        rule_note += ", angular-momentum-conserving (+a, unfused step)"
     if default_workload:
         config = {"workload": workload, "L": L, "density": 10, "phi": 0.3, "colloid_radius": 4.0}
     else:
         config = {"workload": workload, "n_replicas": system.n_rep}
         if a.workload == "phi_sweep_L120":
             config.update({"L": 120, "density": 5, "phi": a.phi, "colloid_radius": 3.0})
+        if a.workload == "solvent_L200":
+            config.update({"L": L, "density": 10})
     config.update({"n_solvent": system.n_solvent, "n_bodies": system.n_bodies, "n_sites": system.n_sites,
                    "n_cells": system.n_cells, "form": "P32: FP32 state, int64 fixed-point cell sums, FP64 bodies",
                    "rule": rule_note, "dt": 0.1, "l2": l2_note, "tuning": tuning,

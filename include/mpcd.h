@@ -75,7 +75,14 @@ typedef struct {
     uint64_t seed;        /* Philox4x32-10 key */
     int32_t sort_period;  /* steps between spatial re-sorts of the solvent;
                              0 = default (20), < 0 = never */
-    int32_t reserved;     /* must be 0 */
+    int32_t angular;      /* 1: angular-momentum-conserving variant of the rule
+                             (SRD+a, MPCD-AT+a, the modification Sec. II.A cites):
+                             after the rule every cell with >= 2 members gets the
+                             rigid rotation v' = v* + w x r_c that restores its
+                             angular momentum about its centre of mass (r_c on the
+                             2^-20 lattice of the binning rule; least-norm w for
+                             collinear members).  Pure solvent only (no bodies:
+                             MPCD_ERR_ARG otherwise); steps run unfused.  0: off */
 } mpcd_params;
 
 /* A rigid discrete-particle template in its principal-axis frame with its
@@ -354,7 +361,7 @@ int mpcd_autotune(mpcd_ctx *ctx, int32_t steps_per_trial, void *stream);
  * velocities are updated in place.
  *
  * Arguments (device pointers, caller-owned, on the current CUDA device):
- *   params     host struct; precision must be MPCD_P32 and reserved 0
+ *   params     host struct; precision must be MPCD_P32 and angular 0
  *              (sort_period and naive_transfer are ignored)
  *   L          host int32[3], cells per edge, each >= 3
  *   n_solvent  particles, 0 <= n <= MPCD_STATIC_MAX_SOLVENT, a multiple of 4

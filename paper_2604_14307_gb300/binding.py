@@ -46,7 +46,7 @@ class Params(C.Structure):
     _fields_ = [("kT", C.c_double), ("dt", C.c_double), ("alpha_deg", C.c_double),
                 ("m_solvent", C.c_double), ("rule", C.c_int32), ("thermostat", C.c_int32),
                 ("precision", C.c_int32), ("naive_transfer", C.c_int32), ("seed", C.c_uint64),
-                ("sort_period", C.c_int32), ("reserved", C.c_int32)]
+                ("sort_period", C.c_int32), ("angular", C.c_int32)]
 
 
 class ShapeDesc(C.Structure):
@@ -205,7 +205,7 @@ class Simulation:
         p = system.params
         self.precision = p.precision
         self.prm = Params(p.kT, p.dt, p.alpha_deg, p.m_solvent, p.rule, p.thermostat,
-                          p.precision, p.naive_transfer, p.seed, sort_period, 0)
+                          p.precision, p.naive_transfer, p.seed, sort_period, getattr(p, "angular", 0))
         self._keep = []
         shapes = (ShapeDesc * max(1, len(system.shapes)))()
         for k, sh in enumerate(system.shapes):
@@ -441,7 +441,8 @@ def collide_solvent_static(params: I.Params, L, x, y, z, vx, vy, vz, tag=None, s
     must not overlap in time: they share the scratch."""
     lib = load()
     prm = Params(params.kT, params.dt, params.alpha_deg, params.m_solvent, params.rule,
-                 params.thermostat, params.precision, params.naive_transfer, params.seed, 0, 0)
+                 params.thermostat, params.precision, params.naive_transfer, params.seed, 0,
+                 getattr(params, "angular", 0))
     arrs = [x, y, z, vx, vy, vz]
     n = int(x.numel())
     for t in arrs + ([tag] if tag is not None else []):

@@ -25,6 +25,7 @@ UNITS = {
     "kernels_bodies.cu": ["-fmad=false"],
     "static_collide.cu": [],
     "kernels_sort.cu": [],
+    "kernels_angular.cu": [],
 }
 
 

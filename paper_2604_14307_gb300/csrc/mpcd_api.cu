@@ -115,6 +115,8 @@ struct mpcd_ctx {
     int32_t *rn_ncand = nullptr;
     double *rn_tot = nullptr;                   // [0] momentum, [1] pairs (as long long)
     double *d_profile = nullptr;                // [2][PROFILE bins] velocity-profile sums
+    void *ang_words = nullptr;                  // [ANG_WORDS][C] angular-momentum sums (+a variants)
+    void *ang_params = nullptr;                 // [C] centre and w of the +a correction
     double f_ext[3] = {0.0, 0.0, 0.0};          // constant force on every body (one replica)
     VacfArgs vacf{};                            // velocity autocorrelations (n_lags 0: off)
     bool have_state = false;                    // mpcd_set_state has run
@@ -502,6 +504,61 @@ int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
     return MPCD_OK;
 }
 
+// one pass of the +a correction (kernels_angular.cu)
+int k_ang(mpcd_ctx *c, int phase, cudaStream_t s)
+{
+    static const char *names[] = {"angular_pre", "angular_post", "angular_params", "angular_apply"};
+    // algorithmic bytes: the solvent arrays each pass reads (and writes), the
+    // cell words written or read once, the per-cell records
+    const double N = (double)c->Ns, C = (double)c->C, r = c->realsz;
+    const double rec = (double)angular_param_bytes(c->prm.precision);
+    const double bytes[] = {N * 6 * r + C * ANG_WORDS * 8, N * 6 * r + C * 6 * 8,
+                            C * (2.0 * ANG_WORDS * 8 + rec), N * 9 * r + C * rec};
+    StepArgs a = make_args(c);
+    return timed(c, names[phase], bytes[phase], s,
+                 [&] { launch_angular(a, phase, c->ang_words, c->ang_params, c->num_sms, s); });
+}
+
+// the unpipelined collision of the solvent at the current step (a2, a5-a7):
+// exchange, binning, cell parameters, rule; with the +a variant the angular
+// sums are taken before and after the rule and the correction applied
+int k_collide(mpcd_ctx *c, cudaStream_t s)
+{
+    const bool ang = c->prm.angular != 0;
+    int e = k_rnemd(c, s, 0, 0);
+    if (!e) e = k_solvent(c, SOLV_BIN, s);
+    if (!e && ang) e = k_ang(c, ANG_PRE, s);
+    if (!e) e = k_params(c, s);
+    if (!e) e = k_solvent(c, SOLV_COLLIDE, s);
+    if (!e && ang) e = k_ang(c, ANG_POST, s);
+    if (!e && ang) e = k_ang(c, ANG_PARAMS, s);
+    if (!e && ang) e = k_ang(c, ANG_APPLY, s);
+    return e;
+}
+
+// whole steps in the unpipelined order stream, couple(PRE), collide,
+// couple(POST) (the +a variants, whose correction needs the cell totals of
+// the rule's velocities before any particle streams on)
+int run_steps_unfused(mpcd_ctx *c, int64_t n, cudaStream_t s)
+{
+    int e = MPCD_OK;
+    for (int64_t k = 0; k < n && !e; ++k) {
+        if ((e = k_stream(c, s))) break;
+        if ((e = k_pre(c, s))) break;
+        if ((e = k_collide(c, s))) break;
+        if ((e = k_post(c, s))) break;
+        if ((e = k_vacf(c, s))) break;
+        if ((e = k_advance(c, s))) break;
+        if (c->prm.sort_period >= 0 && ++c->since_sort >= c->tune.sort_period)
+            if ((e = do_sort(c, 0, s))) break;
+    }
+    if (!e && !c->profiling) {
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) return fail(c, MPCD_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(ce));
+    }
+    return e;
+}
+
 // whole steps, software-pipelined: the solvent pass of step k collides (k),
 // streams and bins for step k+1; beside it, on a second stream, run the site
 // POST coupling of step k and the body step and site PRE coupling of step k+1
@@ -512,6 +569,7 @@ int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
 int run_steps(mpcd_ctx *c, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return MPCD_OK;
+    if (c->prm.angular) return run_steps_unfused(c, n, s);
     int e = k_solvent(c, SOLV_STREAM | SOLV_BIN, s);
     if (!e) e = k_rnemd(c, s, 0, 1);
     if (!e) e = k_bodies(c, s);
@@ -586,7 +644,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     const mpcd_params &p = *params;
     if (!(p.kT > 0) || !(p.dt > 0) || !(p.m_solvent > 0) || !std::isfinite(p.alpha_deg) ||
         (p.rule != MPCD_SRD && p.rule != MPCD_AT) || (p.precision != MPCD_P32 && p.precision != MPCD_P64) ||
-        p.reserved != 0)
+        (p.angular != 0 && p.angular != 1))
         return MPCD_ERR_ARG;
     if (allocator && (!allocator->alloc || !allocator->free)) return MPCD_ERR_ARG;
     int ndev = 0;
@@ -683,8 +741,9 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     int64_t slot = 0, cells = 0, bodies = 0, sites = 0, rows = 0;
     for (int r = 0; r < n_replicas; ++r) {
         const mpcd_replica_desc &d = replicas[r];
-        if (d.L[0] < 3 || d.L[1] < 3 || d.L[2] < 3 || d.L[0] > 4096 || d.L[1] > 4096 || d.L[2] > 4096 ||
-            d.n_solvent < 0 || d.n_bodies < 0 || (d.n_bodies > 0 && !d.body_shape) || d.stream_id < 0) {
+        if (d.L[0] < 3 || d.L[1] < 3 || d.L[2] < 3 || d.L[0] > 2047 || d.L[1] > 2047 || d.L[2] > 2047 ||
+            d.n_solvent < 0 || d.n_bodies < 0 || (d.n_bodies > 0 && !d.body_shape) || d.stream_id < 0 ||
+            (p.angular && d.n_bodies > 0)) {
             delete c;
             return MPCD_ERR_ARG;
         }
@@ -792,6 +851,10 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     ok &= (c->rs_hist = (int32_t *)A(radix_hist_ints(c->Nslots) * 4)) != nullptr;
     ok &= (c->rs_ex = (int32_t *)A(radix_hist_ints(c->Nslots) * 4)) != nullptr;
     ok &= (c->rs_bs = (int32_t *)A(scan_block_sums_size((int64_t)radix_hist_ints(c->Nslots)) * 4)) != nullptr;
+    if (p.angular) {
+        ok &= (c->ang_words = A((size_t)c->C * ANG_WORDS * 8)) != nullptr;
+        ok &= (c->ang_params = A((size_t)c->C * angular_param_bytes(p.precision))) != nullptr;
+    }
     if (!ok) {
         mpcd_destroy(c);
         return MPCD_ERR_OOM;
@@ -833,6 +896,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     }
     if (cudaMemset(c->sums, 0, (size_t)c->C * c->nw * 8) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->params, 0, (size_t)c->C * c->param_bytes) != cudaSuccess) st = MPCD_ERR_CUDA;
+    if (c->ang_words && cudaMemset(c->ang_words, 0, (size_t)c->C * ANG_WORDS * 8) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_step, 0, 8) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_ncount, 0, std::max<int64_t>(1, c->B) * 4) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_bpos_build, 0, std::max<int64_t>(1, c->B) * sizeof(float4)) != cudaSuccess) st = MPCD_ERR_CUDA;
@@ -1085,10 +1149,7 @@ int mpcd_collide(mpcd_ctx *c, void *stream)
     CHECK_CTX(c);
     CK(c, cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
-    int e = k_rnemd(c, s, 0, 0);
-    if (!e) e = k_solvent(c, SOLV_BIN, s);
-    if (!e) e = k_params(c, s);
-    if (!e) e = k_solvent(c, SOLV_COLLIDE, s);
+    int e = k_collide(c, s);
     if (!e) CK(c, cudaGetLastError());
     c->last_key = c->step;
     return e;

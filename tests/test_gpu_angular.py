@@ -1,0 +1,176 @@
+"""GPU tests of the angular-momentum-conserving collision variants (SRD+a,
+MPCD-AT+a; the modification of the rules Sec. II.A cites) for the pure
+solvent, through the C ABI.
+
+* One collision from the same state as the oracle, through the unpipelined
+  calls (stream, couple, collide, couple): positions bit-exact (P32) or
+  within 1e-12 (P64), velocities within
+      tol (|v| + 1 + |w_c|),  tol = 1e-5 (P32), 1e-12 (P64),
+  with w_c the cell's correction from the oracle's trace.  The |w_c| term is
+  derived from the arithmetic: the correction w x r_c is formed in the working
+  precision, so it carries a rounding of order eps |w_c| |r_c| with
+  |r_c| < sqrt(3); w_c is large only in the rare cells whose members are
+  nearly collinear.
+* On the GPU's own data: in every cell the momentum and the angular momentum
+  about the centre of mass (lattice positions) are unchanged to float32
+  rounding, which the plain rule breaks.
+* mpcd_step over two steps (graph-captured) gives bit-identical state to the
+  unpipelined calls repeated.
+* Argument checks: the variant with colloids, and in the static collision.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_14307_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {I.P64: 1e-12, I.P32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_14307_gb300 import binding, build_lib
+    build_lib.build()
+    return binding
+
+
+def solvent_box(rule, thermostat, precision, L=(12, 16, 10), seed=5, angular=1):
+    prm = I.Params(rule=rule, thermostat=thermostat, precision=precision, seed=seed, angular=angular)
+    return I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [L], 5.0, [[]], "solvent_only",
+                          placement_seed=seed)
+
+
+def gpu_one_collision(B, system, st):
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.set_debug(True)
+    sim.stream()
+    sim.couple(B.MPCD_PRE)
+    sim.collide()
+    sim.couple(B.MPCD_POST)
+    d = sim.debug_cells()
+    g = sim.get_state()
+    sim.close()
+    return g, d
+
+
+CASES = [(I.SRD, 1, I.P32), (I.SRD, 0, I.P32), (I.AT, 0, I.P32), (I.SRD, 1, I.P64), (I.AT, 0, I.P64)]
+
+
+@pytest.mark.parametrize("rule,thermostat,prec", CASES)
+@pytest.mark.parametrize("L", [(12, 16, 10), (23, 17, 19)])
+def test_one_collision_matches_oracle(B, rule, thermostat, prec, L):
+    system = solvent_box(rule, thermostat, prec, L=L)
+    st = I.initial_state(system)
+    g, _ = gpu_one_collision(B, system, st)
+
+    osys = O.OracleSystem(system)
+    assert osys.params["angular"] == 1
+    ost = O.OracleState(osys, st)
+    O.stream(osys, ost)
+    tr = O.collide(osys, ost)
+    if prec == I.P32:
+        assert np.array_equal(g.x, ost.x)
+    else:
+        assert np.max(np.abs(g.x - ost.x)) <= 1e-12
+    w = np.linalg.norm(tr["cell_omega"], axis=1)[tr["cell_solvent"]]
+    bound = TOL[prec] * (np.abs(ost.v) + 1.0 + w[:, None])
+    err = np.abs(g.v - ost.v)
+    assert np.all(err <= bound), (err / bound).max()
+    # the correction is really applied: the plain rule's velocities differ by far more
+    o0 = O.OracleSystem(system, angular=0)
+    s0 = O.OracleState(o0, st)
+    O.stream(o0, s0)
+    O.collide(o0, s0, trace=False)
+    assert np.max(np.abs(g.v - s0.v)) > 0.1
+
+
+def lattice(x, S):
+    X = np.floor(np.asarray(x, dtype=np.float64) * 2.0**20).astype(np.int64)
+    t = X - np.asarray(S, dtype=np.int64)[None, :]
+    return np.floor_divide(t, 2**20), (t & (2**20 - 1)) * 2.0**-20
+
+
+def cell_angular_momentum(x, v, S, L):
+    """per cell: member count, momentum and angular momentum about the centre
+    of mass (unit masses, lattice positions)"""
+    k, q = lattice(x, S)
+    cell = np.mod(k[:, 0], L[0]) + L[0] * (np.mod(k[:, 1], L[1]) + L[1] * np.mod(k[:, 2], L[2]))
+    C = L[0] * L[1] * L[2]
+    n = np.bincount(cell, minlength=C)
+    qc = np.stack([np.bincount(cell, q[:, a], C) for a in range(3)], 1) / np.maximum(n, 1)[:, None]
+    rc = q - qc[cell]
+    P = np.stack([np.bincount(cell, v[:, a], C) for a in range(3)], 1)
+    lc = np.cross(rc, v)
+    Lc = np.stack([np.bincount(cell, lc[:, a], C) for a in range(3)], 1)
+    return n, P, Lc
+
+
+@pytest.mark.parametrize("angular", [1, 0])
+def test_gpu_conserves_cell_angular_momentum(B, angular):
+    system = solvent_box(I.SRD, 1, I.P32, L=(20, 20, 20), seed=8, angular=angular)
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    sim.set_debug(True)
+    sim.stream()
+    x1 = sim.get_state().x
+    sim.couple(B.MPCD_PRE)
+    sim.collide()
+    d = sim.debug_cells()
+    g = sim.get_state()
+    sim.close()
+    S = np.asarray(d["shift"]).reshape(-1, 3)[0]
+    Lb = system.replicas[0].L
+    assert np.array_equal(g.x, x1)
+    n0, P0, L0 = cell_angular_momentum(x1, st.v.astype(np.float32).astype(np.float64), S, Lb)
+    n1, P1, L1 = cell_angular_momentum(g.x, g.v, S, Lb)
+    live = n0 >= 2
+    assert np.array_equal(n0, n1)
+    assert np.max(np.abs(P1 - P0)[live]) < 1e-4
+    dl = np.max(np.abs(L1 - L0)[live])
+    if angular:
+        assert dl < 1e-4, dl
+    else:
+        assert dl > 0.1
+
+
+@pytest.mark.parametrize("rule,thermostat", [(I.SRD, 1), (I.AT, 0)])
+def test_step_equals_unpipelined_calls(B, rule, thermostat):
+    system = solvent_box(rule, thermostat, I.P32, L=(16, 12, 14), seed=4)
+    st = I.initial_state(system)
+    a = B.Simulation(system)
+    a.set_state(st)
+    a.step(2)                  # two steps: captured as a CUDA graph
+    ga = a.get_state()
+    a.close()
+    b = B.Simulation(system)
+    b.set_state(st)
+    for _ in range(2):
+        b.stream()
+        b.couple(B.MPCD_PRE)
+        b.collide()
+        b.couple(B.MPCD_POST)
+    gb = b.get_state()
+    b.close()
+    assert np.array_equal(ga.x, gb.x) and np.array_equal(ga.v, gb.v)
+
+
+def test_variant_arguments_are_checked(B):
+    prm = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=3, angular=1)
+    with_sphere = I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [(12, 12, 12)], 5.0, [[0]], "suspension",
+                                 placement_seed=3)
+    with pytest.raises(B.MPCDError) as e:
+        B.Simulation(with_sphere)
+    assert e.value.status == B.MPCD_ERR_ARG
+    bad = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=3, angular=2)
+    box = I.build_system(bad, [I.sphere_shape(2.0, 2, 5.0)], [(8, 8, 8)], 5.0, [[]], "solvent_only",
+                         placement_seed=3)
+    with pytest.raises(B.MPCDError) as e:
+        B.Simulation(box)
+    assert e.value.status == B.MPCD_ERR_ARG
