@@ -17,8 +17,8 @@
 //   k_ang_sums<PRE>   before the rule: count, sum Q, sum Q_a Q_b, + sum Q x P, + sum P
 //   k_ang_sums<POST>  after it:                                  - sum Q x P*, - sum P*
 //   k_ang_params      per cell: centre, Pi and the angular-momentum change in
-//                     FP64, w by Cholesky (least-norm form for collinear
-//                     members); clears the words for the next collision
+//                     FP64, w by the adjugate of Pi (least-norm form for
+//                     collinear members); clears the words for the next collision
 //   k_ang_apply       v = v* + w' x (N Q - sum Q),  w' = w / (N 2^20)
 // The offset from the centre is formed as the exact integer N Q - sum Q: for
 // nearly collinear members w is large along their line while the offsets
@@ -73,76 +73,125 @@ template <typename Real> __device__ __forceinline__ Real solvent_mass(const Step
 template <> __device__ __forceinline__ float solvent_mass<float>(const StepArgs &a) { return a.m_solvent_f; }
 template <> __device__ __forceinline__ double solvent_mass<double>(const StepArgs &a) { return a.m_solvent; }
 
-struct TileFrame {
-    int32_t L[3];
-    int32_t S[3];
-    int32_t base;
-    int64_t beg, end;
-};
-
-__device__ __forceinline__ void load_frame(const StepArgs &a, int t, int64_t step, TileFrame &f)
+// per-replica grid shift of the collision, computed once per collision
+__global__ void k_ang_shift(StepArgs a, int4 *shifts)
 {
-    const Tile tl = a.tiles[t];
-    const DevReplica r = a.reps[tl.rep];
-    for (int k = 0; k < 3; ++k) f.L[k] = r.L[k];
-    grid_shift(r, step, f.S);
-    f.base = r.cell_base;
-    f.beg = tl.begin;
-    f.end = tl.end;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.n_rep) return;
+    int32_t S[3];
+    grid_shift(a.reps[r], *a.d_step, S);
+    shifts[r] = make_int4(S[0], S[1], S[2], 0);
 }
 
+__device__ __forceinline__ void ld4v(const float *p, float (&o)[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4v(const double *p, double (&o)[4])
+{
+    const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
+    o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+}
+__device__ __forceinline__ void st4v(float *p, const float (&o)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4v(double *p, const double (&o)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
+}
+
+// cell and lattice offset Q of each of a thread's 4 particles
+template <typename Real>
+__device__ __forceinline__ void cells4(const Real (&x)[4], const Real (&y)[4], const Real (&z)[4], int4 S,
+                                       const DevReplica &r, int64_t (&c)[4], int (&Q)[4][3])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int X[3] = {lattice_X(x[j]), lattice_X(y[j]), lattice_X(z[j])};
+        const int Sk[3] = {S.x, S.y, S.z};
+        int cc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            cc[k] = axis_cell(X[k], Sk[k], r.L[k]);
+            Q[j][k] = (X[k] - Sk[k]) & 0xFFFFF;
+        }
+        c[j] = r.cell_base + cc[0] + (int64_t)r.L[0] * (cc[1] + (int64_t)r.L[1] * cc[2]);
+    }
+}
+
+// One warp per tile; each lane takes 4 consecutive particles (128-bit loads;
+// tiles start on multiples of 8 slots, and the slots past a replica's last
+// particle are allocated padding), merges runs of equal cells in registers and
+// issues one atomic per word and run.  Word k of particle j is term(k, j); PRE adds
+// words 0-15, POST subtracts the rule's new momentum terms from 10-15.
 template <typename Real, bool PRE>
-__global__ void __launch_bounds__(256) k_ang_sums(StepArgs a, void *words)
+__global__ void __launch_bounds__(256) k_ang_sums(StepArgs a, void *words, const int4 *shifts)
 {
     typedef typename AngWord<Real>::type W;
-    __shared__ TileFrame sf;
     W *w = reinterpret_cast<W *>(words);
     const int64_t C = a.n_cells;
-    const int64_t step = *a.d_step;
     const Real m = solvent_mass<Real>(a);
     const Real *X = reinterpret_cast<const Real *>(a.x), *Y = reinterpret_cast<const Real *>(a.y);
     const Real *Z = reinterpret_cast<const Real *>(a.z), *VX = reinterpret_cast<const Real *>(a.vx);
     const Real *VY = reinterpret_cast<const Real *>(a.vy), *VZ = reinterpret_cast<const Real *>(a.vz);
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) load_frame(a, t, step, sf);
-        __syncthreads();
-        const TileFrame f = sf;
-        for (int64_t i = f.beg + threadIdx.x; i < f.end; i += blockDim.x) {
-            const Real r[3] = {X[i], Y[i], Z[i]};
-            const Real v[3] = {VX[i], VY[i], VZ[i]};
-            int Q[3], cc[3];
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < a.n_tiles; t += gridDim.x * warps) {
+        const Tile tl = a.tiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        const int4 S = shifts[tl.rep];
+        for (int64_t i = tl.begin + 4 * lane; i < tl.end; i += 128) {
+            const int nv = (int)min((int64_t)4, tl.end - i);
+            Real x[4], y[4], z[4], vx[4], vy[4], vz[4];
+            ld4v(X + i, x); ld4v(Y + i, y); ld4v(Z + i, z);
+            ld4v(VX + i, vx); ld4v(VY + i, vy); ld4v(VZ + i, vz);
+            int64_t c[4];
+            int Q[4][3];
+            cells4(x, y, z, S, r, c, Q);
+            W P[4][3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int Xk = lattice_X(r[k]);
-                cc[k] = axis_cell(Xk, f.S[k], f.L[k]);
-                Q[k] = (Xk - f.S[k]) & 0xFFFFF;
+            for (int j = 0; j < 4; ++j) {
+                P[j][0] = mom_term(m, vx[j]); P[j][1] = mom_term(m, vy[j]); P[j][2] = mom_term(m, vz[j]);
             }
-            const int64_t c = f.base + cc[0] + (int64_t)f.L[0] * (cc[1] + (int64_t)f.L[1] * cc[2]);
-            const W P[3] = {mom_term(m, v[0]), mom_term(m, v[1]), mom_term(m, v[2])};
-            const W q[3] = {(W)Q[0], (W)Q[1], (W)Q[2]};
-            const W L[3] = {q[1] * P[2] - q[2] * P[1], q[2] * P[0] - q[0] * P[2], q[0] * P[1] - q[1] * P[0]};
-            if (PRE) {
-                ang_red(w + 0 * C + c, (W)1);
+            bool join[4], head[4];   // join[j]: particle j+1 is in j's cell
 #pragma unroll
-                for (int k = 0; k < 3; ++k) ang_red(w + (1 + k) * C + c, q[k]);
-                ang_red(w + 4 * C + c, q[0] * q[0]);
-                ang_red(w + 5 * C + c, q[1] * q[1]);
-                ang_red(w + 6 * C + c, q[2] * q[2]);
-                ang_red(w + 7 * C + c, q[0] * q[1]);
-                ang_red(w + 8 * C + c, q[0] * q[2]);
-                ang_red(w + 9 * C + c, q[1] * q[2]);
+            for (int j = 0; j < 4; ++j) {
+                join[j] = j + 1 < nv && c[j + 1] == c[j];
+                head[j] = j < nv && (j == 0 || c[j] != c[j - 1]);
+            }
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    ang_red(w + (10 + k) * C + c, L[k]);
-                    ang_red(w + (13 + k) * C + c, P[k]);
+            for (int k = PRE ? 0 : 10; k < ANG_WORDS; ++k) {
+                W v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const W q0 = (W)Q[j][0], q1 = (W)Q[j][1], q2 = (W)Q[j][2];
+                    W e;
+                    switch (k) {
+                    case 0: e = (W)1; break;
+                    case 1: e = q0; break;
+                    case 2: e = q1; break;
+                    case 3: e = q2; break;
+                    case 4: e = q0 * q0; break;
+                    case 5: e = q1 * q1; break;
+                    case 6: e = q2 * q2; break;
+                    case 7: e = q0 * q1; break;
+                    case 8: e = q0 * q2; break;
+                    case 9: e = q1 * q2; break;
+                    case 10: e = q1 * P[j][2] - q2 * P[j][1]; break;
+                    case 11: e = q2 * P[j][0] - q0 * P[j][2]; break;
+                    case 12: e = q0 * P[j][1] - q1 * P[j][0]; break;
+                    default: e = P[j][k - 13]; break;
+                    }
+                    v[j] = PRE ? e : -e;
                 }
-            } else {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    ang_red(w + (10 + k) * C + c, -L[k]);
-                    ang_red(w + (13 + k) * C + c, -P[k]);
-                }
+                for (int j = 2; j >= 0; --j)
+                    if (join[j]) v[j] += v[j + 1];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (head[j]) ang_red(w + k * C + c[j], v[j]);
             }
         }
     }
@@ -161,16 +210,17 @@ __device__ void cell_omega(const W (&wd)[ANG_WORDS], double m, double pscale, do
     om[0] = om[1] = om[2] = 0.0;
     const double N = (double)wd[0];
     if (N < 2.0) return;
+    const double iN = 1.0 / N;
     const double sQ[3] = {(double)wd[1], (double)wd[2], (double)wd[3]};
-    const double Qc[3] = {sQ[0] / N, sQ[1] / N, sQ[2] / N};
+    const double Qc[3] = {sQ[0] * iN, sQ[1] * iN, sQ[2] * iN};
     // lattice covariance C (exact sums; one rounding in the centre term)
     double Cm[3][3];
-    Cm[0][0] = (double)wd[4] - sQ[0] * sQ[0] / N;
-    Cm[1][1] = (double)wd[5] - sQ[1] * sQ[1] / N;
-    Cm[2][2] = (double)wd[6] - sQ[2] * sQ[2] / N;
-    Cm[0][1] = Cm[1][0] = (double)wd[7] - sQ[0] * sQ[1] / N;
-    Cm[0][2] = Cm[2][0] = (double)wd[8] - sQ[0] * sQ[2] / N;
-    Cm[1][2] = Cm[2][1] = (double)wd[9] - sQ[1] * sQ[2] / N;
+    Cm[0][0] = (double)wd[4] - sQ[0] * Qc[0];
+    Cm[1][1] = (double)wd[5] - sQ[1] * Qc[1];
+    Cm[2][2] = (double)wd[6] - sQ[2] * Qc[2];
+    Cm[0][1] = Cm[1][0] = (double)wd[7] - sQ[0] * Qc[1];
+    Cm[0][2] = Cm[2][0] = (double)wd[8] - sQ[0] * Qc[2];
+    Cm[1][2] = Cm[2][1] = (double)wd[9] - sQ[1] * Qc[2];
     const double tr = Cm[0][0] + Cm[1][1] + Cm[2][2];
     // angular-momentum change about the centre, in units of 2^-20 pscale
     const double dP[3] = {(double)wd[13], (double)wd[14], (double)wd[15]};
@@ -178,41 +228,25 @@ __device__ void cell_omega(const W (&wd)[ANG_WORDS], double m, double pscale, do
                     (double)wd[11] - (Qc[2] * dP[0] - Qc[0] * dP[2]),
                     (double)wd[12] - (Qc[0] * dP[1] - Qc[1] * dP[0])};
     if (!(tr > 0.0)) return;                  // every member on one lattice point
-    // G = tr(C) I - C = Pi / (m 2^-40); solve G x = dL
-    double G[3][3];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) G[i][j] = (i == j ? tr : 0.0) - Cm[i][j];
-    const double tol = 1e-12 * tr;
+    // G = tr(C) I - C = Pi / (m 2^-40); solve G x = dL by its adjugate
+    const double a00 = tr - Cm[0][0], a11 = tr - Cm[1][1], a22 = tr - Cm[2][2];
+    const double a01 = -Cm[0][1], a02 = -Cm[0][2], a12 = -Cm[1][2];
+    const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+    const double c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+    const double det = a00 * c00 + a01 * c01 + a02 * c02;
     double x[3];
-    bool ok = G[0][0] > tol;
-    double l00 = 0, l10 = 0, l20 = 0, l11 = 0, l21 = 0, l22 = 0;
-    if (ok) {
-        l00 = sqrt(G[0][0]);
-        l10 = G[1][0] / l00;
-        l20 = G[2][0] / l00;
-        const double d1 = G[1][1] - l10 * l10;
-        ok = d1 > tol;
-        if (ok) {
-            l11 = sqrt(d1);
-            l21 = (G[2][1] - l20 * l10) / l11;
-            const double d2 = G[2][2] - l20 * l20 - l21 * l21;
-            ok = d2 > tol;
-            if (ok) l22 = sqrt(d2);
-        }
-    }
-    if (ok) {
-        const double y0 = dL[0] / l00;
-        const double y1 = (dL[1] - l10 * y0) / l11;
-        const double y2 = (dL[2] - l20 * y0 - l21 * y1) / l22;
-        x[2] = y2 / l22;
-        x[1] = (y1 - l21 * x[2]) / l11;
-        x[0] = (y0 - l10 * x[1] - l20 * x[2]) / l00;
+    if (det > 1e-12 * tr * tr * tr) {
+        const double inv = 1.0 / det;
+        x[0] = (c00 * dL[0] + c01 * dL[1] + c02 * dL[2]) * inv;
+        x[1] = (c01 * dL[0] + c11 * dL[1] + c12 * dL[2]) * inv;
+        x[2] = (c02 * dL[0] + c12 * dL[1] + c22 * dL[2]) * inv;
     } else {
         // collinear members: C = tr(C) d d^T, G = tr(C) (I - d d^T); least-norm x
         // = (dL - d (d.dL)) / tr(C) with d d^T = C / tr(C)
+        const double it = 1.0 / tr;
         for (int i = 0; i < 3; ++i) {
             const double CdL = Cm[i][0] * dL[0] + Cm[i][1] * dL[1] + Cm[i][2] * dL[2];
-            x[i] = (dL[i] - CdL / tr) / tr;
+            x[i] = (dL[i] - CdL * it) * it;
         }
     }
     // Pi w = dL_phys: Pi = m 2^-40 G, dL_phys = 2^-20 pscale dL
@@ -261,35 +295,42 @@ __device__ __forceinline__ double offset_real(const AngParams<double> &p, int Q,
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) k_ang_apply(StepArgs a, const AngParams<Real> *params)
+__global__ void __launch_bounds__(256) k_ang_apply(StepArgs a, const AngParams<Real> *params, const int4 *shifts)
 {
-    __shared__ TileFrame sf;
-    const int64_t step = *a.d_step;
     const Real *X = reinterpret_cast<const Real *>(a.x), *Y = reinterpret_cast<const Real *>(a.y);
     const Real *Z = reinterpret_cast<const Real *>(a.z);
     Real *VX = reinterpret_cast<Real *>(a.vx), *VY = reinterpret_cast<Real *>(a.vy);
     Real *VZ = reinterpret_cast<Real *>(a.vz);
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) load_frame(a, t, step, sf);
-        __syncthreads();
-        const TileFrame f = sf;
-        for (int64_t i = f.beg + threadIdx.x; i < f.end; i += blockDim.x) {
-            const Real r[3] = {X[i], Y[i], Z[i]};
-            int cc[3], Q[3];
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < a.n_tiles; t += gridDim.x * warps) {
+        const Tile tl = a.tiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        const int4 S = shifts[tl.rep];
+        for (int64_t i = tl.begin + 4 * lane; i < tl.end; i += 128) {
+            const int nv = (int)min((int64_t)4, tl.end - i);
+            Real x[4], y[4], z[4], vx[4], vy[4], vz[4];
+            ld4v(X + i, x); ld4v(Y + i, y); ld4v(Z + i, z);
+            ld4v(VX + i, vx); ld4v(VY + i, vy); ld4v(VZ + i, vz);
+            int64_t c[4];
+            int Q[4][3];
+            cells4(x, y, z, S, r, c, Q);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int Xk = lattice_X(r[k]);
-                cc[k] = axis_cell(Xk, f.S[k], f.L[k]);
-                Q[k] = (Xk - f.S[k]) & 0xFFFFF;
+            for (int j = 0; j < 4; ++j) {
+                if (j >= nv) break;
+                const AngParams<Real> p = params[c[j]];
+                const Real rc[3] = {offset_real(p, Q[j][0], 0), offset_real(p, Q[j][1], 1),
+                                    offset_real(p, Q[j][2], 2)};
+                vx[j] = vx[j] + (p.w[1] * rc[2] - p.w[2] * rc[1]);
+                vy[j] = vy[j] + (p.w[2] * rc[0] - p.w[0] * rc[2]);
+                vz[j] = vz[j] + (p.w[0] * rc[1] - p.w[1] * rc[0]);
             }
-            const int64_t c = f.base + cc[0] + (int64_t)f.L[0] * (cc[1] + (int64_t)f.L[1] * cc[2]);
-            const AngParams<Real> p = params[c];
-            const Real rc[3] = {offset_real(p, Q[0], 0), offset_real(p, Q[1], 1), offset_real(p, Q[2], 2)};
-            const Real wx = p.w[0], wy = p.w[1], wz = p.w[2];
-            VX[i] = VX[i] + (wy * rc[2] - wz * rc[1]);
-            VY[i] = VY[i] + (wz * rc[0] - wx * rc[2]);
-            VZ[i] = VZ[i] + (wx * rc[1] - wy * rc[0]);
+            if (nv == 4) {
+                st4v(VX + i, vx); st4v(VY + i, vy); st4v(VZ + i, vz);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < nv) { VX[i + j] = vx[j]; VY[i + j] = vy[j]; VZ[i + j] = vz[j]; }
+            }
         }
     }
 }
@@ -301,22 +342,24 @@ size_t angular_param_bytes(int precision)
     return precision == 1 ? sizeof(AngParams<float>) : sizeof(AngParams<double>);
 }
 
-void launch_angular(const StepArgs &a, int phase, void *words, void *params, int num_sms, cudaStream_t s)
+void launch_angular(const StepArgs &a, int phase, void *words, void *params, int4 *shifts, int num_sms,
+                    cudaStream_t s)
 {
     if (a.n_cells == 0) return;
     const int grid_p = std::max(1, num_sms * 16);
-    const int grid_t = (int)std::max(1, std::min(a.n_tiles, num_sms * 16));
+    const int grid_t = (int)std::max(1, std::min((a.n_tiles + 7) / 8, num_sms * 8));   // 8 warps, one tile each
     const bool p32 = a.precision == 1;
     switch (phase) {
     case ANG_PRE:
         if (a.n_tiles == 0) return;
-        if (p32) k_ang_sums<float, true><<<grid_t, 256, 0, s>>>(a, words);
-        else k_ang_sums<double, true><<<grid_t, 256, 0, s>>>(a, words);
+        k_ang_shift<<<(a.n_rep + 127) / 128, 128, 0, s>>>(a, shifts);
+        if (p32) k_ang_sums<float, true><<<grid_t, 256, 0, s>>>(a, words, shifts);
+        else k_ang_sums<double, true><<<grid_t, 256, 0, s>>>(a, words, shifts);
         break;
     case ANG_POST:
         if (a.n_tiles == 0) return;
-        if (p32) k_ang_sums<float, false><<<grid_t, 256, 0, s>>>(a, words);
-        else k_ang_sums<double, false><<<grid_t, 256, 0, s>>>(a, words);
+        if (p32) k_ang_sums<float, false><<<grid_t, 256, 0, s>>>(a, words, shifts);
+        else k_ang_sums<double, false><<<grid_t, 256, 0, s>>>(a, words, shifts);
         break;
     case ANG_PARAMS:
         if (p32) k_ang_params<float><<<grid_p, 256, 0, s>>>(a, words, reinterpret_cast<AngParams<float> *>(params));
@@ -324,8 +367,8 @@ void launch_angular(const StepArgs &a, int phase, void *words, void *params, int
         break;
     case ANG_APPLY:
         if (a.n_tiles == 0) return;
-        if (p32) k_ang_apply<float><<<grid_t, 256, 0, s>>>(a, reinterpret_cast<const AngParams<float> *>(params));
-        else k_ang_apply<double><<<grid_t, 256, 0, s>>>(a, reinterpret_cast<const AngParams<double> *>(params));
+        if (p32) k_ang_apply<float><<<grid_t, 256, 0, s>>>(a, reinterpret_cast<const AngParams<float> *>(params), shifts);
+        else k_ang_apply<double><<<grid_t, 256, 0, s>>>(a, reinterpret_cast<const AngParams<double> *>(params), shifts);
         break;
     default:
         break;

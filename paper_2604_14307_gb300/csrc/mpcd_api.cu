@@ -116,7 +116,8 @@ struct mpcd_ctx {
     double *rn_tot = nullptr;                   // [0] momentum, [1] pairs (as long long)
     double *d_profile = nullptr;                // [2][PROFILE bins] velocity-profile sums
     void *ang_words = nullptr;                  // [ANG_WORDS][C] angular-momentum sums (+a variants)
-    void *ang_params = nullptr;                 // [C] centre and w of the +a correction
+    void *ang_params = nullptr;                 // [C] sum Q, N and w' of the +a correction
+    int4 *ang_shift = nullptr;                  // [nrep] grid shift of the current collision
     double f_ext[3] = {0.0, 0.0, 0.0};          // constant force on every body (one replica)
     VacfArgs vacf{};                            // velocity autocorrelations (n_lags 0: off)
     bool have_state = false;                    // mpcd_set_state has run
@@ -516,7 +517,7 @@ int k_ang(mpcd_ctx *c, int phase, cudaStream_t s)
                             C * (2.0 * ANG_WORDS * 8 + rec), N * 9 * r + C * rec};
     StepArgs a = make_args(c);
     return timed(c, names[phase], bytes[phase], s,
-                 [&] { launch_angular(a, phase, c->ang_words, c->ang_params, c->num_sms, s); });
+                 [&] { launch_angular(a, phase, c->ang_words, c->ang_params, c->ang_shift, c->num_sms, s); });
 }
 
 // the unpipelined collision of the solvent at the current step (a2, a5-a7):
@@ -854,6 +855,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     if (p.angular) {
         ok &= (c->ang_words = A((size_t)c->C * ANG_WORDS * 8)) != nullptr;
         ok &= (c->ang_params = A((size_t)c->C * angular_param_bytes(p.precision))) != nullptr;
+        ok &= (c->ang_shift = (int4 *)A((size_t)c->nrep * sizeof(int4))) != nullptr;
     }
     if (!ok) {
         mpcd_destroy(c);

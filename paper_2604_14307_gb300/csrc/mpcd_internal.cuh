@@ -368,7 +368,9 @@ void launch_gather_out(const StepArgs &a, const uint32_t *vals, void *rec, void 
 enum : int { ANG_PRE = 0, ANG_POST = 1, ANG_PARAMS = 2, ANG_APPLY = 3 };
 constexpr int ANG_WORDS = 16;                 // int64 (P32) or double (P64) words per cell
 size_t angular_param_bytes(int precision);   // per cell: centre (3), w (3), padding
-void launch_angular(const StepArgs &a, int phase, void *words, void *params, int num_sms, cudaStream_t s);
+// shifts: [n_rep] per-replica grid shift of the collision, written by the ANG_PRE phase
+void launch_angular(const StepArgs &a, int phase, void *words, void *params, int4 *shifts, int num_sms,
+                    cudaStream_t s);
 
 // bodies and sites (kernels_bodies.cu)
 void launch_body_md(const StepArgs &a, cudaStream_t s);
