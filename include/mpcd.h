@@ -98,7 +98,8 @@ typedef struct {
 
 /* One independent periodic box; replicas are simulated together. */
 typedef struct {
-    int32_t L[3];             /* cells per edge (>= 3 each) */
+    int32_t L[3];             /* cells per edge (3 to 2047 each: the binning rule forms
+                                 floor(x 2^20) in 32 bits) */
     int64_t n_solvent;        /* solvent particles of this replica */
     int32_t n_bodies;
     int32_t stream_id;        /* >= 0, distinct within a context: the replica's random
