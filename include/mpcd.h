@@ -81,8 +81,11 @@ typedef struct {
                              rigid rotation v' = v* + w x r_c that restores its
                              angular momentum about its centre of mass (r_c on the
                              2^-20 lattice of the binning rule; least-norm w for
-                             collinear members).  Pure solvent only (no bodies:
-                             MPCD_ERR_ARG otherwise); steps run unfused.  0: off */
+                             collinear members).  Colloid sites take part like
+                             solvent; their corrected velocities enter the
+                             transfer to the body.  Needs one site mass for all
+                             shapes (MPCD_ERR_ARG otherwise); steps run unfused.
+                             0: off */
 } mpcd_params;
 
 /* A rigid discrete-particle template in its principal-axis frame with its

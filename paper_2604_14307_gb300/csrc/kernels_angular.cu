@@ -14,26 +14,28 @@
 // an integer, which makes the geometric sums exact.
 //
 // Passes around the plain collision of a step (all keyed on the same step):
-//   k_ang_sums<PRE>   before the rule: count, sum Q, sum Q_a Q_b, + sum Q x P, + sum P
-//   k_ang_sums<POST>  after it:                                  - sum Q x P*, - sum P*
-//   k_ang_params      per cell: centre, Pi and the angular-momentum change in
-//                     FP64, w by the adjugate of Pi (least-norm form for
-//                     collinear members); clears the words for the next collision
-//   k_ang_apply       v = v* + w' x (N Q - sum Q),  w' = w / (N 2^20)
-// The offset from the centre is formed as the exact integer N Q - sum Q: for
-// nearly collinear members w is large along their line while the offsets
-// across it are small, and an offset rounded in the working precision would
-// carry an error of order eps |w| into the velocity.
-// Word layout, SoA [ANG_WORDS][n_cells]:
-//   0 N; 1-3 sum Q; 4-9 sum Q_a Q_b (xx, yy, zz, xy, xz, yz);
-//   10-12 sum Q x (P - P*); 13-15 sum (P - P*).
-// P32: P = round(fl32(m v) 2^20), the momentum term of the plain cell words,
-// and every word an int64 sum (exact and independent of the order of the
+//   k_ang_shift       the grid shift of every replica (once per collision)
+//   k_ang_sums<PRE>   solvent, before the rule: count, sum Q, sum Q_a Q_b,
+//                     + sum Q x P, + sum P (the sites add theirs from the
+//                     thermalised velocities, kernels_bodies.cu)
+//   k_ang_sums<POST>  after the rule: - sum Q x P*, - sum P* (sites likewise)
+//   k_ang_params      per cell: centre of mass, Pi and the angular-momentum
+//                     change in FP64, w by the adjugate of Pi (least-norm form
+//                     for collinear members); clears the words
+//   k_ang_apply       solvent: v = v* + w' x (M Q - sum mu Q), w' = w / (M 2^20);
+//                     the site POST coupling applies the same to the sites
+//                     before it transfers their momentum change to the body
+// Word layout and record: AW_* and AngParams in mpcd_internal.cuh.  The
+// geometric sums are kept per species (solvent, sites) and exact; masses enter
+// in the per-cell solve (P32: mu = round(m 2^24), the quantised masses of the
+// cell words).  The offset from the centre is formed as the exact integer
+// M Q - sum mu Q: for nearly collinear members w is large along their line
+// while the offsets across it are small, and an offset rounded in the working
+// precision would carry an error of order eps |w| into the velocity.
+// P32: every word an int64 sum (exact and independent of the order of the
 // atomics; wrap-around of partial sums cancels as long as the final sum lies
-// within +-2^63).  P64: P = m v in double; the Q sums are exact integers in
-// double, the momentum sums FP64 atomics.
-// The solvent mass is uniform, so Pi = m 2^-40 (tr(C) I - C) with C the
-// lattice covariance sum Q_a Q_b - sum Q_a sum Q_b / N.
+// within +-2^63).  P64: the Q sums are exact integers in double, the momentum
+// sums FP64 atomics.
 #include <algorithm>
 
 #include "mpcd_internal.cuh"
@@ -41,16 +43,6 @@
 namespace mpcd {
 
 namespace {
-
-template <typename Real> struct AngWord;
-template <> struct AngWord<float> { typedef long long type; };
-template <> struct AngWord<double> { typedef double type; };
-
-__device__ __forceinline__ void ang_red(long long *p, long long v)
-{
-    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
-}
-__device__ __forceinline__ void ang_red(double *p, double v) { atomicAdd(p, v); }
 
 // X = floor(x 2^20) of the binning rule, as in the plain passes (box edges
 // below 2048 cells keep it within int32)
@@ -125,13 +117,14 @@ __device__ __forceinline__ void cells4(const Real (&x)[4], const Real (&y)[4], c
 // One warp per tile; each lane takes 4 consecutive particles (128-bit loads;
 // tiles start on multiples of 8 slots, and the slots past a replica's last
 // particle are allocated padding), merges runs of equal cells in registers and
-// issues one atomic per word and run.  Word k of particle j is term(k, j); PRE adds
-// words 0-15, POST subtracts the rule's new momentum terms from 10-15.
+// issues one atomic per word and run.  PRE adds the solvent's 16 terms, POST
+// subtracts the rule's new momentum terms.
 template <typename Real, bool PRE>
-__global__ void __launch_bounds__(256) k_ang_sums(StepArgs a, void *words, const int4 *shifts)
+__global__ void __launch_bounds__(256) k_ang_sums(StepArgs a)
 {
     typedef typename AngWord<Real>::type W;
-    W *w = reinterpret_cast<W *>(words);
+    W *w = reinterpret_cast<W *>(a.ang_words);
+    const int4 *shifts = a.ang_shift;
     const int64_t C = a.n_cells;
     const Real m = solvent_mass<Real>(a);
     const Real *X = reinterpret_cast<const Real *>(a.x), *Y = reinterpret_cast<const Real *>(a.y);
@@ -161,8 +154,12 @@ __global__ void __launch_bounds__(256) k_ang_sums(StepArgs a, void *words, const
                 join[j] = j + 1 < nv && c[j + 1] == c[j];
                 head[j] = j < nv && (j == 0 || c[j] != c[j - 1]);
             }
+            // the solvent's words: count, sum Q, sum Q_a Q_b (PRE only), then
+            // the momentum words; k indexes the 16 terms, wk the word
 #pragma unroll
-            for (int k = PRE ? 0 : 10; k < ANG_WORDS; ++k) {
+            for (int k = PRE ? 0 : 10; k < 16; ++k) {
+                const int wk = k == 0 ? AW_COUNT : k < 4 ? AW_SQ + k - 1 : k < 10 ? AW_QQ + k - 4
+                                                        : k < 13 ? AW_L + k - 10 : AW_P + k - 13;
                 W v[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -191,44 +188,56 @@ __global__ void __launch_bounds__(256) k_ang_sums(StepArgs a, void *words, const
                     if (join[j]) v[j] += v[j + 1];
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (head[j]) ang_red(w + k * C + c[j], v[j]);
+                    if (head[j]) ang_red(w + wk * C + c[j], v[j]);
             }
         }
     }
 }
 
-// per-cell record of the correction: sum Q, N and w' = w / (N 2^20)
-template <typename Real> struct AngParams;
-template <> struct AngParams<float> { uint32_t sq[3]; int32_t n; float w[3]; float pad; };
-template <> struct AngParams<double> { double sq[3]; double n; double w[3]; double pad; };
-static_assert(sizeof(AngParams<float>) == 32 && sizeof(AngParams<double>) == 64, "record sizes");
-
-// w from the words of one cell (lattice units: Q in 2^-20, P in pscale)
-template <typename W>
-__device__ void cell_omega(const W (&wd)[ANG_WORDS], double m, double pscale, double om[3])
+// record of one cell from its words.  mu_s, mu_b: the solvent and site mass
+// in the units of the form (P32: round(m 2^24), P64: m); pscale: the unit of
+// the P terms (P32: 2^-20, P64: 1); mscale: the unit of mu (P32: 2^-24, P64: 1).
+template <typename Real, typename W>
+__device__ void cell_record(const W (&wd)[ANG_WORDS], double mu_s, double mu_b, double pscale, double mscale,
+                            AngParams<Real> &o)
 {
-    om[0] = om[1] = om[2] = 0.0;
-    const double N = (double)wd[0];
-    if (N < 2.0) return;
-    const double iN = 1.0 / N;
-    const double sQ[3] = {(double)wd[1], (double)wd[2], (double)wd[3]};
-    const double Qc[3] = {sQ[0] * iN, sQ[1] * iN, sQ[2] * iN};
-    // lattice covariance C (exact sums; one rounding in the centre term)
+    const long long cnt = (long long)wd[AW_COUNT];
+    const double ns = (double)(cnt & 0xFFF), nb = (double)((cnt >> 12) & 0x3FF);
+    const double M = ns * mu_s + nb * mu_b;     // exact (integers below 2^53 in P32)
+    double sw[3];
+    for (int k = 0; k < 3; ++k) {
+        if constexpr (sizeof(Real) == 4) {
+            // exact in int64: mu Q sums below M 2^20
+            const long long v = (long long)mu_s * (long long)wd[AW_SQ + k] + (long long)mu_b * (long long)wd[AW_SQB + k];
+            o.sw[k] = v;
+            sw[k] = (double)v;
+        } else {
+            sw[k] = mu_s * (double)wd[AW_SQ + k] + mu_b * (double)wd[AW_SQB + k];
+            o.sw[k] = sw[k];
+        }
+        o.w[k] = (Real)0;
+    }
+    if constexpr (sizeof(Real) == 4) o.M = (long long)M;
+    else o.M = M;
+    o.pad = (Real)0;
+    if (ns + nb < 2.0) return;
+    const double iM = 1.0 / M;
+    const double Qc[3] = {sw[0] * iM, sw[1] * iM, sw[2] * iM};
+    // mass-weighted lattice covariance about the centre of mass
     double Cm[3][3];
-    Cm[0][0] = (double)wd[4] - sQ[0] * Qc[0];
-    Cm[1][1] = (double)wd[5] - sQ[1] * Qc[1];
-    Cm[2][2] = (double)wd[6] - sQ[2] * Qc[2];
-    Cm[0][1] = Cm[1][0] = (double)wd[7] - sQ[0] * Qc[1];
-    Cm[0][2] = Cm[2][0] = (double)wd[8] - sQ[0] * Qc[2];
-    Cm[1][2] = Cm[2][1] = (double)wd[9] - sQ[1] * Qc[2];
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int q = 0; q < 6; ++q) {
+        const double v = mu_s * (double)wd[AW_QQ + q] + mu_b * (double)wd[AW_QQB + q] - sw[ia[q]] * Qc[ib[q]];
+        Cm[ia[q]][ib[q]] = Cm[ib[q]][ia[q]] = v;
+    }
     const double tr = Cm[0][0] + Cm[1][1] + Cm[2][2];
-    // angular-momentum change about the centre, in units of 2^-20 pscale
-    const double dP[3] = {(double)wd[13], (double)wd[14], (double)wd[15]};
-    double dL[3] = {(double)wd[10] - (Qc[1] * dP[2] - Qc[2] * dP[1]),
-                    (double)wd[11] - (Qc[2] * dP[0] - Qc[0] * dP[2]),
-                    (double)wd[12] - (Qc[0] * dP[1] - Qc[1] * dP[0])};
     if (!(tr > 0.0)) return;                  // every member on one lattice point
-    // G = tr(C) I - C = Pi / (m 2^-40); solve G x = dL by its adjugate
+    // angular-momentum change about the centre (units 2^-20 pscale)
+    const double dP[3] = {(double)wd[AW_P], (double)wd[AW_P + 1], (double)wd[AW_P + 2]};
+    const double dL[3] = {(double)wd[AW_L] - (Qc[1] * dP[2] - Qc[2] * dP[1]),
+                          (double)wd[AW_L + 1] - (Qc[2] * dP[0] - Qc[0] * dP[2]),
+                          (double)wd[AW_L + 2] - (Qc[0] * dP[1] - Qc[1] * dP[0])};
+    // G = tr(C) I - C = Pi / (mscale 2^-40); solve G x = dL by its adjugate
     const double a00 = tr - Cm[0][0], a11 = tr - Cm[1][1], a22 = tr - Cm[2][2];
     const double a01 = -Cm[0][1], a02 = -Cm[0][2], a12 = -Cm[1][2];
     const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
@@ -249,19 +258,23 @@ __device__ void cell_omega(const W (&wd)[ANG_WORDS], double m, double pscale, do
             x[i] = (dL[i] - CdL * it) * it;
         }
     }
-    // Pi w = dL_phys: Pi = m 2^-40 G, dL_phys = 2^-20 pscale dL
-    const double s = pscale * 1048576.0 / m;
-    for (int k = 0; k < 3; ++k) om[k] = x[k] * s;
+    // Pi w = dL_phys with Pi = mscale 2^-40 G and dL_phys = 2^-20 pscale dL;
+    // the record keeps w' = w / (M 2^20)
+    const double s = pscale / (mscale * M);
+    for (int k = 0; k < 3; ++k) o.w[k] = (Real)(x[k] * s);
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(256) k_ang_params(StepArgs a, void *words, AngParams<Real> *params)
+__global__ void __launch_bounds__(256) k_ang_params(StepArgs a)
 {
     typedef typename AngWord<Real>::type W;
-    W *w = reinterpret_cast<W *>(words);
+    W *w = reinterpret_cast<W *>(a.ang_words);
+    AngParams<Real> *params = reinterpret_cast<AngParams<Real> *>(const_cast<void *>(a.ang_params));
     const int64_t C = a.n_cells;
-    const double m = sizeof(Real) == 4 ? (double)a.m_solvent_f : a.m_solvent;   // the mass of the P terms
-    const double pscale = sizeof(Real) == 4 ? 0x1p-20 : 1.0;
+    const bool p32 = sizeof(Real) == 4;
+    const double mu_s = p32 ? (double)a.qm_solvent : a.m_solvent;
+    const double mu_b = p32 ? (double)a.qm_site : a.m_site;
+    const double pscale = p32 ? 0x1p-20 : 1.0, mscale = p32 ? 0x1p-24 : 1.0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         W wd[ANG_WORDS];
 #pragma unroll
@@ -269,34 +282,17 @@ __global__ void __launch_bounds__(256) k_ang_params(StepArgs a, void *words, Ang
             wd[k] = w[k * C + c];
             w[k * C + c] = (W)0;
         }
-        double om[3];
-        cell_omega(wd, m, pscale, om);
-        const double n = (double)wd[0];
-        const double s = n >= 2.0 ? 1.0 / (n * 1048576.0) : 0.0;
         AngParams<Real> o;
-        for (int k = 0; k < 3; ++k) {
-            o.sq[k] = (decltype(o.sq[0]))wd[1 + k];
-            o.w[k] = (Real)(om[k] * s);
-        }
-        o.n = (decltype(o.n))wd[0];
-        o.pad = (Real)0;
+        cell_record<Real>(wd, mu_s, mu_b, pscale, mscale, o);
         params[c] = o;
     }
 }
 
-// exact integer offset N Q - sum Q (|.| < N 2^20) in the working precision
-__device__ __forceinline__ float offset_real(const AngParams<float> &p, int Q, int k)
-{
-    return ll2f((long long)p.n * Q - (long long)p.sq[k]);
-}
-__device__ __forceinline__ double offset_real(const AngParams<double> &p, int Q, int k)
-{
-    return p.n * (double)Q - p.sq[k];   // integers below 2^53: exact
-}
-
 template <typename Real>
-__global__ void __launch_bounds__(256) k_ang_apply(StepArgs a, const AngParams<Real> *params, const int4 *shifts)
+__global__ void __launch_bounds__(256) k_ang_apply(StepArgs a)
 {
+    const AngParams<Real> *params = reinterpret_cast<const AngParams<Real> *>(a.ang_params);
+    const int4 *shifts = a.ang_shift;
     const Real *X = reinterpret_cast<const Real *>(a.x), *Y = reinterpret_cast<const Real *>(a.y);
     const Real *Z = reinterpret_cast<const Real *>(a.z);
     Real *VX = reinterpret_cast<Real *>(a.vx), *VY = reinterpret_cast<Real *>(a.vy);
@@ -317,12 +313,9 @@ __global__ void __launch_bounds__(256) k_ang_apply(StepArgs a, const AngParams<R
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (j >= nv) break;
-                const AngParams<Real> p = params[c[j]];
-                const Real rc[3] = {offset_real(p, Q[j][0], 0), offset_real(p, Q[j][1], 1),
-                                    offset_real(p, Q[j][2], 2)};
-                vx[j] = vx[j] + (p.w[1] * rc[2] - p.w[2] * rc[1]);
-                vy[j] = vy[j] + (p.w[2] * rc[0] - p.w[0] * rc[2]);
-                vz[j] = vz[j] + (p.w[0] * rc[1] - p.w[1] * rc[0]);
+                Real v[3] = {vx[j], vy[j], vz[j]};
+                ang_correct(params[c[j]], Q[j], v);
+                vx[j] = v[0]; vy[j] = v[1]; vz[j] = v[2];
             }
             if (nv == 4) {
                 st4v(VX + i, vx); st4v(VY + i, vy); st4v(VZ + i, vz);
@@ -339,11 +332,11 @@ __global__ void __launch_bounds__(256) k_ang_apply(StepArgs a, const AngParams<R
 
 size_t angular_param_bytes(int precision)
 {
+    static_assert(sizeof(AngParams<float>) == 48 && sizeof(AngParams<double>) == 64, "record sizes");
     return precision == 1 ? sizeof(AngParams<float>) : sizeof(AngParams<double>);
 }
 
-void launch_angular(const StepArgs &a, int phase, void *words, void *params, int4 *shifts, int num_sms,
-                    cudaStream_t s)
+void launch_angular(const StepArgs &a, int phase, int num_sms, cudaStream_t s)
 {
     if (a.n_cells == 0) return;
     const int grid_p = std::max(1, num_sms * 16);
@@ -351,24 +344,24 @@ void launch_angular(const StepArgs &a, int phase, void *words, void *params, int
     const bool p32 = a.precision == 1;
     switch (phase) {
     case ANG_PRE:
+        k_ang_shift<<<(a.n_rep + 127) / 128, 128, 0, s>>>(a, a.ang_shift);
         if (a.n_tiles == 0) return;
-        k_ang_shift<<<(a.n_rep + 127) / 128, 128, 0, s>>>(a, shifts);
-        if (p32) k_ang_sums<float, true><<<grid_t, 256, 0, s>>>(a, words, shifts);
-        else k_ang_sums<double, true><<<grid_t, 256, 0, s>>>(a, words, shifts);
+        if (p32) k_ang_sums<float, true><<<grid_t, 256, 0, s>>>(a);
+        else k_ang_sums<double, true><<<grid_t, 256, 0, s>>>(a);
         break;
     case ANG_POST:
         if (a.n_tiles == 0) return;
-        if (p32) k_ang_sums<float, false><<<grid_t, 256, 0, s>>>(a, words, shifts);
-        else k_ang_sums<double, false><<<grid_t, 256, 0, s>>>(a, words, shifts);
+        if (p32) k_ang_sums<float, false><<<grid_t, 256, 0, s>>>(a);
+        else k_ang_sums<double, false><<<grid_t, 256, 0, s>>>(a);
         break;
     case ANG_PARAMS:
-        if (p32) k_ang_params<float><<<grid_p, 256, 0, s>>>(a, words, reinterpret_cast<AngParams<float> *>(params));
-        else k_ang_params<double><<<grid_p, 256, 0, s>>>(a, words, reinterpret_cast<AngParams<double> *>(params));
+        if (p32) k_ang_params<float><<<grid_p, 256, 0, s>>>(a);
+        else k_ang_params<double><<<grid_p, 256, 0, s>>>(a);
         break;
     case ANG_APPLY:
         if (a.n_tiles == 0) return;
-        if (p32) k_ang_apply<float><<<grid_t, 256, 0, s>>>(a, reinterpret_cast<const AngParams<float> *>(params), shifts);
-        else k_ang_apply<double><<<grid_t, 256, 0, s>>>(a, reinterpret_cast<const AngParams<double> *>(params), shifts);
+        if (p32) k_ang_apply<float><<<grid_t, 256, 0, s>>>(a);
+        else k_ang_apply<double><<<grid_t, 256, 0, s>>>(a);
         break;
     default:
         break;

@@ -689,7 +689,44 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
 // POST coupling: site collision and the per-warp partial sums of the
 // momentum dP = sum m (v' - v) and angular momentum dL = sum d x m (v' - v)
 // transferred to the body (Eqs. 3-4); k_body_impulse adds them in FP64.
+// the collision rule for one site: v -> vn with the parameters p of its cell
 template <typename Real>
+__device__ __forceinline__ void site_rule(const StepArgs &a, const DevReplica &r, int64_t step, int64_t g,
+                                          const Real (&v)[3], const Real (&p)[8], Real m, Real (&vn)[3])
+{
+    vn[0] = v[0]; vn[1] = v[1]; vn[2] = v[2];
+    if (p[3] >= Real(0)) {
+        const Real kT = (Real)a.kT, ca = (Real)a.cos_a, sa = (Real)a.sin_a;
+        if (a.rule == 0) {
+            const Real w[3] = {v[0] - p[0], v[1] - p[1], v[2] - p[2]};
+            const Real nd = p[4] * w[0] + p[5] * w[1] + p[6] * w[2];
+            const Real cx = p[5] * w[2] - p[6] * w[1], cy = p[6] * w[0] - p[4] * w[2];
+            const Real cz = p[4] * w[1] - p[5] * w[0];
+            const Real tt = nd * (Real(1) - ca);
+            vn[0] = p[0] + p[3] * (w[0] * ca + cx * sa + p[4] * tt);
+            vn[1] = p[1] + p[3] * (w[1] * ca + cy * sa + p[5] * tt);
+            vn[2] = p[2] + p[3] * (w[2] * ca + cz * sa + p[6] * tt);
+        } else {
+            Real xi[3];
+            normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
+            const Real sc = sqrt(kT / m);
+            for (int k = 0; k < 3; ++k) vn[k] = p[k] + sc * xi[k] - p[4 + k];
+        }
+    }
+}
+
+// lattice offset of a stored site position inside its shifted cell (+a variants)
+template <typename Real>
+__device__ __forceinline__ void site_lattice_q(const Real (&x)[3], int4 S, int (&Q)[3])
+{
+    Q[0] = ang_lattice_q(x[0], S.x);
+    Q[1] = ang_lattice_q(x[1], S.y);
+    Q[2] = ang_lattice_q(x[2], S.z);
+}
+
+// POST coupling; ANG: with the +a correction of the site's cell applied to the
+// rule's velocity before the momentum change is taken
+template <typename Real, bool ANG>
 __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_post(StepArgs a)
 {
     __shared__ Real sPose[POSE_W];
@@ -703,7 +740,6 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
     Pose<Real> P;
     for (int k = 0; k < 9; ++k) P.Q[k] = sPose[k];
     for (int k = 0; k < 3; ++k) { P.R[k] = sPose[9 + k]; P.V[k] = 0; P.W[k] = 0; }
-    const Real kT = (Real)a.kT, ca = (Real)a.cos_a, sa = (Real)a.sin_a;
     const Real *SV = reinterpret_cast<const Real *>(a.site_v);
     const int64_t NS = a.n_sites;
     int bad = 0;
@@ -713,26 +749,17 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
         Real d[3], x[3];
         site_geom(a, t, P, r, d, x, bad);
         const Real v[3] = {SV[g], SV[NS + g], SV[2 * NS + g]};
-        Real vn[3] = {v[0], v[1], v[2]};
+        Real vn[3];
         Real p[8];
-        load_cell<Real>(a, (int64_t)r.cell_base + a.site_cell[g], p);
+        const int64_t cell = (int64_t)r.cell_base + a.site_cell[g];
+        load_cell<Real>(a, cell, p);
         const Real m = site_mass<Real>(a, t);
-        if (p[3] >= Real(0)) {
-            if (a.rule == 0) {
-                const Real w[3] = {v[0] - p[0], v[1] - p[1], v[2] - p[2]};
-                const Real nd = p[4] * w[0] + p[5] * w[1] + p[6] * w[2];
-                const Real cx = p[5] * w[2] - p[6] * w[1], cy = p[6] * w[0] - p[4] * w[2];
-                const Real cz = p[4] * w[1] - p[5] * w[0];
-                const Real tt = nd * (Real(1) - ca);
-                vn[0] = p[0] + p[3] * (w[0] * ca + cx * sa + p[4] * tt);
-                vn[1] = p[1] + p[3] * (w[1] * ca + cy * sa + p[5] * tt);
-                vn[2] = p[2] + p[3] * (w[2] * ca + cz * sa + p[6] * tt);
-            } else {
-                Real xi[3];
-                normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
-                const Real sc = sqrt(kT / m);
-                for (int k = 0; k < 3; ++k) vn[k] = p[k] + sc * xi[k] - p[4 + k];
-            }
+        site_rule<Real>(a, r, step, g, v, p, m, vn);
+        if constexpr (ANG) {
+            const Real xs[3] = {x[0], x[1], x[2]};
+            int Q[3];
+            site_lattice_q(xs, a.ang_shift[B.rep], Q);
+            ang_correct(reinterpret_cast<const AngParams<Real> *>(a.ang_params)[cell], Q, vn);
         }
         const Real dp[3] = {m * (vn[0] - v[0]), m * (vn[1] - v[1]), m * (vn[2] - v[2])};
         acc[0] += dp[0]; acc[1] += dp[1]; acc[2] += dp[2];
@@ -787,8 +814,93 @@ void launch_sites_pre(const StepArgs &a, int max_sites, cudaStream_t s)
 void launch_sites_post(const StepArgs &a, int, cudaStream_t s)
 {
     if (a.n_bodies == 0) return;
-    if (a.precision == 1) k_sites_post<float><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
-    else k_sites_post<double><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+    const bool ang = a.ang_params != nullptr;
+    if (a.precision == 1) {
+        if (ang) k_sites_post<float, true><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+        else k_sites_post<float, false><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+    } else {
+        if (ang) k_sites_post<double, true><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+        else k_sites_post<double, false><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+    }
+}
+
+// +a variants: the sites' contributions to the angular words of their cells,
+// one CTA per body.  PRE: count, sum Q, sum Q_a Q_b, + Q x P, + P from the
+// thermalised velocities of Eq. 7; POST: - Q x P*, - P* from the rule's
+// velocities (recomputed with the same arithmetic as the POST coupling).
+__device__ __forceinline__ long long site_mom_term(float m, float v) { return q20(__fmul_rn(m, v)); }
+__device__ __forceinline__ double site_mom_term(double m, double v) { return m * v; }
+
+template <typename Real, bool PRE>
+__global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_ang_sites(StepArgs a)
+{
+    typedef typename AngWord<Real>::type W;
+    __shared__ Real sPose[POSE_W];
+    const DevBody &B = a.bodies[blockIdx.x];
+    const int64_t site_begin = B.site_begin;
+    const DevShape sh = a.shapes[B.shape];
+    const DevReplica r = a.reps[B.rep];
+    const int64_t step = *a.d_step;
+    const int4 S = a.ang_shift[B.rep];
+    W *w = reinterpret_cast<W *>(a.ang_words);
+    const int64_t C = a.n_cells;
+    if (threadIdx.x < POSE_W) sPose[threadIdx.x] = pose_ptr(a, blockIdx.x, Real(0))[threadIdx.x];
+    __syncthreads();
+    Pose<Real> P;
+    for (int k = 0; k < 9; ++k) P.Q[k] = sPose[k];
+    for (int k = 0; k < 3; ++k) { P.R[k] = sPose[9 + k]; P.V[k] = 0; P.W[k] = 0; }
+    const Real *SV = reinterpret_cast<const Real *>(a.site_v);
+    const int64_t NS = a.n_sites;
+    int bad = 0;
+    for (int j = threadIdx.x; j < sh.n_sites; j += blockDim.x) {
+        const int64_t t = sh.site_begin + j, g = site_begin + j;
+        Real d[3], x[3];
+        site_geom(a, t, P, r, d, x, bad);
+        const Real v[3] = {SV[g], SV[NS + g], SV[2 * NS + g]};
+        const int64_t cell = (int64_t)r.cell_base + a.site_cell[g];
+        const Real m = site_mass<Real>(a, t);
+        Real u[3] = {v[0], v[1], v[2]};
+        if (!PRE) {
+            Real p[8];
+            load_cell<Real>(a, cell, p);
+            site_rule<Real>(a, r, step, g, v, p, m, u);
+        }
+        const Real xs[3] = {x[0], x[1], x[2]};
+        int Qi[3];
+        site_lattice_q(xs, S, Qi);
+        const W q[3] = {(W)Qi[0], (W)Qi[1], (W)Qi[2]};
+        const W Pm[3] = {(W)site_mom_term(m, u[0]), (W)site_mom_term(m, u[1]), (W)site_mom_term(m, u[2])};
+        const W L[3] = {q[1] * Pm[2] - q[2] * Pm[1], q[2] * Pm[0] - q[0] * Pm[2], q[0] * Pm[1] - q[1] * Pm[0]};
+        const W sg = PRE ? (W)1 : (W)-1;
+        if (PRE) {
+            ang_red(w + AW_COUNT * C + cell, (W)4096);
+            for (int k = 0; k < 3; ++k) ang_red(w + (AW_SQB + k) * C + cell, q[k]);
+            ang_red(w + (AW_QQB + 0) * C + cell, q[0] * q[0]);
+            ang_red(w + (AW_QQB + 1) * C + cell, q[1] * q[1]);
+            ang_red(w + (AW_QQB + 2) * C + cell, q[2] * q[2]);
+            ang_red(w + (AW_QQB + 3) * C + cell, q[0] * q[1]);
+            ang_red(w + (AW_QQB + 4) * C + cell, q[0] * q[2]);
+            ang_red(w + (AW_QQB + 5) * C + cell, q[1] * q[2]);
+        }
+        for (int k = 0; k < 3; ++k) {
+            ang_red(w + (AW_L + k) * C + cell, sg * L[k]);
+            ang_red(w + (AW_P + k) * C + cell, sg * Pm[k]);
+        }
+    }
+    if (bad) atomicOr(a.d_err, ERR_POSITION);
+}
+
+void launch_angular_sites(const StepArgs &a, int phase, cudaStream_t s)
+{
+    if (a.n_bodies == 0) return;
+    const bool p32 = a.precision == 1;
+    if (phase == ANG_PRE) {
+        if (p32) k_ang_sites<float, true><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+        else k_ang_sites<double, true><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+    } else if (phase == ANG_POST) {
+        if (p32) k_ang_sites<float, false><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+        else k_ang_sites<double, false><<<a.n_bodies, SITE_THREADS, 0, s>>>(a);
+    }
 }
 
 void launch_body_impulse(const StepArgs &a, cudaStream_t s)

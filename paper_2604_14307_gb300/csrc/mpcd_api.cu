@@ -116,7 +116,7 @@ struct mpcd_ctx {
     double *rn_tot = nullptr;                   // [0] momentum, [1] pairs (as long long)
     double *d_profile = nullptr;                // [2][PROFILE bins] velocity-profile sums
     void *ang_words = nullptr;                  // [ANG_WORDS][C] angular-momentum sums (+a variants)
-    void *ang_params = nullptr;                 // [C] sum Q, N and w' of the +a correction
+    void *ang_params = nullptr;                 // [C] AngParams records of the +a correction
     int4 *ang_shift = nullptr;                  // [nrep] grid shift of the current collision
     double f_ext[3] = {0.0, 0.0, 0.0};          // constant force on every body (one replica)
     VacfArgs vacf{};                            // velocity autocorrelations (n_lags 0: off)
@@ -191,6 +191,10 @@ StepArgs make_args(const mpcd_ctx *c)
     a.sin_af = (float)a.sin_a;
     a.qm_solvent = (long long)std::llrint((double)a.m_solvent_f * 16777216.0);
     a.m_site_f = (float)c->m_site;
+    a.m_site = c->m_site;
+    a.ang_words = c->ang_words;
+    a.ang_params = c->ang_params;
+    a.ang_shift = c->ang_shift;
     a.qm_site = (long long)std::llrint((double)a.m_site_f * 16777216.0);
     a.reps = c->d_reps;
     a.n_rep = c->nrep;
@@ -505,7 +509,8 @@ int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
     return MPCD_OK;
 }
 
-// one pass of the +a correction (kernels_angular.cu)
+// one pass of the +a correction (kernels_angular.cu; the sites' sums in
+// kernels_bodies.cu)
 int k_ang(mpcd_ctx *c, int phase, cudaStream_t s)
 {
     static const char *names[] = {"angular_pre", "angular_post", "angular_params", "angular_apply"};
@@ -513,11 +518,16 @@ int k_ang(mpcd_ctx *c, int phase, cudaStream_t s)
     // cell words written or read once, the per-cell records
     const double N = (double)c->Ns, C = (double)c->C, r = c->realsz;
     const double rec = (double)angular_param_bytes(c->prm.precision);
-    const double bytes[] = {N * 6 * r + C * ANG_WORDS * 8, N * 6 * r + C * 6 * 8,
+    const double bytes[] = {N * 6 * r + C * 16 * 8, N * 6 * r + C * 6 * 8,
                             C * (2.0 * ANG_WORDS * 8 + rec), N * 9 * r + C * rec};
     StepArgs a = make_args(c);
-    return timed(c, names[phase], bytes[phase], s,
-                 [&] { launch_angular(a, phase, c->ang_words, c->ang_params, c->ang_shift, c->num_sms, s); });
+    int e = timed(c, names[phase], bytes[phase], s, [&] { launch_angular(a, phase, c->num_sms, s); });
+    if (!e && c->B > 0 && (phase == ANG_PRE || phase == ANG_POST)) {
+        const double sb = (double)c->Nsite * (3.0 * r + 4.0);
+        e = timed(c, phase == ANG_PRE ? "angular_sites_pre" : "angular_sites_post", sb, s,
+                  [&] { launch_angular_sites(a, phase, s); });
+    }
+    return e;
 }
 
 // the unpipelined collision of the solvent at the current step (a2, a5-a7):
@@ -701,7 +711,8 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
             tm.push_back(d.m[j]);
             // the P32 cell record counts sites and needs one site mass per context
             if (c->m_site == 0.0) c->m_site = d.m[j];
-            if (p.precision == MPCD_P32 && d.m[j] != c->m_site) {
+            // (so do the +a variants, whose cell sums are kept per species)
+            if ((p.precision == MPCD_P32 || p.angular) && d.m[j] != c->m_site) {
                 delete c;
                 return MPCD_ERR_ARG;
             }
@@ -743,8 +754,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     for (int r = 0; r < n_replicas; ++r) {
         const mpcd_replica_desc &d = replicas[r];
         if (d.L[0] < 3 || d.L[1] < 3 || d.L[2] < 3 || d.L[0] > 2047 || d.L[1] > 2047 || d.L[2] > 2047 ||
-            d.n_solvent < 0 || d.n_bodies < 0 || (d.n_bodies > 0 && !d.body_shape) || d.stream_id < 0 ||
-            (p.angular && d.n_bodies > 0)) {
+            d.n_solvent < 0 || d.n_bodies < 0 || (d.n_bodies > 0 && !d.body_shape) || d.stream_id < 0) {
             delete c;
             return MPCD_ERR_ARG;
         }

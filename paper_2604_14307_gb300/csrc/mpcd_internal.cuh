@@ -87,6 +87,7 @@ struct StepArgs {
     float kTf, dtf, m_solvent_f, cos_af, sin_af;
     long long qm_solvent, qm_site;  // round(m 2^24) of the solvent and of the sites (P32)
     float m_site_f;                 // site mass of the P32 form (uniform)
+    double m_site;                  // the same in double (the +a variants need a uniform site mass)
     const DevReplica *reps;
     int32_t n_rep;
     const Tile *tiles;              // solvent tiles
@@ -131,6 +132,10 @@ struct StepArgs {
     int32_t step_offset;            // added to *d_step by the site PRE pass (1 when it runs
                                     // for the next step before the counter advances)
     int *d_err;
+    // angular-momentum-conserving variants (null when off)
+    void *ang_words;                // [ANG_WORDS][n_cells]
+    const void *ang_params;         // [n_cells] AngParams records
+    int4 *ang_shift;                // [n_rep] grid shift of the current collision
 };
 
 // ---------------------------------------------------------------------------
@@ -364,13 +369,63 @@ void launch_keys_out(const StepArgs &a, uint32_t *keys, uint32_t *vals, int64_t 
 void launch_gather_out(const StepArgs &a, const uint32_t *vals, void *rec, void *xa, void *va, int64_t n_rows,
                        int64_t nslots, int num_sms, cudaStream_t s);
 
-// angular-momentum-conserving collision variants of the solvent (kernels_angular.cu)
+// angular-momentum-conserving collision variants (kernels_angular.cu for the
+// solvent and the per-cell solve, kernels_bodies.cu for the sites).
+// Cell words, SoA [ANG_WORDS][n_cells], int64 (P32) or double (P64); Q is a
+// member's integer lattice offset inside its shifted cell (units 2^-20), P its
+// momentum term (P32: round(fl32(m v) 2^20); P64: m v):
+enum : int { AW_COUNT = 0,      // 1 per solvent particle, 2^12 per site
+             AW_SQ = 1,         // 1-3   sum Q of the solvent
+             AW_SQB = 4,        // 4-6   sum Q of the sites
+             AW_QQ = 7,         // 7-12  sum Q_a Q_b of the solvent (xx, yy, zz, xy, xz, yz)
+             AW_QQB = 13,       // 13-18 the same of the sites
+             AW_L = 19,         // 19-21 sum Q x (P - P*)
+             AW_P = 22,         // 22-24 sum (P - P*)
+             ANG_WORDS = 25 };
 enum : int { ANG_PRE = 0, ANG_POST = 1, ANG_PARAMS = 2, ANG_APPLY = 3 };
-constexpr int ANG_WORDS = 16;                 // int64 (P32) or double (P64) words per cell
-size_t angular_param_bytes(int precision);   // per cell: centre (3), w (3), padding
-// shifts: [n_rep] per-replica grid shift of the collision, written by the ANG_PRE phase
-void launch_angular(const StepArgs &a, int phase, void *words, void *params, int4 *shifts, int num_sms,
-                    cudaStream_t s);
+
+// Per-cell record of the correction: the mass-weighted lattice sums sw = sum mu Q,
+// the cell mass M = sum mu (mu = round(m 2^24) in P32, m in P64) and
+// w' = w / (M 2^20); a member's offset from the centre of mass is (M Q - sw),
+// an exact integer in P32 (|.| < M 2^20 < 2^63 for cell masses below 2^19).
+template <typename Real> struct AngParams;
+template <> struct AngParams<float> { long long sw[3]; long long M; float w[3]; float pad; };
+template <> struct AngParams<double> { double sw[3]; double M; double w[3]; double pad; };
+
+__device__ __forceinline__ int ang_lattice_q(float x, int S) { return (__float2int_rd(x * 1048576.0f) - S) & 0xFFFFF; }
+__device__ __forceinline__ int ang_lattice_q(double x, int S) { return (__double2int_rd(x * 1048576.0) - S) & 0xFFFFF; }
+__device__ __forceinline__ float ang_offset(const AngParams<float> &p, int Q, int k)
+{
+    return ll2f(p.M * (long long)Q - p.sw[k]);
+}
+__device__ __forceinline__ double ang_offset(const AngParams<double> &p, int Q, int k)
+{
+    return p.M * (double)Q - p.sw[k];
+}
+// v += w' x (M Q - sw) for a member with lattice offset Q
+template <typename Real>
+__device__ __forceinline__ void ang_correct(const AngParams<Real> &p, const int (&Q)[3], Real (&v)[3])
+{
+    const Real rc[3] = {ang_offset(p, Q[0], 0), ang_offset(p, Q[1], 1), ang_offset(p, Q[2], 2)};
+    v[0] = v[0] + (p.w[1] * rc[2] - p.w[2] * rc[1]);
+    v[1] = v[1] + (p.w[2] * rc[0] - p.w[0] * rc[2]);
+    v[2] = v[2] + (p.w[0] * rc[1] - p.w[1] * rc[0]);
+}
+__device__ __forceinline__ void ang_red(long long *p, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ void ang_red(double *p, double v) { atomicAdd(p, v); }
+template <typename Real> struct AngWord;
+template <> struct AngWord<float> { typedef long long type; };
+template <> struct AngWord<double> { typedef double type; };
+
+size_t angular_param_bytes(int precision);
+// solvent phases and the per-cell solve; ANG_PRE also writes a.ang_shift
+void launch_angular(const StepArgs &a, int phase, int num_sms, cudaStream_t s);
+// the sites' sums (ANG_PRE: thermalised velocities; ANG_POST: the rule's velocities);
+// the correction itself is applied by the site POST coupling when a.ang_params is set
+void launch_angular_sites(const StepArgs &a, int phase, cudaStream_t s);
 
 // bodies and sites (kernels_bodies.cu)
 void launch_body_md(const StepArgs &a, cudaStream_t s);

@@ -1,6 +1,5 @@
 """GPU tests of the angular-momentum-conserving collision variants (SRD+a,
-MPCD-AT+a; the modification of the rules Sec. II.A cites) for the pure
-solvent, through the C ABI.
+MPCD-AT+a; the modification of the rules Sec. II.A cites), through the C ABI.
 
 * One collision from the same state as the oracle, through the unpipelined
   calls (stream, couple, collide, couple): positions bit-exact (P32) or
@@ -11,12 +10,18 @@ solvent, through the C ABI.
   precision, so it carries a rounding of order eps |w_c| |r_c| with
   |r_c| < sqrt(3); w_c is large only in the rare cells whose members are
   nearly collinear.
+* With colloids: the sites take part in the correction and their corrected
+  velocities enter the transfer (Eqs. 3-5).  Solvent velocities within the bar
+  above; each body's momentum and angular momentum within the sum of its
+  sites' bars, tol sum_j m_j (|v'_j| + 1 + |w_c(j)|) (times |d_j| for L), which
+  the per-site bar implies by the triangle inequality.
 * On the GPU's own data: in every cell the momentum and the angular momentum
   about the centre of mass (lattice positions) are unchanged to float32
   rounding, which the plain rule breaks.
 * mpcd_step over two steps (graph-captured) gives bit-identical state to the
   unpipelined calls repeated.
-* Argument checks: the variant with colloids, and in the static collision.
+* Argument checks: the variant with shapes of different site masses, an
+  invalid flag.
 """
 import numpy as np
 import pytest
@@ -88,6 +93,44 @@ def test_one_collision_matches_oracle(B, rule, thermostat, prec, L):
     O.stream(o0, s0)
     O.collide(o0, s0, trace=False)
     assert np.max(np.abs(g.v - s0.v)) > 0.1
+
+
+def suspension_box(rule, prec, seed=6):
+    prm = I.Params(rule=rule, thermostat=1, precision=prec, seed=seed, angular=1)
+    return I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [(12, 16, 12)], 5.0, [[0, 0, 0]], "suspension",
+                          placement_seed=seed)
+
+
+@pytest.mark.parametrize("rule,prec", [(I.SRD, I.P32), (I.AT, I.P32), (I.SRD, I.P64), (I.AT, I.P64)])
+def test_one_collision_with_colloid_sites_matches_oracle(B, rule, prec):
+    system = suspension_box(rule, prec)
+    st = I.initial_state(system)
+    g, _ = gpu_one_collision(B, system, st)
+
+    osys = O.OracleSystem(system)
+    ost = O.OracleState(osys, st)
+    O.stream(osys, ost)
+    P0 = ost.P.copy()
+    tr = O.collide(osys, ost)
+    tol = TOL[prec]
+    wc = np.linalg.norm(tr["cell_omega"], axis=1)
+    # solvent
+    w = wc[tr["cell_solvent"]]
+    err = np.abs(g.v - ost.v)
+    assert np.all(err <= tol * (np.abs(ost.v) + 1.0 + w[:, None])), (err / (np.abs(ost.v) + 1 + w[:, None])).max()
+    # bodies: the transfer of the corrected site velocities
+    ns = osys.n_sites
+    vpost = tr["site_vpost"].reshape(-1, 3)[:ns]
+    ws = wc[tr["cell_site"][:ns]]
+    m = np.concatenate([system.shapes[0].m for _ in range(osys.n_bodies)])
+    per_site = tol * m * (np.abs(vpost).max(1) + 1.0 + ws)
+    sb = osys.site_base
+    for b in range(osys.n_bodies):
+        bar_p = per_site[sb[b]:sb[b + 1]].sum()
+        assert np.all(np.abs(g.P[b] - ost.P[b]) <= bar_p + tol * np.abs(ost.P[b])), b
+        bar_l = 2.0 * bar_p                          # |d_j| = radius 2
+        assert np.all(np.abs(g.Lm[b] - ost.Lm[b]) <= bar_l + tol * np.abs(ost.Lm[b])), b
+    assert np.max(np.abs(ost.P - P0)) > 1e-3            # the collision moved the bodies
 
 
 def lattice(x, S):
@@ -162,12 +205,17 @@ def test_step_equals_unpipelined_calls(B, rule, thermostat):
 
 
 def test_variant_arguments_are_checked(B):
-    prm = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=3, angular=1)
-    with_sphere = I.build_system(prm, [I.sphere_shape(2.0, 2, 5.0)], [(12, 12, 12)], 5.0, [[0]], "suspension",
-                                 placement_seed=3)
-    with pytest.raises(B.MPCDError) as e:
-        B.Simulation(with_sphere)
-    assert e.value.status == B.MPCD_ERR_ARG
+    # the plain FP64 form accepts shapes of different site masses; the +a variants do not
+    two = [I.sphere_shape(2.0, 2, 5.0), I.sphere_shape(2.0, 2, 3.0)]
+    for angular, ok in ((0, True), (1, False)):
+        prm = I.Params(rule=I.SRD, thermostat=1, precision=I.P64, seed=3, angular=angular)
+        box = I.build_system(prm, two, [(16, 16, 16)], 5.0, [[0, 1]], "two_masses", placement_seed=3)
+        if ok:
+            B.Simulation(box).close()
+        else:
+            with pytest.raises(B.MPCDError) as e:
+                B.Simulation(box)
+            assert e.value.status == B.MPCD_ERR_ARG
     bad = I.Params(rule=I.SRD, thermostat=1, precision=I.P32, seed=3, angular=2)
     box = I.build_system(bad, [I.sphere_shape(2.0, 2, 5.0)], [(8, 8, 8)], 5.0, [[]], "solvent_only",
                          placement_seed=3)
