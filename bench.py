@@ -59,8 +59,8 @@ def args_():
                     help="collision rule of the workload: SRD with the cell thermostat (the benchmark) or "
                          "MPCD-AT (for the ALU-side measurement of the Philox/Box-Muller path)")
     ap.add_argument("--angular", action="store_true",
-                    help="angular-momentum-conserving variant of the rule (SRD+a / MPCD-AT+a); pure solvent "
-                         "only (--workload solvent_L200)")
+                    help="angular-momentum-conserving variant of the rule (SRD+a / MPCD-AT+a) on the "
+                         "suspension or the pure solvent (--workload solvent_L200)")
     ap.add_argument("--no-protocols", action="store_true",
                     help="skip the transport-protocol measurements (momentum exchange, sedimentation, VACF)")
     return ap.parse_args()
@@ -337,10 +337,14 @@ def main():
             name = f"suspension_L120_phi{a.phi:g}_d6_162sites_density5_SRD130_thermostat"
             return I.suspension(120, 5.0, a.phi, 3.0, 2, 5.0, I.SRD, 1, precision, seed=seed, name=name), name
         w = WORKLOAD if a.rule == "srd" else WORKLOAD.replace("SRD130_thermostat", "MPCD-AT")
-        return I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, rule, thermo, precision, seed=seed, name=w), w
+        sysm = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, rule, thermo, precision, seed=seed, name=w)
+        if a.angular:
+            sysm.params.angular = 1
+            w += "+a"
+        return sysm, w
 
     system, workload = make_system(I.P32)
-    default_workload = a.workload == "suspension"
+    default_workload = a.workload == "suspension" and not a.angular
     state = I.initial_state(system)
     n_upd = system.n_solvent + system.n_sites
 
@@ -473,7 +477,7 @@ def main():
                  if system.params.rule == I.SRD else "MPCD-AT (Andersen thermostat rule)")
     if getattr(system.params, "angular", 0):
         rule_note += ", angular-momentum-conserving (+a, unfused step)"
-    if default_workload:
+    if a.workload == "suspension":
         config = {"workload": workload, "L": L, "density": 10, "phi": 0.3, "colloid_radius": 4.0}
     else:
         config = {"workload": workload, "n_replicas": system.n_rep}
