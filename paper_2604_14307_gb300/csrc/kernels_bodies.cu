@@ -20,7 +20,12 @@
 //               segmented reduction of dP = sum m (v' - v) and
 //               dL = sum d x m (v' - v) (Eqs. 3-4) into the body's momenta;
 //               the sites are reset to rigid motion (Eq. 5) implicitly, since
-//               the next step recomputes them from P and L.
+//               the next step recomputes them from P and L.  The ANG instance
+//               (angular-momentum-conserving variants) adds the cell's
+//               rigid-rotation correction to the rule's velocity first.
+// k_ang_sites   the sites' terms of the +a cell words: before the rule from
+//               the thermalised velocities, after it from the rule's
+//               velocities (recomputed with the POST coupling's arithmetic).
 // This file is compiled without fused multiply-add so that the FP64 body and
 // site-position arithmetic rounds the same way as the oracle.
 #include "mpcd_internal.cuh"

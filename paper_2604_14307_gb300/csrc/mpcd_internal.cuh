@@ -20,6 +20,9 @@
 //   protocols (allocated on first use) the exchange's key histogram, member
 //             lists and candidates; the velocity-profile sums; the per-body
 //             autocorrelation rings and sums.
+//   +a        (angular-momentum-conserving variants only) ANG_WORDS more words
+//             per cell, one AngParams record per cell, one grid shift per
+//             replica.
 #pragma once
 
 #include <cuda_runtime.h>
