@@ -1,6 +1,7 @@
-// Angular-momentum-conserving variants of the collision rules for the solvent
-// (SRD+a and MPCD-AT+a: the modification of the rules that Sec. II.A of
-// arXiv 2604.14307 cites from Noguchi and Gompper).
+// Angular-momentum-conserving variants of the collision rules (SRD+a and
+// MPCD-AT+a: the modification of the rules that Sec. II.A of arXiv 2604.14307
+// cites from Noguchi and Gompper): the solvent's passes and the per-cell solve;
+// the colloid sites' share lives beside the other site kernels.
 //
 // After the plain rule has produced v*, every cell with two or more members
 // gets the rigid rotation v' = v* + w x r_c that gives back its angular
