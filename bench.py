@@ -146,26 +146,72 @@ def recorded_traffic(kernel: str):
     return e if h == e.get("source_sha256") else None
 
 
-def cpu_baseline(steps: int = 8, L: int = 80):
-    """The FP64 oracle as it stands, one host core, on a bounded sample of the
-    workload: an L=80 box with the same density, volume fraction, colloid
-    radius and 642-site shells (5.5M particle-updates per step)."""
+def host_cpu():
+    """(threads this process may use, CPU model) of the host."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return len(os.sched_getaffinity(0)), model or "unknown"
+
+
+def cpu_baseline(Bd, steps: int = 6, L: int = 80):
+    """The plain FP64 oracle as it stands, one host core, on a bounded sample of
+    the workload: an L=80 box with the same density, volume fraction, colloid
+    radius and 642-site shells (5.5M particle-updates per step).  The first of
+    its steps also serves as the FP64 reference of one GPU step of the FP32
+    form from the same state (oracle.parity: the FP32 form's error against the
+    FP64 method on this sample)."""
     import oracle as O
+    from oracle import parity as OP
     from paper_2604_14307_gb300 import inputs as I
     s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1, name="sample")
     st = I.initial_state(s)
-    osys = O.OracleSystem(s)
-    ost = O.OracleState(osys, st)
     n = s.n_solvent + s.n_sites
-    times = []
-    for _ in range(steps):
+    t0 = time.perf_counter()
+    ref = OP.fp64_reference(s, st)          # one FP64 step: stream, then the collision with its trace
+    times = [time.perf_counter() - t0]
+    osys, ost, _ = ref
+    ost_run = O.OracleState(osys, st)
+    O.step(osys, ost_run, 1)                # the same step without the trace (not timed)
+    for _ in range(steps - 1):
         t0 = time.perf_counter()
-        O.step(osys, ost, 1)
+        O.step(osys, ost_run, 1)
         times.append(time.perf_counter() - t0)
+    # the FP32 form on the GPU, one unpipelined step from the same state
+    sim = Bd.Simulation(s, sort_period=-1)
+    sim.set_debug(True)
+    sim.set_state(st)
+    sim.stream()
+    sim.couple(Bd.MPCD_PRE)
+    sim.collide()
+    d = sim.debug_cells()
+    sim.couple(Bd.MPCD_POST)
+    g = sim.get_state()
+    sim.close()
+    par = OP.compare(s, st, g, d["site_cell"], d["shift"], ref=ref)
+    cores, model = host_cpu()
     return {"value": n / float(np.median(times)), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} FP64-oracle step(s) of an L={L} box with the workload's density, "
+            "mode": "plain FP64 (no float32 decision, no fixed-point word)",
+            "host_threads": cores, "cpu_model": model,
+            "sample": f"{steps} plain-FP64 oracle step(s) of an L={L} box with the workload's density, "
                       f"phi, radius and sites ({n} particle-updates per step), median time",
-            "seconds": float(sum(times))}
+            "seconds": float(sum(times))}, par
 
 
 def body_protocols(sim, stream, steps: int = 20):
@@ -270,7 +316,7 @@ def run_reference(a, ws, rank):
     L = 60
     s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1, name="sample")
     st = I.initial_state(s)
-    osys = O.OracleSystem(s)
+    osys = O.OracleSystem(s, precision=O.P64)   # the plain FP64 method
     ost = O.OracleState(osys, st)
     n = s.n_solvent + s.n_sites
     O.step(osys, ost, a.warmup)
@@ -278,7 +324,7 @@ def run_reference(a, ws, rank):
     O.step(osys, ost, a.steps)
     dt = time.perf_counter() - t0
     v = n * a.steps / dt
-    sample = (f"FP64 oracle, one host core, each step one step of an L={L} box with the "
+    sample = (f"plain FP64 oracle, one host core, each step one step of an L={L} box with the "
               f"workload's density, phi, radius and 642-site shells ({n} particle-updates)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
@@ -352,11 +398,23 @@ def main():
     sim.set_state(state)
     tuning = sim.tuning() if a.no_tune else sim.autotune(steps_per_trial=10)
     sim.step(a.warmup)
+    # mpcd_step(n) replays a CUDA graph keyed by (n, solvent buffer parity,
+    # steps since the last re-sort); a call of n steps counts n - 1 of them
+    # towards the next re-sort (the last step's pass is not a fused one), so
+    # after a re-sort the keys of repeated n-step calls cycle with a period of
+    # at most twice the sort period: recording every graph of the cycle before
+    # the timed call makes that call a replay
+    sim.sort()
+    period = max(1, int(tuning["sort_period"]))
+    since, par, seen = 0, 0, set()
+    while a.steps >= 2 and (since, par) not in seen:
+        seen.add((since, par))
+        sim.step(a.steps)
+        par ^= ((since + a.steps - 1) // period) & 1
+        since = (since + a.steps - 1) % period
     torch.cuda.synchronize()
-    sim.set_profiling(True)
-    sim.reset_profile()
 
-    # ---------------------------------------------------------------- timed
+    # ------------------------------------------------------- timed (graph)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -376,6 +434,19 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     value = n_upd * a.steps * ws / (ms_max / 1e3)
+
+    # ------------------------------------ profiled pass (per-kernel events)
+    # the same number of steps launched kernel by kernel with CUDA events on
+    # each kernel's stream (no graph); it gives the per-kernel times and the
+    # roofline of the dominant kernel, and its own step time
+    sim.set_profiling(True)
+    sim.reset_profile()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    sim.step(a.steps)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = p0.elapsed_time(p1)
     prof = sim.profile()
     sim.set_profiling(False)
 
@@ -393,14 +464,17 @@ def main():
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs copy)",
             "bytes_per_launch": pk["bytes_per_launch"], "ms_per_launch": per_launch_ms,
-            "share_of_step": pk["total_ms"] / ms}
+            "share_of_step": pk["total_ms"] / ms_prof,
+            "measured_in": "profiled pass (kernel-by-kernel launches with CUDA events, same step count)"}
     launches = a.steps + sum(v["launches"] * (5 if k == "sort" else 1) for k, v in prof.items())
     # whole-step effective bandwidth: algorithmic bytes of every kernel / step time
     step_bytes = sum(v["bytes_per_launch"] * v["launches"] for v in prof.values()) / a.steps
     hbm_eff = {"bytes_per_update": step_bytes / n_upd, "gbs": step_bytes / (ms / a.steps / 1e3) / 1e9}
     hbm_eff["frac"] = hbm_eff["gbs"] / hbm
     kernels = {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / max(v["launches"], 1),
-                   "share": v["total_ms"] / ms} for k, v in prof.items()}
+                   "share": v["total_ms"] / ms_prof} for k, v in prof.items()}
+    profiled = {"ms_per_step": ms_prof / a.steps, "steps": a.steps,
+                "note": "kernel-by-kernel launches with CUDA events (no graph); the headline is the graph replay"}
 
     # ------------------------------------------------ end to end (host buffers)
     hb = sim.host_buffers(pinned=True)
@@ -464,9 +538,9 @@ def main():
     if protocols_on:
         protocols = {"rnemd": rnemd_protocol(Bd, I, stream, peaks()[0]), **bodyp}
 
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and not a.no_cpu and default_workload:   # the oracle sample is of the benchmark composition
-        cpu = cpu_baseline()
+        cpu, parity = cpu_baseline(Bd)
         cpu.pop("seconds", None)
 
     state_bytes_dev = system.n_solvent * 28 + system.n_cells * 56
@@ -495,11 +569,11 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
-            "roofline": roof, "hbm_effective": hbm_eff, "kernels": kernels,
+            "roofline": roof, "hbm_effective": hbm_eff, "kernels": kernels, "profiled_pass": profiled,
             "kernels_note": ("sites_post, body_impulse, body_md, body_force and the next step's sites_pre run "
                              "on a second stream beside solvent_fused; their event spans include shared time"),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "p64": p64, "protocols": protocols,
+            "p64": p64, "protocols": protocols, "parity_vs_fp64": parity,
             "diag_check": {"ke_solvent_per_particle": diag["ke_solvent"] / system.n_solvent},
         }
         print(json.dumps(out))

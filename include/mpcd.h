@@ -197,6 +197,26 @@ int mpcd_step(mpcd_ctx *ctx, int64_t nsteps, void *stream);
  * change any result. */
 int mpcd_sort(mpcd_ctx *ctx, int32_t canonical, void *stream);
 
+/* Binning as a counting sort (Sec. II.A; the cell assignment under the random
+ * grid shift): the canonical member order of the collision at the current
+ * step.  Call it between mpcd_couple(PRE) and mpcd_collide (for a context
+ * without colloids, any time after mpcd_stream): every solvent particle at its
+ * current position under the grid shift of that collision, and every site in
+ * the cell its PRE coupling assigned, is counted into its cell (histogram), the
+ * counts are scanned into each cell's first slot, the members are scattered and
+ * each cell's members are ordered solvent before sites, each by ascending id.
+ *   order       host int64[n_solvent + n_sites]: the members cell by cell; a
+ *               solvent particle is given as its row in the host state arrays
+ *               (replica offset + tag), a site as n_solvent + its index in the
+ *               body-major site order
+ *   cell_start  host int64[n_cells + 1]: cell c holds order[cell_start[c] ..
+ *               cell_start[c + 1]), cells numbered replica by replica
+ * The result is unique (integer work), so it is reproducible bit for bit.  The
+ * time step itself never needs it: its cell sums are order-independent integer
+ * sums.  Scratch is allocated on the first call.  Changes no state;
+ * synchronises the stream. */
+int mpcd_cell_order(mpcd_ctx *ctx, int64_t *order, int64_t *cell_start, void *stream);
+
 /* FP64 diagnostics of the current state.  Synchronises the stream. */
 int mpcd_diagnostics(mpcd_ctx *ctx, mpcd_diag *out, void *stream);
 
@@ -367,7 +387,8 @@ int mpcd_autotune(mpcd_ctx *ctx, int32_t steps_per_trial, void *stream);
  * Arguments (device pointers, caller-owned, on the current CUDA device):
  *   params     host struct; precision must be MPCD_P32 and angular 0
  *              (sort_period and naive_transfer are ignored)
- *   L          host int32[3], cells per edge, each >= 3
+ *   L          host int32[3], cells per edge, each 3 to 2047 (the binning
+ *              rule forms floor(x 2^20) in 32 bits)
  *   n_solvent  particles, 0 <= n <= MPCD_STATIC_MAX_SOLVENT, a multiple of 4
  *   x, y, z    float[n] positions in [0, L) (not checked)
  *   vx, vy, vz float[n] velocities, updated in place
@@ -377,7 +398,9 @@ int mpcd_autotune(mpcd_ctx *ctx, int32_t steps_per_trial, void *stream);
  *   stream     cudaStream_t as void*; the work is enqueued asynchronously
  *   msg        optional host buffer of msg_len bytes for an error message
  * Every device array must be 16-byte aligned.  The P32 per-cell limits of
- * mpcd_debug_cells apply (at most 4095 particles and |sum m v| < 2048 per cell).
+ * mpcd_debug_cells apply (at most 4095 particles and |sum m v| < 2048 per cell);
+ * this call does not check them: a cell beyond them gets wrong velocities and
+ * no error is reported.
  *
  * Scratch: the cell sums and collision parameters live in one statically
  * reserved device array of the library (about 4.1 MB per device, reserved by

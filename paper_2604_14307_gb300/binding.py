@@ -33,7 +33,7 @@ EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "m
            "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
            "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static", "mpcd_set_rnemd",
            "mpcd_rnemd_totals", "mpcd_velocity_profile", "mpcd_set_body_force",
-           "mpcd_body_displacements", "mpcd_set_vacf", "mpcd_get_vacf"]
+           "mpcd_body_displacements", "mpcd_set_vacf", "mpcd_get_vacf", "mpcd_cell_order"]
 
 
 class MPCDError(RuntimeError):
@@ -142,6 +142,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "mpcd_get_vacf": [vp, vp, vp, vp, vp],
             "mpcd_rnemd_totals": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), vp],
             "mpcd_velocity_profile": [vp, i32, i32, i32, vp, vp, vp],
+            "mpcd_cell_order": [vp, vp, vp, vp],
             "mpcd_collide_solvent_static": [C.POINTER(Params), C.POINTER(C.c_int32 * 3), i64, vp, vp, vp,
                                             vp, vp, vp, vp, i64, vp, C.c_char_p, C.c_size_t],
         }
@@ -326,6 +327,15 @@ class Simulation:
 
     def sort(self, canonical: bool = False, stream=None):
         self._check(self.lib.mpcd_sort(self.ctx, int(canonical), self._s(stream)))
+
+    def cell_order(self, stream=None):
+        """Canonical member order of the collision at the current step (call it
+        after couple(PRE)): (order int64[N_s + N_sites], cell_start int64[C + 1])."""
+        n = self.sizes.n_solvent + self.sizes.n_sites
+        order = np.zeros(max(n, 1), dtype=np.int64)
+        start = np.zeros(self.sizes.n_cells + 1, dtype=np.int64)
+        self._check(self.lib.mpcd_cell_order(self.ctx, order.ctypes.data, start.ctypes.data, self._s(stream)))
+        return order[:n], start
 
     def diagnostics(self, stream=None) -> dict:
         d = Diag()

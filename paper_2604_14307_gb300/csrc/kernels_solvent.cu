@@ -2156,4 +2156,119 @@ void launch_velocity_profile(const StepArgs &a, int bin_axis, int vel_axis, int 
     else k_velocity_profile<double><<<grid, 512, 0, s>>>(a, bin_axis, vel_axis, n_bins, mass, mom);
 }
 
+
+// ------------------------------------- canonical member order (Sec. II.A)
+// The binning step as a counting sort: every solvent particle (at its current
+// position, under the grid shift of the collision keyed by *d_step) and every
+// site (its cell from the PRE coupling) is counted into its cell; an
+// exclusive scan of the counts gives each cell's first slot; a scatter
+// places the members; each cell's segment is then put in the canonical order
+// (solvent before sites, each by ascending id), so that the result does not
+// depend on the order of the atomics.  Keys: a solvent particle is its host
+// row (row_begin + tag), a site is ORDER_SITE + its global index.
+constexpr unsigned long long ORDER_SITE = 1ull << 62;
+
+template <typename Real>
+__device__ __forceinline__ int64_t order_solvent_cell(const DevReplica &r, const int32_t (&S)[3], Real x, Real y,
+                                                      Real z)
+{
+    return (int64_t)r.cell_base + cell_axis(x, S[0], r.L[0]) +
+           (int64_t)r.L[0] * (cell_axis(y, S[1], r.L[1]) + r.L[1] * cell_axis(z, S[2], r.L[2]));
+}
+
+// SCATTER = false: counts[c] += 1 per member; true: keys[ex[c] + slot] = key
+template <typename Real, bool SCATTER>
+__global__ void __launch_bounds__(256) k_order_solvent(StepArgs a, int32_t *counts, const int32_t *ex,
+                                                       int32_t *cursor, unsigned long long *keys)
+{
+    const Real *X = (const Real *)a.x, *Y = (const Real *)a.y, *Z = (const Real *)a.z;
+    const int64_t step = *a.d_step;
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const Tile tl = a.tiles[t];
+        const DevReplica r = a.reps[tl.rep];
+        int32_t S[3];
+        grid_shift(r, step, S);
+        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
+            const int64_t c = order_solvent_cell(r, S, X[i], Y[i], Z[i]);
+            if (!SCATTER) {
+                atomicAdd(counts + c, 1);
+            } else {
+                const int64_t pos = (int64_t)ex[c] + atomicAdd(cursor + c, 1);
+                keys[pos] = (unsigned long long)(r.row_begin + a.tag[i]);
+            }
+        }
+    }
+}
+
+// sites: one CTA per body
+template <bool SCATTER>
+__global__ void __launch_bounds__(128) k_order_sites(StepArgs a, int32_t *counts, const int32_t *ex,
+                                                     int32_t *cursor, unsigned long long *keys)
+{
+    const DevBody &B = a.bodies[blockIdx.x];
+    const DevReplica r = a.reps[B.rep];
+    const int n = a.shapes[B.shape].n_sites;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t g = B.site_begin + j;
+        const int64_t c = (int64_t)r.cell_base + a.site_cell[g];
+        if (!SCATTER) {
+            atomicAdd(counts + c, 1);
+        } else {
+            const int64_t pos = (int64_t)ex[c] + atomicAdd(cursor + c, 1);
+            keys[pos] = ORDER_SITE | (unsigned long long)g;
+        }
+    }
+}
+
+// per cell: insertion sort of its segment by key (segments hold ~10-40),
+// then the final ids (solvent: host row; site: n_solvent + site index) and
+// the int64 cell starts
+__global__ void __launch_bounds__(256) k_order_cells(int64_t n_cells, const int32_t *ex,
+                                                     unsigned long long *keys, int64_t n_solvent,
+                                                     int64_t *order, int64_t *start)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = ex[c], e = ex[c + 1];
+        for (int64_t i = b + 1; i < e; ++i) {
+            const unsigned long long k = keys[i];
+            int64_t j = i - 1;
+            while (j >= b && keys[j] > k) {
+                keys[j + 1] = keys[j];
+                --j;
+            }
+            keys[j + 1] = k;
+        }
+        for (int64_t i = b; i < e; ++i) {
+            const unsigned long long k = keys[i];
+            order[i] = (k & ORDER_SITE) ? n_solvent + (int64_t)(k & ~ORDER_SITE) : (int64_t)k;
+        }
+        start[c] = b;
+        if (c == n_cells - 1) start[n_cells] = e;
+    }
+}
+
+void launch_cell_order(const StepArgs &a, int64_t n_solvent, int32_t *counts, int32_t *ex, int32_t *cursor,
+                       int32_t *scan_bs, unsigned long long *keys, int64_t *order, int64_t *start, int num_sms,
+                       cudaStream_t s)
+{
+    const int64_t C = a.n_cells;
+    cudaMemsetAsync(counts, 0, (C + 1) * sizeof(int32_t), s);
+    cudaMemsetAsync(cursor, 0, C * sizeof(int32_t), s);
+    const int grid = std::max(1, std::min(a.n_tiles, num_sms * 8));
+    if (a.n_tiles > 0) {
+        if (a.precision == 1) k_order_solvent<float, false><<<grid, 256, 0, s>>>(a, counts, ex, cursor, keys);
+        else k_order_solvent<double, false><<<grid, 256, 0, s>>>(a, counts, ex, cursor, keys);
+    }
+    if (a.n_bodies > 0) k_order_sites<false><<<a.n_bodies, 128, 0, s>>>(a, counts, ex, cursor, keys);
+    launch_scan(counts, ex, C + 1, scan_bs, s);   // counts[C] = 0: ex[C] = number of members
+    if (a.n_tiles > 0) {
+        if (a.precision == 1) k_order_solvent<float, true><<<grid, 256, 0, s>>>(a, counts, ex, cursor, keys);
+        else k_order_solvent<double, true><<<grid, 256, 0, s>>>(a, counts, ex, cursor, keys);
+    }
+    if (a.n_bodies > 0) k_order_sites<true><<<a.n_bodies, 128, 0, s>>>(a, counts, ex, cursor, keys);
+    const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((C + 255) / 256, (int64_t)num_sms * 16));
+    k_order_cells<<<cgrid, 256, 0, s>>>(C, ex, keys, n_solvent, order, start);
+}
+
 }  // namespace mpcd

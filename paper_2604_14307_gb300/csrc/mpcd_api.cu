@@ -120,6 +120,10 @@ struct mpcd_ctx {
     int4 *ang_shift = nullptr;                  // [nrep] grid shift of the current collision
     double f_ext[3] = {0.0, 0.0, 0.0};          // constant force on every body (one replica)
     VacfArgs vacf{};                            // velocity autocorrelations (n_lags 0: off)
+    // canonical member order (mpcd_cell_order; allocated on first use)
+    int32_t *ord_counts = nullptr, *ord_ex = nullptr, *ord_cursor = nullptr, *ord_bs = nullptr;
+    unsigned long long *ord_keys = nullptr;
+    int64_t *ord_out = nullptr, *ord_start = nullptr;
     bool have_state = false;                    // mpcd_set_state has run
 };
 
@@ -1216,6 +1220,38 @@ int mpcd_sort(mpcd_ctx *c, int32_t canonical, void *stream)
     int e = do_sort(c, canonical, (cudaStream_t)stream);
     if (!e) CK(c, cudaGetLastError());
     return e;
+}
+
+int mpcd_cell_order(mpcd_ctx *c, int64_t *order, int64_t *cell_start, void *stream)
+{
+    CHECK_CTX(c);
+    if (!order || !cell_start) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = c->Ns + c->Nsite, C = c->C;
+    if (!c->ord_counts) {
+        c->ord_counts = (int32_t *)dalloc(c, (C + 1) * sizeof(int32_t));
+        c->ord_ex = (int32_t *)dalloc(c, (C + 1) * sizeof(int32_t));
+        c->ord_cursor = (int32_t *)dalloc(c, C * sizeof(int32_t));
+        c->ord_bs = (int32_t *)dalloc(c, scan_block_sums_size(C + 1) * sizeof(int32_t));
+        c->ord_keys = (unsigned long long *)dalloc(c, std::max<int64_t>(N, 1) * 8);
+        c->ord_out = (int64_t *)dalloc(c, std::max<int64_t>(N, 1) * 8);
+        c->ord_start = (int64_t *)dalloc(c, (C + 1) * 8);
+        if (!c->ord_counts || !c->ord_ex || !c->ord_cursor || !c->ord_bs || !c->ord_keys || !c->ord_out ||
+            !c->ord_start)
+            return fail(c, MPCD_ERR_OOM, "cell-order buffers: allocation failed");
+    }
+    StepArgs a = make_io_args(c);
+    int e = timed(c, "cell_order", (double)N * (3.0 * c->realsz + 4.0 + 4 * 8.0) + (double)C * 16.0, s, [&] {
+        launch_cell_order(a, c->Ns, c->ord_counts, c->ord_ex, c->ord_cursor, c->ord_bs, c->ord_keys, c->ord_out,
+                          c->ord_start, c->num_sms, s);
+    });
+    if (e) return e;
+    CK(c, cudaGetLastError());
+    if (N) CK(c, cudaMemcpyAsync(order, c->ord_out, N * 8, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(cell_start, c->ord_start, (C + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    return MPCD_OK;
 }
 
 int mpcd_diagnostics(mpcd_ctx *c, mpcd_diag *o, void *stream)

@@ -351,6 +351,12 @@ void launch_sort_scatter(const StepArgs &a, const int32_t *offsets, int32_t *cur
 void launch_sort_canonical(const StepArgs &a, void *const arr[6], uint32_t *tag,
                            const int32_t *offsets, cudaStream_t s);
 size_t scan_block_sums_size(int64_t n);
+// canonical member order of the collision at *d_step (counting sort by cell:
+// histogram, scan, scatter, per-cell order solvent before sites, ascending id);
+// counts and ex hold n_cells + 1 entries, keys and order n_solvent + n_sites
+void launch_cell_order(const StepArgs &a, int64_t n_solvent, int32_t *counts, int32_t *ex, int32_t *cursor,
+                       int32_t *scan_bs, unsigned long long *keys, int64_t *order, int64_t *start, int num_sms,
+                       cudaStream_t s);
 
 // host-state ingest / egress by stable radix sort (kernels_sort.cu)
 size_t radix_hist_ints(int64_t n);          // ints of the per-pass digit histogram

@@ -99,7 +99,9 @@ extern "C" int mpcd_collide_solvent_static(const mpcd_params *p, const int32_t L
     if (!(p->kT > 0.0) || !(p->m_solvent > 0.0) || !(p->alpha_deg == p->alpha_deg) ||
         (p->thermostat != 0 && p->thermostat != 1) || p->angular != 0)
         return reject(msg, msg_len, "invalid params (kT > 0, m_solvent > 0, thermostat 0/1, angular 0)");
-    if (L[0] < 3 || L[1] < 3 || L[2] < 3) return reject(msg, msg_len, "every box edge L must be >= 3 cells");
+    // the binning rule forms floor(x 2^20) in 32 bits, so an edge must stay below 2048 cells
+    if (L[0] < 3 || L[1] < 3 || L[2] < 3 || L[0] > 2047 || L[1] > 2047 || L[2] > 2047)
+        return reject(msg, msg_len, "every box edge L must be 3 to 2047 cells");
     const int64_t cells = (int64_t)L[0] * L[1] * L[2];
     if (cells > MAX_CELLS) {
         snprintf(buf, sizeof buf, "box of %lld cells exceeds the static scratch limit of %lld cells",

@@ -32,6 +32,7 @@ from paper_2604_14307_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = {I.P64: 1e-12, I.P32: 1e-5}
+ORDINARY = {I.P64: 1e-13, I.P32: 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -87,6 +88,14 @@ def test_one_collision_matches_oracle(B, rule, thermostat, prec, L):
     bound = TOL[prec] * (np.abs(ost.v) + 1.0 + w[:, None])
     err = np.abs(g.v - ost.v)
     assert np.all(err <= bound), (err / bound).max()
+    # ordinary cells (|w_c| < 10, all but the nearly collinear ones): the error
+    # model's own bound (a numpy restatement of the kernel arithmetic stays
+    # below 3.8e-7 (P32) and 3.5e-14 (P64) of |v| + 1 + |w_c|), with room for
+    # the device's float32 transcendentals
+    ordinary = w < 10.0
+    rel = (err / (np.abs(ost.v) + 1.0 + w[:, None]))[ordinary]
+    print("ordinary cells: max error", rel.max(), "of", int(ordinary.sum()), "particles")
+    assert rel.max() <= ORDINARY[prec], rel.max()
     # the correction is really applied: the plain rule's velocities differ by far more
     o0 = O.OracleSystem(system, angular=0)
     s0 = O.OracleState(o0, st)

@@ -7,8 +7,8 @@
   are keyed by its stream id, not by its position;
 * equipartition on the GPU (Sec. III.A): over a large ensemble of single
   spheres the mean translational and rotational kinetic energies per body are
-  (3/2) kT (1 - M/M_total) and (3/2) kT within 4 standard errors (block
-  averages), with no other slack.
+  (3/2) kT (1 - M/M_total) and (3/2) kT within 3 standard errors (50 block
+  averages of a long run), with no other slack.
 """
 import math
 
@@ -81,7 +81,7 @@ def block_mean_err(x, nblocks=20):
 
 
 def test_equipartition_of_the_rigid_sphere_ensemble(B, golden):
-    n_rep, L, burn, steps, every = 512, 12, 300, 4000, 5
+    n_rep, L, burn, steps, every = 512, 12, 300, 10000, 5
     system = I.batched_single_sphere(n_rep=n_rep, precision=I.P32, seed=11, Ls=(L,))
     sim = B.Simulation(system)
     sim.set_state(I.initial_state(system))
@@ -97,8 +97,9 @@ def test_equipartition_of_the_rigid_sphere_ensemble(B, golden):
     Mtot = M + 5.0 * L**3
     expect_T = golden["mean_E_T"]["expected"] * (1 - M / Mtot)
     expect_R = golden["mean_E_R"]["expected"]
-    mT, eT = block_mean_err(ET)
-    mR, eR = block_mean_err(ER)
-    assert abs(mT - expect_T) < 4 * eT, (mT, eT, expect_T)
-    assert abs(mR - expect_R) < 4 * eR, (mR, eR, expect_R)
+    mT, eT = block_mean_err(ET, nblocks=50)
+    mR, eR = block_mean_err(ER, nblocks=50)
+    print("E_T", mT, "+-", eT, "expected", expect_T, "; E_R", mR, "+-", eR, "expected", expect_R)
+    assert abs(mT - expect_T) < 3 * eT, (mT, eT, expect_T)
+    assert abs(mR - expect_R) < 3 * eR, (mR, eR, expect_R)
     assert eT < 0.01 and eR < 0.01        # the ensemble is large enough to mean something
