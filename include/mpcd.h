@@ -228,14 +228,18 @@ const char *mpcd_last_error(const mpcd_ctx *ctx);
 /* Capture buffers for tests.  After mpcd_set_debug(ctx, 1) every collision
  * keeps a copy of its cell sums before they are consumed.
  * sums:      [sum_words][n_cells].  P32: int64 words, exact sums over the cell
- *              w0 = (p_x, p_y), w1 = (p_z, count), p = round(fl32(m v) 2^20),
- *              SRD: w2 = round(fl32(m v.v) 2^28); AT: w2 = (q_x, q_y),
- *              w3 = (q_z, 0), q = round(fl32(m xi) 2^20); (hi, lo) is the pair of
- *              signed 32-bit halves hi 2^32 + lo; count is 1 per solvent particle
- *              and 2^12 per site.  P64: doubles N, M, m v (3), then m v.v (SRD)
- *              or m xi (3) (AT).  The P32 form needs one site mass per context,
- *              at most 4095 solvent particles and 1023 sites per cell and
- *              |sum m v_a| < 2048 per cell.
+ *              of per-particle integers: w0 = p_x + 2^48 [solvent],
+ *              w1 = p_y + 2^48 [site], w2 = p_z with p = round(fl32(m v) 2^32)
+ *              (the low 48 bits of w0 and w1 are the signed momentum sums, the
+ *              high 16 bits the cell's solvent and site counts); SRD:
+ *              w3 = round(e 2^28), e = fl32(fl32(px vx) + fl32(py vy)) + fl32(pz vz)
+ *              in float32; AT: w3, w4, w5 = round(fl32(m xi) 2^32).  The 2^-32
+ *              quantum is below the float32 spacing of every |m v| >= 2^-9, so
+ *              the momentum words are the exact sums of the stored float32
+ *              momenta.  P64: doubles N, M, m v (3), then m v.v (SRD) or m xi
+ *              (3) (AT).  The P32 form needs one site mass per context, at most
+ *              65535 solvent particles and 65535 sites per cell and
+ *              |sum m v_a| < 2^15 per cell (not checked).
  * params:    [n_cells][param_bytes] collision parameters (u, kappa, axis / xibar).
  * site_cell: [n_sites] replica-local cell of every site.
  * site_v:    [n_sites][3] site velocities entering the collision (float/double).
@@ -398,12 +402,12 @@ int mpcd_autotune(mpcd_ctx *ctx, int32_t steps_per_trial, void *stream);
  *   stream     cudaStream_t as void*; the work is enqueued asynchronously
  *   msg        optional host buffer of msg_len bytes for an error message
  * Every device array must be 16-byte aligned.  The P32 per-cell limits of
- * mpcd_debug_cells apply (at most 4095 particles and |sum m v| < 2048 per cell);
- * this call does not check them: a cell beyond them gets wrong velocities and
- * no error is reported.
+ * mpcd_debug_cells apply (at most 65535 particles and |sum m v_a| < 2^15 per
+ * cell); this call does not check them: a cell beyond them gets wrong
+ * velocities and no error is reported.
  *
  * Scratch: the cell sums and collision parameters live in one statically
- * reserved device array of the library (about 4.1 MB per device, reserved by
+ * reserved device array of the library (about 5.2 MB per device, reserved by
  * the CUDA runtime when it loads that part of the library on the device, at
  * the latest on the first call), sized for MPCD_STATIC_MAX_CELLS cells.  A box with more cells, more particles than
  * MPCD_STATIC_MAX_SOLVENT, a misaligned pointer or an n that is not a multiple

@@ -202,7 +202,7 @@ def collide(osys: OracleSystem, st: OracleState, trace: bool = True) -> dict:
     tr = _Trace()
     if trace:
         Ns, Nsite, Ct, B, R = osys.n_solvent, osys.n_sites, osys.n_cells, osys.n_bodies, len(osys.L)
-        nw = 4
+        nw = 6
         shapes = dict(shift=((R, 3), np.int32), cell_solvent=((Ns,), np.int32),
                       cell_site=((Nsite,), np.int32), site_r=((Nsite, 3), np.float64),
                       site_v=((Nsite, 3), np.float64), site_vpost=((Nsite, 3), np.float64),

@@ -101,7 +101,7 @@ typedef struct {
     double *site_r;        /* [Nsites][3] stored site positions */
     double *site_v;        /* [Nsites][3] velocities entering the collision */
     double *site_vpost;    /* [Nsites][3] velocities after the collision */
-    int64_t *fixed;        /* [4][Ctot] fixed-point cell words (P32 form; SRD uses 3) */
+    int64_t *fixed;        /* [6][Ctot] fixed-point cell words (P32 form; SRD uses 4) */
     double *sums;          /* [6][Ctot]: N, M, sum m v (3), sum m v.v */
     double *cell_u;        /* [Ctot][3] */
     double *cell_axis;     /* [Ctot][3] */
@@ -353,32 +353,38 @@ void orc_grid_shift(const orc_sys *s, int rep, int64_t step, int32_t S[3])
 /* ------------------------------------------------------------------ */
 /* fixed-point cell record of the P32 form                              */
 /* ------------------------------------------------------------------ */
-/* Int64 words per cell, each an exact sum of per-particle integers; a pair
- * word holds two signed 32-bit halves, hi * 2^32 + lo:
- *   w0 = (p_x, p_y),  w1 = (p_z, count)        p = round(fl32(m v) 2^20)
- *   SRD: w2 = round(e 2^28), e = fl32(fl32(fl32(px vx) + fl32(py vy)) + fl32(pz vz))
- *   AT:  w2 = (q_x, q_y), w3 = (q_z, 0)        q = round(fl32(m xi) 2^20)
- * count = 1 for a solvent particle, 2^12 for a site (solvent in bits 0-11,
- * sites in bits 12-21).  Rounding is to nearest, ties to even, of the float
- * value times the power of two (an exact scaling). */
-static int64_t qs(float x, float pow2) { return (int64_t)llrintf(x * pow2); }
-static int64_t pack2(int64_t hi, int64_t lo) { return (int64_t)((uint64_t)hi << 32) + lo; }
+/* Int64 words per cell, each an exact sum of per-particle integers:
+ *   w0 = p_x + 2^48 [solvent],  w1 = p_y + 2^48 [site],  w2 = p_z
+ *                                                 p = round(fl32(m v) 2^32)
+ *   SRD: w3 = round(e 2^28), e = fl32(fl32(fl32(px vx) + fl32(py vy)) + fl32(pz vz))
+ *   AT:  w3, w4, w5 = q                           q = round(fl32(m xi) 2^32)
+ * The low 48 bits of w0 and w1 are the signed momentum sums, the high 16 bits
+ * the counts of solvent particles and of sites.  The momentum quantum 2^-32 is
+ * below the float32 spacing of every |m v| >= 2^-9, so the momentum words are
+ * the exact sums of the stored float32 momenta (the cell momentum that the
+ * collision conserves, Sec. II.A).  Rounding is to nearest, ties to even, of
+ * the float value times the power of two (an exact scaling, done in double). */
+#define W_COUNT ((int64_t)1 << 48)
+static int64_t qs(float x, double pow2) { return (int64_t)llrint((double)x * pow2); }
 
-static void record_terms(float m, const float v[3], int is_site, int rule, int64_t w[4])
+static void record_terms(float m, const float v[3], int is_site, int rule, int64_t w[6])
 {
     float px = m * v[0], py = m * v[1], pz = m * v[2];
     float e = (px * v[0] + py * v[1]) + pz * v[2];   /* unfused: -ffp-contract=off */
-    int64_t cnt = is_site ? ((int64_t)1 << 12) : 1;
-    w[0] = pack2(qs(px, 1048576.0f), qs(py, 1048576.0f));                      /* 2^20 */
-    w[1] = pack2(qs(pz, 1048576.0f), cnt);
-    w[2] = rule == ORC_SRD ? qs(e, 268435456.0f) : 0;                            /* 2^28 */
-    w[3] = 0;
+    w[0] = qs(px, 0x1p32) + (is_site ? 0 : W_COUNT);
+    w[1] = qs(py, 0x1p32) + (is_site ? W_COUNT : 0);
+    w[2] = qs(pz, 0x1p32);
+    w[3] = rule == ORC_SRD ? qs(e, 0x1p28) : 0;
+    w[4] = w[5] = 0;
 }
 
-static void unpack2(int64_t w, int64_t *hi, int64_t *lo)
+/* a count|momentum word: signed low 48 bits and the 16-bit count above them */
+static void unpack48(int64_t w, int64_t *count, int64_t *lo)
 {
-    *lo = (int64_t)(int32_t)(uint32_t)(w & 0xFFFFFFFF);
-    *hi = (w - *lo) / ((int64_t)1 << 32);
+    int64_t l = w & (W_COUNT - 1);
+    if (l >= W_COUNT / 2) l -= W_COUNT;
+    *lo = l;
+    *count = (int64_t)((uint64_t)(w - l) >> 48);
 }
 
 /* ------------------------------------------------------------------ */
@@ -804,7 +810,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
             uint32_t lc = (uint32_t)(c - cbase[r]);
             int64_t n = start[c + 1] - start[c];
             double M = 0, pm[3] = { 0, 0, 0 }, e2 = 0;
-            int64_t fx[4] = { 0, 0, 0, 0 };
+            int64_t fx[6] = { 0, 0, 0, 0, 0, 0 };
             for (int64_t k = start[c]; k < start[c + 1]; ++k) {
                 int64_t id = order[k];
                 double m = id < Ns ? s->m_solvent : 0.0;
@@ -819,9 +825,9 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                 for (int a = 0; a < 3; ++a) { pm[a] += m * v[a]; e2 += m * v[a] * v[a]; }
                 if (p32) {
                     float vf[3] = { f32(v[0]), f32(v[1]), f32(v[2]) };
-                    int64_t w[4];
+                    int64_t w[6];
                     record_terms(f32(m), vf, id >= Ns, s->rule, w);
-                    for (int q = 0; q < 4; ++q) fx[q] += w[q];
+                    for (int q = 0; q < 6; ++q) fx[q] += w[q];
                 }
             }
             double u[3] = { 0, 0, 0 };
@@ -832,14 +838,16 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                 orc_srd_axis(s, r, st->step, lc, axis);
                 if (s->thermostat && p32) {
                     /* P32 form: the kinetic energy entering the thermostat is the
-                     * one its fixed-point sums carry, i.e. of the stored float
-                     * velocities with float32 products m v.v (the same numbers as
-                     * the words above), evaluated here in FP64 */
-                    int64_t h[3], l[3];
-                    unpack2(fx[0], &h[0], &l[0]);
-                    unpack2(fx[1], &h[1], &l[1]);
-                    double S1[3] = { (double)h[0] * 0x1p-20, (double)l[0] * 0x1p-20, (double)h[1] * 0x1p-20 };
-                    double S2 = (double)fx[2] * 0x1p-28, pp = 0.0;
+                     * one its fixed-point sums carry: the exact momentum sums of
+                     * the stored float32 momenta and the sum of the float32
+                     * products m v.v (the same numbers as the words above),
+                     * evaluated here in FP64 */
+                    int64_t cnt, S1i[3];
+                    unpack48(fx[0], &cnt, &S1i[0]);
+                    unpack48(fx[1], &cnt, &S1i[1]);
+                    S1i[2] = fx[2];
+                    double S1[3] = { (double)S1i[0] * 0x1p-32, (double)S1i[1] * 0x1p-32, (double)S1i[2] * 0x1p-32 };
+                    double S2 = (double)fx[3] * 0x1p-28, pp = 0.0;
                     for (int a = 0; a < 3; ++a) pp += S1[a] * S1[a];
                     double Erel = 0.5 * (S2 - pp / M);
                     double Ep = thermostat_energy(s, r, st->step, lc, n);
@@ -886,14 +894,13 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                     if (p32) {
                         float q[3];
                         for (int a = 0; a < 3; ++a) q[a] = f32(m) * f32(sc * nn[a]);
-                        fx[2] += pack2(qs(q[0], 1048576.0f), qs(q[1], 1048576.0f));
-                        fx[3] += pack2(qs(q[2], 1048576.0f), 0);
+                        for (int a = 0; a < 3; ++a) fx[3 + a] += qs(q[a], 0x1p32);
                     }
                 }
                 for (int a = 0; a < 3; ++a) xib[a] = mx[a] / M;
             }
             if (p32 && tr && tr->fixed)
-                for (int q = 0; q < 4; ++q) tr->fixed[q * Ctot + c] = fx[q];
+                for (int q = 0; q < 6; ++q) tr->fixed[q * Ctot + c] = fx[q];
             if (tr && tr->sums) {
                 tr->sums[0 * Ctot + c] = (double)n; tr->sums[1 * Ctot + c] = M;
                 for (int a = 0; a < 3; ++a) tr->sums[(2 + a) * Ctot + c] = pm[a];

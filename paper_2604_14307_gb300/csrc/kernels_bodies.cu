@@ -674,14 +674,16 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
         }
         if (valid) {
             if constexpr (sizeof(Real) == 4) {
-                long long w[4];
+                long long w[MAX_WORDS32];
                 unsigned long long *S = reinterpret_cast<unsigned long long *>(a.sums);
                 if (a.rule == 0) {
                     record_terms<0>(m, v[0], v[1], v[2], xi, true, w);
-                    for (int k = 0; k < 3; ++k) atomicAdd(S + k * a.n_cells + cell, (unsigned long long)w[k]);
+                    for (int k = 0; k < Words32<0>::n; ++k)
+                        atomicAdd(S + k * a.n_cells + cell, (unsigned long long)w[k]);
                 } else {
                     record_terms<1>(m, v[0], v[1], v[2], xi, true, w);
-                    for (int k = 0; k < 4; ++k) atomicAdd(S + k * a.n_cells + cell, (unsigned long long)w[k]);
+                    for (int k = 0; k < Words32<1>::n; ++k)
+                        atomicAdd(S + k * a.n_cells + cell, (unsigned long long)w[k]);
                 }
             } else {
                 add_sums64(a, cell, m, v, xi);

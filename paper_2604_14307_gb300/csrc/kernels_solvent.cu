@@ -222,22 +222,6 @@ __device__ __forceinline__ void terms64(double m, double vx, double vy, double v
     }
 }
 
-// backward run totals over a thread's 4 consecutive particles: T[j] is the sum
-// of the run that starts at j (static indices only)
-__device__ __forceinline__ unsigned run_totals(const int (&c)[4], int nv, long long (&w)[4][4])
-{
-#pragma unroll
-    for (int j = 2; j >= 0; --j)
-        if (j + 1 < nv && c[j + 1] == c[j])
-#pragma unroll
-            for (int k = 0; k < 4; ++k) w[j][k] += w[j + 1][k];
-    unsigned heads = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (j < nv && (j == 0 || c[j] != c[j - 1])) heads |= 1u << j;
-    return heads;
-}
-
 __device__ __forceinline__ void red_add(long long *p, long long v)
 {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
@@ -266,16 +250,27 @@ __device__ __forceinline__ void bin4(const StepArgs &a, const Real (&x)[4], cons
         }
     }
     if constexpr (sizeof(Real) == 4) {
+        // forward run merging: one running total, flushed when the cell changes
         constexpr int NW = Words32<RULE>::n;
-        long long w[4][4];
+        long long acc[MAX_WORDS32];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) record_terms<RULE>(m, vx[j], vy[j], vz[j], xi[j], false, w[j]);
-        const unsigned heads = run_totals(cc, nv, w);
+        for (int j = 0; j < 4; ++j) {
+            long long w[MAX_WORDS32];
+            record_terms<RULE>(m, vx[j], vy[j], vz[j], xi[j], false, w);
+            if (j > 0 && j < nv && cc[j] == cc[j - 1]) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if ((heads >> j) & 1u)
+                for (int k = 0; k < NW; ++k) acc[k] += w[k];
+            } else {
+                if (j > 0 && j - 1 < nv)
 #pragma unroll
-                for (int k = 0; k < NW; ++k) red_add(sums + k * C + cc[j], w[j][k]);
+                    for (int k = 0; k < NW; ++k) red_add(sums + k * C + cc[j - 1], acc[k]);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) acc[k] = w[k];
+            }
+        }
+        if (nv == 4)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) red_add(sums + k * C + cc[3], acc[k]);
     } else {
         constexpr int NW = RULE == 0 ? 6 : 8;
 #pragma unroll
@@ -1266,7 +1261,7 @@ __device__ __forceinline__ float i128f(__int128 x)
 // fixed-point sums, without cancellation: about a fixed-point reference
 // velocity w0 ~ u,  sum m|v - w0|^2 = S2 - 2 w0.S1 + M |w0|^2 is formed in exact
 // int128 arithmetic and E_rel = (that - |S1 - M w0|^2 / M) / 2.
-// Units: S1 of 2^-20, S2 of 2^-28, Mq of 2^-24, w0 of 2^-20; products of 2^-64.
+// Units: S1 of 2^-32, S2 of 2^-28, Mq of 2^-24, w0 of 2^-20; products of 2^-64.
 __device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long S1[3], long long S2, float M,
                                                   const float u[3])
 {
@@ -1276,14 +1271,14 @@ __device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long 
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         W[k] = __float2int_rn(fminf(fmaxf(u[k] * 1048576.0f, -5.0e8f), 5.0e8f));
-        D -= ((__int128)W[k] * S1[k]) << 25;
+        D -= ((__int128)W[k] * S1[k]) << 13;
         W2 += (long long)W[k] * W[k];
     }
     D += (__int128)Mq * W2;
     float r = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const __int128 dk = ((__int128)S1[k] << 44) - (((__int128)Mq * W[k]) << 20);
+        const __int128 dk = ((__int128)S1[k] << 32) - (((__int128)Mq * W[k]) << 20);
         const float df = i128f(dk) * 5.421010862427522170037264e-20f;   // 2^-64
         r += df * df;
     }
@@ -1301,14 +1296,15 @@ constexpr int PARAM_TILES = 2;
 
 template <int RULE>
 __device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplica &r, int64_t step, int64_t c,
-                                              const long long (&w)[4])
+                                              const long long (&w)[MAX_WORDS32])
 {
     const float kT = a.kTf;
-    const float s20 = 9.5367431640625e-07f;   // 2^-20
-    long long S1[3], cnt;
-    unpack2(w[0], S1[0], S1[1]);
-    unpack2(w[1], S1[2], cnt);
-    const int ns = (int)(cnt & 0xFFF), nb = (int)((cnt >> 12) & 0x3FF), n = ns + nb;
+    const float s32 = 2.3283064365386962890625e-10f;   // 2^-32
+    long long S1[3], cs, cb;
+    unpack48(w[0], cs, S1[0]);
+    unpack48(w[1], cb, S1[1]);
+    S1[2] = w[2];
+    const int ns = (int)cs, nb = (int)cb, n = ns + nb;
     float rec[8] = {0.f, 0.f, 0.f, -1.f, 0.f, 0.f, 0.f, 0.f};
     if (n >= 2) {
         const long long Mq = (long long)ns * a.qm_solvent + (long long)nb * a.qm_site;
@@ -1316,7 +1312,7 @@ __device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplic
         const float iM = 1.0f / M;
         float u[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) u[k] = ll2f(S1[k]) * s20 * iM;
+        for (int k = 0; k < 3; ++k) u[k] = ll2f(S1[k]) * s32 * iM;
         rec[0] = u[0]; rec[1] = u[1]; rec[2] = u[2];
         const uint32_t lc = (uint32_t)(c - r.cell_base);
         if (RULE == 0) {
@@ -1329,17 +1325,14 @@ __device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplic
             rec[4] = -rho * cs; rec[5] = -rho * sn; rec[6] = zz;
             float kappa = 1.0f;
             if (a.thermostat) {
-                const float erel = rel_energy_fixed(Mq, S1, w[2], M, u);
+                const float erel = rel_energy_fixed(Mq, S1, w[3], M, u);
                 const float g = gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
                 kappa = erel > 0.0f ? sqrtf(kT * g / erel) : 1.0f;
             }
             rec[3] = kappa;
         } else {
-            long long qx, qy, qz, zero;
-            unpack2(w[2], qx, qy);
-            unpack2(w[3], qz, zero);
             rec[3] = 1.0f;
-            rec[4] = ll2f(qx) * s20 * iM; rec[5] = ll2f(qy) * s20 * iM; rec[6] = ll2f(qz) * s20 * iM;
+            rec[4] = ll2f(w[3]) * s32 * iM; rec[5] = ll2f(w[4]) * s32 * iM; rec[6] = ll2f(w[5]) * s32 * iM;
         }
     }
     float4 *o = reinterpret_cast<float4 *>(a.params) + 2 * c;
@@ -1397,7 +1390,7 @@ __global__ void __launch_bounds__(256, 4) k_params32(StepArgs a)
         const Tile tl = stile[k];
         const int64_t c = tl.begin + threadIdx.x;
         if (c < tl.end) {
-            long long w[4] = {0, 0, 0, 0};
+            long long w[MAX_WORDS32] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int j = 0; j < NW; ++j) w[j] = sw[k][j][threadIdx.x];
             const DevReplica r = a.reps[tl.rep];
@@ -1922,7 +1915,7 @@ __device__ __forceinline__ void rn_fix(const StepArgs &a, int c, float v0, float
 {
     constexpr int NW = Words32<RULE>::n;
     const float xi[3] = {0.f, 0.f, 0.f};
-    long long w0[4], w1[4];
+    long long w0[MAX_WORDS32], w1[MAX_WORDS32];
     record_terms<RULE>(a.m_solvent_f, v0, vy, vz, xi, false, w0);
     record_terms<RULE>(a.m_solvent_f, v1, vy, vz, xi, false, w1);
     long long *sums = reinterpret_cast<long long *>(a.sums);

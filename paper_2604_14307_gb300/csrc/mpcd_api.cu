@@ -677,7 +677,8 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     c->nrep = n_replicas;
     c->nshapes = n_shapes;
     c->realsz = p.precision == MPCD_P32 ? 4 : 8;
-    c->nw = p.precision == MPCD_P32 ? (p.rule == MPCD_SRD ? 3 : 4) : (p.rule == MPCD_SRD ? 6 : 8);
+    c->nw = p.precision == MPCD_P32 ? (p.rule == MPCD_SRD ? Words32<0>::n : Words32<1>::n)
+                                    : (p.rule == MPCD_SRD ? 6 : 8);
     c->param_bytes = p.precision == MPCD_P32 ? 32 : 64;
     if (p.sort_period > 0) c->tune.sort_period = p.sort_period;
 

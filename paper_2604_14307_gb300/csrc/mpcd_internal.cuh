@@ -215,17 +215,39 @@ __device__ __forceinline__ long long pack2(long long hi, long long lo)
 }
 
 // The P32 cell words (SoA arrays of n_cells int64), exact sums over a cell of
-//   w0 = (p_x, p_y),  w1 = (p_z, count)           p = round(fl32(m v) 2^20)
-//   SRD: w2 = round(e 2^28), e = fl32(fl32(fl32(px vx) + fl32(py vy)) + fl32(pz vz))
-//   AT:  w2 = (q_x, q_y), w3 = (q_z, 0)           q = round(fl32(m xi) 2^20)
-// where (hi, lo) is the signed 32-bit pair hi 2^32 + lo and count is 1 for a
-// solvent particle, 2^12 for a site.
-template <int RULE> struct Words32 { static constexpr int n = RULE == 0 ? 3 : 4; };
+//   w0 = p_x + 2^48 [solvent],  w1 = p_y + 2^48 [site],  w2 = p_z
+//                                                  p = round(fl32(m v) 2^32)
+//   SRD: w3 = round(e 2^28), e = fl32(fl32(fl32(px vx) + fl32(py vy)) + fl32(pz vz))
+//   AT:  w3, w4, w5 = q                            q = round(fl32(m xi) 2^32)
+// The low 48 bits of w0 and w1 hold the signed momentum sums, the high 16 bits
+// the cell's solvent and site counts.  The 2^-32 quantum is below one float32
+// ulp of every |m v| >= 2^-9, so the momentum sums are the exact sums of the
+// float32 momenta (a term below 2^-9 is rounded by at most 2^-33).  Limits per
+// cell: |sum m v_a| < 2^15, at most 65535 solvent particles and 65535 sites.
+template <int RULE> struct Words32 { static constexpr int n = RULE == 0 ? 4 : 6; };
+constexpr int MAX_WORDS32 = 6;
+constexpr long long COUNT48 = 1LL << 48;
 
-// round-half-even(f 2^20) for |f 2^20| < 2^31 (every momentum term within the
-// P32 limits): the power-of-two scale is exact, so one 32-bit conversion gives
-// the same integer as qfix<20>
+// round-half-even(f 2^20) for |f 2^20| < 2^31: the power-of-two scale is
+// exact, so one 32-bit conversion gives the same integer as qfix<20> (the
+// momentum terms of the angular-momentum words)
 __device__ __forceinline__ long long q20(float f) { return (long long)__float2int_rn(__fmul_rn(f, 1048576.0f)); }
+
+// round-half-even(f 2^32) as int64 for |f| < 2^15, with 32-bit conversions
+// only.  t = f 2^8 is exact; with h = floor(t), f 2^32 = h 2^24 + (t - h) 2^24.
+// For |t| >= 1/2 (and t >= 0) the difference r = t - h is exact and r 2^24
+// is an integer or is rounded once by the last conversion; for t in [-1/2, 0)
+// r = t + 1 lies in [1/2, 1), where float32 has the spacing 2^-24, so forming
+// r rounds t 2^24 + 2^24 to an integer - the rounding the result needs (ties
+// to even: 2^24 is even).  Identical to qfix<32>(f).
+__device__ __forceinline__ long long q32(float f)
+{
+    const float t = __fmul_rn(f, 256.0f);
+    const int h = __float2int_rd(t);
+    const float r = __fsub_rn(t, __int2float_rn(h));
+    const int l = __float2int_rn(__fmul_rn(r, 16777216.0f));
+    return (long long)((unsigned long long)(long long)h << 24) + l;
+}
 
 // round-half-even(e 2^28) as int64 for 0 <= e < 2^28 (a kinetic-energy term),
 // with 32-bit conversions only: e = 16 h + r with h = floor(e / 16) (exact) and
@@ -242,20 +264,28 @@ __device__ __forceinline__ long long q28_nonneg(float e)
 
 template <int RULE>
 __device__ __forceinline__ void record_terms(float m, float vx, float vy, float vz, const float *xi, bool site,
-                                             long long w[4])
+                                             long long (&w)[MAX_WORDS32])
 {
     const float px = __fmul_rn(m, vx), py = __fmul_rn(m, vy), pz = __fmul_rn(m, vz);
-    const long long cnt = site ? (1LL << 12) : 1LL;
-    w[0] = pack2(q20(px), q20(py));
-    w[1] = pack2(q20(pz), cnt);
+    w[0] = q32(px) + (site ? 0LL : COUNT48);
+    w[1] = q32(py) + (site ? COUNT48 : 0LL);
+    w[2] = q32(pz);
     if (RULE == 0) {
         const float e = __fadd_rn(__fadd_rn(__fmul_rn(px, vx), __fmul_rn(py, vy)), __fmul_rn(pz, vz));
-        w[2] = q28_nonneg(e);
-        w[3] = 0;
+        w[3] = q28_nonneg(e);
+        w[4] = w[5] = 0;
     } else {
-        w[2] = pack2(q20(__fmul_rn(m, xi[0])), q20(__fmul_rn(m, xi[1])));
-        w[3] = pack2(q20(__fmul_rn(m, xi[2])), 0);
+        w[3] = q32(__fmul_rn(m, xi[0]));
+        w[4] = q32(__fmul_rn(m, xi[1]));
+        w[5] = q32(__fmul_rn(m, xi[2]));
     }
+}
+
+// a count|momentum word: the signed low 48 bits and the high 16-bit count
+__device__ __forceinline__ void unpack48(long long w, long long &count, long long &lo)
+{
+    lo = (long long)((unsigned long long)w << 16) >> 16;
+    count = (long long)((unsigned long long)(w - lo) >> 48);
 }
 
 // split a pair word into its signed 32-bit halves

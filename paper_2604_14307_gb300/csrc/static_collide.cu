@@ -23,7 +23,7 @@ constexpr int64_t TILE = 2048;                 // particles per work tile (a mul
 constexpr int64_t CELL_TILE = 256;             // cells per parameter tile (one CTA each)
 constexpr int64_t MAX_TILES = MAX_SOLVENT / TILE;
 constexpr int64_t MAX_CTILES = MAX_CELLS / CELL_TILE;
-constexpr int MAX_WORDS = 4;                   // P32 cell words: 3 (SRD) or 4 (AT)
+constexpr int MAX_WORDS = MAX_WORDS32;         // P32 cell words: 4 (SRD) or 6 (AT)
 
 // byte offsets inside the scratch array (each 256-byte aligned)
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -38,7 +38,7 @@ constexpr size_t SCRATCH_BYTES = OFF_ERR + 256;
 
 }  // namespace
 
-// The whole scratch of the call (about 4.1 MB), reserved in the module image.
+// The whole scratch of the call (about 5.2 MB), reserved in the module image.
 static __device__ __align__(256) unsigned char g_static_scratch[SCRATCH_BYTES];
 
 namespace {
@@ -147,7 +147,7 @@ extern "C" int mpcd_collide_solvent_static(const mpcd_params *p, const int32_t L
         su = g_setup[dev];
     }
 
-    const int nw = p->rule == MPCD_SRD ? 3 : 4;
+    const int nw = p->rule == MPCD_SRD ? Words32<0>::n : Words32<1>::n;
     DevReplica rep{};
     rep.L[0] = L[0]; rep.L[1] = L[1]; rep.L[2] = L[2];
     rep.cell_base = 0;

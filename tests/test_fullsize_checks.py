@@ -22,7 +22,7 @@ def oracle_step(system):
     p0 = momenta()
     O.stream(osys, ost)
     tr = O.collide(osys, ost)
-    nw = 3 if system.params.rule == I.SRD else 4
+    nw = 4 if system.params.rule == I.SRD else 6
     C = osys.n_cells
     par = np.zeros((C, 8))
     par[:, 0:3] = tr["cell_u"]
@@ -56,7 +56,7 @@ def test_checks_accept_the_oracle_and_reject_perturbations(make):
     # a cell word off by one unit is caught
     dd = dict(d)
     dd["sums"] = d["sums"].copy()
-    live = np.where(d["sums"][1] != 0)[0]
+    live = np.where(d["sums"][0] != 0)[0]
     dd["sums"][0, live[3]] += 1
     with pytest.raises(AssertionError):
         verify_step(system, st, gx, gv, dd, p0, p1, n_sample=300)

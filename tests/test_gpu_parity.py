@@ -52,24 +52,25 @@ def site_mask_cells(osys, tr):
     return m
 
 
-def halves(x):
-    lo = (x & 0xFFFFFFFF).astype(np.int64)
-    lo = np.where(lo >= 2**31, lo - 2**32, lo)
-    return (x - lo) >> 32, lo
+def unpack48(w):
+    """count|momentum word -> (count, signed low 48 bits)"""
+    w = np.asarray(w, dtype=np.int64)
+    lo = w & np.int64(2**48 - 1)
+    lo = np.where(lo >= 2**47, lo - 2**48, lo)
+    return ((w - lo).view(np.uint64) >> np.uint64(48)).astype(np.int64), lo
 
 
 def decode_record(w, rule):
     """P32 cell words -> physical sums (see include/mpcd.h)"""
     out = {}
-    px, py = halves(w[0])
-    pz, _ = halves(w[1])
-    out["p0"], out["p1"], out["p2"] = px * 2.0**-20, py * 2.0**-20, pz * 2.0**-20
+    out["p0"] = unpack48(w[0])[1] * 2.0**-32
+    out["p1"] = unpack48(w[1])[1] * 2.0**-32
+    out["p2"] = w[2] * 2.0**-32
     if rule == I.SRD:
-        out["e"] = w[2] * 2.0**-28
+        out["e"] = w[3] * 2.0**-28
     else:
-        qx, qy = halves(w[2])
-        qz, _ = halves(w[3])
-        out["q0"], out["q1"], out["q2"] = qx * 2.0**-20, qy * 2.0**-20, qz * 2.0**-20
+        for k in range(3):
+            out[f"q{k}"] = w[3 + k] * 2.0**-32
     return out
 
 
@@ -114,13 +115,14 @@ def one_step(B, system, check_sums=True):
         if prec == I.P32:
             w, fx = d["sums"], tr["fixed"]
             sm = site_mask_cells(osys, tr)
-            # counts (low half of w1): integer, bit-exact everywhere
-            assert np.array_equal(halves(w[1])[1], halves(fx[1])[1])
+            # counts (high 16 bits of w0, w1): integer, bit-exact everywhere
+            assert np.array_equal(unpack48(w[0])[0], unpack48(fx[0])[0])
+            assert np.array_equal(unpack48(w[1])[0], unpack48(fx[1])[0])
             if system.params.rule == I.SRD:
                 # only solvent (identical float inputs): every word bit-exact
-                assert np.array_equal(w[:, ~sm], fx[:3, ~sm])
+                assert np.array_equal(w[:, ~sm], fx[:4, ~sm])
             else:
-                assert np.array_equal(w[:2, ~sm], fx[:2, ~sm])
+                assert np.array_equal(w[:3, ~sm], fx[:3, ~sm])
             # with sites: decoded values within the tolerance
             gd, od = decode_record(w, system.params.rule), decode_record(fx, system.params.rule)
             M = tr["sums"][1]
@@ -275,7 +277,8 @@ def test_conservation_and_canonical_sort(B):
     # random walk of N steps x N_s roundings of about one ulp(1) = 2^-23 each
     # (|v| ~ sqrt(kT/m) = 1).  Ten times its size: the loss of one site's
     # momentum (m |v| ~ 1) or of one cell's would be 100x above the bar.
-    bar = 10.0 * np.sqrt(20 * system.n_solvent) * system.params.m_solvent * 2.0**-23
+    m2 = system.n_solvent * system.params.m_solvent ** 2 + system.n_sites * system.shapes[0].m[0] ** 2
+    bar = 10.0 * np.sqrt(20 * m2) * 2.0**-23
     print("total momentum change", np.abs(p1 - p0), "bar", bar)
     assert np.all(np.abs(p1 - p0) < bar), (np.abs(p1 - p0), bar)
     before = sim.get_state()

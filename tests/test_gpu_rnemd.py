@@ -95,7 +95,7 @@ def check_against_oracle(B, system, max_pairs, pipelined):
             sites[tr["cell_site"] + osys.cell_base[0]] = True
         # (AT: the noise words come from float32 transcendentals on the GPU, so
         # the momentum/count words are the exact ones there)
-        nw = 3 if system.params.rule == I.SRD else 2
+        nw = 4 if system.params.rule == I.SRD else 3
         assert np.array_equal(d["sums"][:nw, ~sites], tr["fixed"][:nw, ~sites])
     else:
         w = d["sums"]

@@ -108,43 +108,44 @@ def test_cell_sums_and_canonical_order_brute_force():
 
 
 def rne(x):
-    """round-to-nearest-even of float32 values (already scaled) to int64"""
+    """round-to-nearest-even of exactly scaled float values to int64"""
     return np.rint(x).astype(np.int64)
 
 
-def pack2(hi, lo):
-    return ((hi.astype(np.uint64) << np.uint64(32)).astype(np.int64) + lo)
+def unpack48(w):
+    """count|momentum word -> (count, signed low 48 bits)"""
+    w = np.asarray(w, dtype=np.int64)
+    lo = w & np.int64(2**48 - 1)
+    lo = np.where(lo >= 2**47, lo - 2**48, lo)
+    cnt = ((w - lo).view(np.uint64) >> np.uint64(48)).astype(np.int64)
+    return cnt, lo
 
 
 def record_numpy(cell, m, v, is_site, C, rule=I.SRD, xi=None):
-    """The P32 cell words recomputed with numpy float32 arithmetic:
-    w0 = (p_x, p_y), w1 = (p_z, count) at 2^20; SRD w2 = round(e 2^28);
-    AT w2 = (q_x, q_y), w3 = (q_z, 0), q = m xi."""
+    """The P32 cell words recomputed with numpy: float32 products, then the
+    float values scaled exactly in float64 and rounded to integers:
+    w0 = p_x + 2^48 [solvent], w1 = p_y + 2^48 [site], w2 = p_z with
+    p = round(fl32(m v) 2^32); SRD w3 = round(e 2^28); AT w3..w5 =
+    round(fl32(m xi) 2^32)."""
     mf = m.astype(np.float32)
     vf = v.astype(np.float32)
     p = mf[:, None] * vf                                   # float32 products
     e = (p[:, 0] * vf[:, 0] + p[:, 1] * vf[:, 1]) + p[:, 2] * vf[:, 2]
-    cnt = np.where(is_site, 1 << 12, 1).astype(np.int64)
-    s20 = np.float32(2.0**20)
-    w = np.zeros((4, len(m)), dtype=np.int64)
-    w[0] = pack2(rne(p[:, 0] * s20), rne(p[:, 1] * s20))
-    w[1] = pack2(rne(p[:, 2] * s20), cnt)
+    s32 = 2.0**32
+    w = np.zeros((6, len(m)), dtype=np.int64)
+    w[0] = rne(p[:, 0].astype(np.float64) * s32) + np.where(is_site, 0, 2**48)
+    w[1] = rne(p[:, 1].astype(np.float64) * s32) + np.where(is_site, 2**48, 0)
+    w[2] = rne(p[:, 2].astype(np.float64) * s32)
     if rule == I.SRD:
-        w[2] = rne(e * np.float32(2.0**28))
+        w[3] = rne(e.astype(np.float64) * 2.0**28)
     else:
         q = mf[:, None] * xi.astype(np.float32)
-        w[2] = pack2(rne(q[:, 0] * s20), rne(q[:, 1] * s20))
-        w[3] = pack2(rne(q[:, 2] * s20), np.zeros(len(m), dtype=np.int64))
-    out = np.zeros((4, C), dtype=np.int64)
-    for k in range(4):
+        for k in range(3):
+            w[3 + k] = rne(q[:, k].astype(np.float64) * s32)
+    out = np.zeros((6, C), dtype=np.int64)
+    for k in range(6):
         np.add.at(out[k], cell, w[k])
     return out
-
-
-def unpack2(w):
-    lo = (w & 0xFFFFFFFF).astype(np.int64)
-    lo = np.where(lo >= 2**31, lo - 2**32, lo)
-    return (w - lo) >> 32, lo
 
 
 def test_fixed_point_record_is_an_exact_integer_sum():
@@ -155,19 +156,27 @@ def test_fixed_point_record_is_an_exact_integer_sum():
     ref = record_numpy(cell, m, v0, is_site, 64)
     assert np.array_equal(tr["fixed"], ref)
     # decoding recovers the counts, the masses, the momenta and the energy
-    px, py = unpack2(tr["fixed"][0])
-    pz, cnt = unpack2(tr["fixed"][1])
-    n = (cnt & 0xFFF) + ((cnt >> 12) & 0x3FF)
-    assert np.array_equal(n, tr["sums"][0].astype(np.int64))
-    M = (cnt & 0xFFF) * 1.0 + ((cnt >> 12) & 0x3FF) * 5.0
+    ns, px = unpack48(tr["fixed"][0])
+    nb, py = unpack48(tr["fixed"][1])
+    pz = tr["fixed"][2]
+    assert np.array_equal(ns + nb, tr["sums"][0].astype(np.int64))
+    assert nb.sum() == osys.n_sites and ns.sum() == osys.n_solvent
+    M = ns * 1.0 + nb * 5.0
     assert np.allclose(M, tr["sums"][1], rtol=0, atol=1e-12)
+    # the momentum words are the exact sums of the float32 momenta fl32(m v):
+    # within the float32 rounding of each m v of the FP64 sums, and exactly
+    # the float64 sum of the float32 products (rounded to 2^-32) for m = 1
+    mf = m.astype(np.float32)
+    pf = (mf[:, None] * v0.astype(np.float32)).astype(np.float64)
     for k, h in enumerate((px, py, pz)):
-        assert np.allclose(h * 2.0**-20, tr["sums"][2 + k], atol=1e-4)
-    assert np.allclose(tr["fixed"][2] * 2.0**-28, tr["sums"][5], rtol=1e-6, atol=1e-6)
+        exact = np.bincount(cell, weights=pf[:, k], minlength=64)
+        assert np.allclose(h * 2.0**-32, exact, rtol=0, atol=2.0**-32 * 40)
+        assert np.allclose(h * 2.0**-32, tr["sums"][2 + k], rtol=0, atol=1e-6)
+    assert np.allclose(tr["fixed"][3] * 2.0**-28, tr["sums"][5], rtol=1e-6, atol=1e-6)
 
 
 def test_fixed_point_record_of_the_at_rule():
-    """AT form: no energy; noise sums as 32-bit pairs at 2^-20."""
+    """AT form: no energy; noise sums m xi at 2^-32 in words 3-5."""
     s, st = tiny_system(L=4, density=6.0, precision=I.P32, site_mass=5.0, rule=I.AT)
     osys, ost, pre, tr = run_collision(s, st)
     cell, m, v0, _ = members(osys, pre, tr, ost)
@@ -176,9 +185,30 @@ def test_fixed_point_record_of_the_at_rule():
     xi = O.normals(osys, 0, st.step, ids, O.TAG_AT) * np.sqrt(1.0 / m)[:, None]
     ref = record_numpy(cell, m, v0, ids >= ns, 64, rule=I.AT, xi=xi)
     assert np.array_equal(tr["fixed"], ref)
-    px, py = unpack2(tr["fixed"][0])
-    assert np.allclose(px * 2.0**-20, tr["sums"][2], atol=1e-4)
-    assert np.allclose(py * 2.0**-20, tr["sums"][3], atol=1e-4)
+    _, px = unpack48(tr["fixed"][0])
+    _, py = unpack48(tr["fixed"][1])
+    assert np.allclose(px * 2.0**-32, tr["sums"][2], atol=1e-6)
+    assert np.allclose(py * 2.0**-32, tr["sums"][3], atol=1e-6)
+    for k in range(3):
+        mx = np.bincount(cell, weights=m * xi[:, k], minlength=64)
+        assert np.allclose(tr["fixed"][3 + k] * 2.0**-32, mx, atol=1e-6)
+
+
+def test_fixed_point_words_are_exact_below_one_ulp():
+    """The 2^-32 momentum quantum against float32: every float32 |m v| >= 2^-9
+    is a multiple of 2^-32, so the word holds it exactly; smaller values round
+    by at most 2^-33 (the per-cell momentum sums are exact sums of the stored
+    float32 momenta, Sec. II.A)."""
+    rng = np.random.default_rng(5)
+    f = np.concatenate([rng.standard_normal(20000), rng.standard_normal(2000) * 1e-3,
+                        [2.0**-9, -2.0**-9, 3.0 * 2.0**-10, 1.5 * 2.0**-32, 2.5 * 2.0**-32, 30000.0]])
+    f = f.astype(np.float32).astype(np.float64)
+    q = rne(f * 2.0**32)
+    big = np.abs(f) >= 2.0**-9
+    assert np.array_equal(q[big] * 2.0**-32, f[big])
+    assert np.all(np.abs(q * 2.0**-32 - f) <= 2.0**-33)
+    # ties go to even: 1.5 -> 2, 2.5 -> 2 (in units of 2^-32)
+    assert list(q[-3:-1]) == [2, 2]
 
 
 # --------------------------------------------------------------- collision ---
@@ -223,26 +253,38 @@ def test_srd_rotates_relative_velocity_by_alpha():
     assert n_checked > 100
 
 
-def test_p32_thermostat_uses_the_fixed_point_energy():
-    """In the P32 form kappa^2 = E'/E_rel with E_rel formed from the cell's
-    fixed-point sums (float32 products m v.v of the stored velocities)."""
+def test_p32_thermostat_energy_is_the_relative_energy_of_the_stored_state():
+    """In the P32 form kappa^2 = E'/E_rel with E_rel from the cell's words.
+    Pinned against the plain definition E_rel = 1/2 sum m |v - u|^2 of the
+    stored float32 velocities (FP64): the difference can only come from the
+    float32 products fl32(fl32(m v_a) v_a) summed in float32 per particle
+    (at most 4 roundings of 2^-24 e_i each), the 2^-29 rounding of each energy
+    term and the float32 rounding of m v in the momentum sums."""
     s, st = tiny_system(L=4, density=6.0, precision=I.P32, site_mass=5.0, thermostat=1)
     osys, ost, pre, tr = run_collision(s, st)
     cell, m, v0, v1 = members(osys, pre, tr, ost)
-    fx = tr["fixed"]
+    vf = v0.astype(np.float32).astype(np.float64)
+    mf = m.astype(np.float32).astype(np.float64)
+    e = (mf[:, None] * vf * vf).sum(1)
+    n_checked = 0
     for c in range(64):
         sel = cell == c
         if sel.sum() < 2:
             continue
-        px, py = unpack2(fx[0:1, c])
-        pz, _ = unpack2(fx[1:2, c])
-        S1 = np.array([px[0], py[0], pz[0]]) * 2.0**-20
-        S2 = fx[2, c] * 2.0**-28
-        Erel = 0.5 * (S2 - (S1 @ S1) / m[sel].sum())
-        u = tr["cell_u"][c]
-        Epost = 0.5 * (m[sel, None] * (v1[sel] - u) ** 2).sum()
-        # the post-collision relative energy is kappa^2 E_rel (rotation keeps |v - u|)
-        assert abs(Epost - tr["cell_kappa"][c] ** 2 * Erel) < 1e-5 * max(Epost, 1e-3)
+        M = mf[sel].sum()
+        u = (mf[sel, None] * vf[sel]).sum(0) / M
+        E = 0.5 * (mf[sel, None] * (vf[sel] - u) ** 2).sum()
+        S1 = np.abs(mf[sel, None] * vf[sel]).sum(0)
+        bound = 0.5 * ((4 * 2.0**-24 * e[sel] + 2.0**-29).sum() + 2 * 2.0**-24 * (S1 @ S1) / M)
+        Ep = O.thermostat_energy(osys, 0, 0, c, int(sel.sum()))
+        E32 = Ep / tr["cell_kappa"][c] ** 2
+        assert abs(E32 - E) <= bound * (1 + 1e-9) + 1e-15 * Ep, (c, E32, E, bound)
+        # and the collision realises it: post-collision relative energy = kappa^2 E_rel,
+        # up to the float32 rounding of the stored new velocities
+        Epost = 0.5 * (m[sel, None] * (v1[sel] - tr["cell_u"][c]) ** 2).sum()
+        assert abs(Epost - Ep) < 2.0**-20 * max(Ep, 1e-3)
+        n_checked += 1
+    assert n_checked > 40
 
 
 def test_thermostat_energy_follows_eq6_gamma():
@@ -553,9 +595,7 @@ def test_exported_axis_and_thermostat_match_the_collision():
     for c in sel:
         assert np.array_equal(O.srd_axis(osys, 0, 0, int(c)), tr["cell_axis"][c])
         fx = tr["fixed"][:, c]
-        lo0 = (int(fx[0]) + 2**31) % 2**32 - 2**31
-        lo1 = (int(fx[1]) + 2**31) % 2**32 - 2**31
-        S1 = np.array([(int(fx[0]) - lo0) >> 32, lo0, (int(fx[1]) - lo1) >> 32], dtype=np.float64) * 2.0**-20
-        erel = 0.5 * (float(fx[2]) * 2.0**-28 - float(S1 @ S1) / M[c])
+        S1 = np.array([unpack48(fx[0])[1], unpack48(fx[1])[1], fx[2]], dtype=np.float64) * 2.0**-32
+        erel = 0.5 * (float(fx[3]) * 2.0**-28 - float(S1 @ S1) / M[c])
         kappa = np.sqrt(O.thermostat_energy(osys, 0, 0, int(c), int(n[c])) / erel)
         assert abs(kappa - tr["cell_kappa"][c]) <= 1e-12 * kappa
