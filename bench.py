@@ -55,6 +55,9 @@ def args_():
                          "batched workloads and the paper-shaped phi sweep (--phi), for the record")
     ap.add_argument("--phi", type=float, default=0.3, help="volume fraction of phi_sweep_L120")
     ap.add_argument("--n-rep", type=int, default=0, help="replicas of the batched workloads (0: their default)")
+    ap.add_argument("--thermostat", type=int, default=2, choices=[1, 2],
+                    help="cell thermostat of the SRD workloads: E' ~ Gamma(3(Nc-1)/2, kT) drawn by "
+                         "Marsaglia-Tsang rejection (2, the default) or as a sum of exponentials (1)")
     ap.add_argument("--rule", default="srd", choices=["srd", "at"],
                     help="collision rule of the workload: SRD with the cell thermostat (the benchmark) or "
                          "MPCD-AT (for the ALU-side measurement of the Philox/Box-Muller path)")
@@ -170,7 +173,7 @@ def host_cpu():
     return len(os.sched_getaffinity(0)), model or "unknown"
 
 
-def cpu_baseline(Bd, steps: int = 6, L: int = 80):
+def cpu_baseline(Bd, thermostat: int, steps: int = 6, L: int = 80):
     """The plain FP64 oracle as it stands, one host core, on a bounded sample of
     the workload: an L=80 box with the same density, volume fraction, colloid
     radius and 642-site shells (5.5M particle-updates per step).  The first of
@@ -180,7 +183,7 @@ def cpu_baseline(Bd, steps: int = 6, L: int = 80):
     import oracle as O
     from oracle import parity as OP
     from paper_2604_14307_gb300 import inputs as I
-    s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1, name="sample")
+    s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, thermostat, I.P32, seed=1, name="sample")
     st = I.initial_state(s)
     n = s.n_solvent + s.n_sites
     t0 = time.perf_counter()
@@ -204,7 +207,7 @@ def cpu_baseline(Bd, steps: int = 6, L: int = 80):
     sim.couple(Bd.MPCD_POST)
     g = sim.get_state()
     sim.close()
-    par = OP.compare(s, st, g, d["site_cell"], d["shift"], ref=ref)
+    par = OP.compare(s, st, g, d["site_cell"], d["shift"], ref=ref, params=d["params"])
     cores, model = host_cpu()
     return {"value": n / float(np.median(times)), "unit": UNIT, "cores": 1, "kind": "oracle",
             "mode": "plain FP64 (no float32 decision, no fixed-point word)",
@@ -314,7 +317,7 @@ def run_reference(a, ws, rank):
     import oracle as O
     from paper_2604_14307_gb300 import inputs as I
     L = 60
-    s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, 1, I.P32, seed=1, name="sample")
+    s = I.suspension(L, 10.0, 0.3, 4.0, 3, 10.0, I.SRD, a.thermostat, I.P32, seed=1, name="sample")
     st = I.initial_state(s)
     osys = O.OracleSystem(s, precision=O.P64)   # the plain FP64 method
     ost = O.OracleState(osys, st)
@@ -356,7 +359,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     L = a.L
-    rule, thermo = (I.SRD, 1) if a.rule == "srd" else (I.AT, 0)
+    rule, thermo = (I.SRD, a.thermostat) if a.rule == "srd" else (I.AT, 0)
 
     def make_system(precision):
         """The workload in the given arithmetic form (seeded per rank)."""
@@ -540,14 +543,16 @@ def main():
 
     cpu, parity = None, None
     if rank == 0 and not a.no_cpu and default_workload:   # the oracle sample is of the benchmark composition
-        cpu, parity = cpu_baseline(Bd)
+        cpu, parity = cpu_baseline(Bd, a.thermostat)
         cpu.pop("seconds", None)
 
     state_bytes_dev = system.n_solvent * 28 + system.n_cells * 56
     l2_note = ("no flush: state per GPU (%.1f GB) is larger than L2 (129 MB)" % (state_bytes_dev / 1e9)
                if state_bytes_dev > 129e6 else
                "no flush: the state fits in L2 (129 MB), so the bandwidth fraction is not meaningful")
-    rule_note = ("SRD alpha=130" + (" + cell-level thermostat" if system.params.thermostat else "")
+    rule_note = ("SRD alpha=130" + ({1: " + cell-level thermostat (E' as a sum of exponentials)",
+                                      2: " + cell-level thermostat (E' by Marsaglia-Tsang rejection)"}
+                                     .get(system.params.thermostat, ""))
                  if system.params.rule == I.SRD else "MPCD-AT (Andersen thermostat rule)")
     if getattr(system.params, "angular", 0):
         rule_note += ", angular-momentum-conserving (+a, unfused step)"

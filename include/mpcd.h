@@ -68,8 +68,15 @@ typedef struct {
     double alpha_deg;     /* SRD rotation angle (130 in the paper) */
     double m_solvent;     /* solvent particle mass */
     int32_t rule;         /* MPCD_SRD or MPCD_AT */
-    int32_t thermostat;   /* 1: cell-level thermostat for SRD (AT is intrinsically
-                             thermostatted and ignores it) */
+    int32_t thermostat;   /* cell-level thermostat for SRD (AT is intrinsically
+                             thermostatted and ignores it): each cell's relative
+                             kinetic energy is rescaled to E' ~ Gamma(3(N_c-1)/2, kT)
+                             (Eq. 6).  0: off; 1: E' drawn without rejection as a
+                             sum of unit exponentials (the reference form);
+                             2: E' drawn by the rejection method of Marsaglia and
+                             Tsang (same distribution, about one Philox block per
+                             cell; FP32 and FP64 may decide a rejection differently
+                             in rare cells) */
     int32_t precision;    /* MPCD_P64 or MPCD_P32 */
     int32_t naive_transfer; /* 1: skip Eq. 7 (negative control of Fig. S1) */
     uint64_t seed;        /* Philox4x32-10 key */

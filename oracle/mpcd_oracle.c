@@ -28,7 +28,9 @@
  *            counter (step, id, tag, j); uniform u = (x + 0.5) 2^-32;
  *            Box-Muller normals; axis z = 2u1 - 1, phi = 2 pi u2;
  *   thermostat E' ~ Gamma(3(Nc-1)/2, kT) (Eq. 6 with n = 3(Nc-1)) drawn as a sum
- *            of floor(n/2) unit exponentials plus z^2/2 for odd n; kappa = sqrt(E'/E_rel);
+ *            of floor(n/2) unit exponentials plus z^2/2 for odd n (thermostat = 1),
+ *            or by the rejection method of Marsaglia and Tsang (thermostat = 2);
+ *            kappa = sqrt(E'/E_rel);
  *   cells with fewer than two particles are left unchanged;
  *   sort order within a cell: solvent before sites, each by ascending id;
  *   the momentum change is an impulse at the collision; centre sites are
@@ -57,7 +59,7 @@
 #define ORC_AT 1
 
 enum { TAG_SHIFT = 1, TAG_AXIS = 2, TAG_THERMO = 3, TAG_THERMO_ODD = 4,
-       TAG_SITE = 5, TAG_AT = 6 };
+       TAG_SITE = 5, TAG_AT = 6, TAG_THERMO_MT = 7 };
 
 typedef struct {
     double kT, dt, alpha_deg, m_solvent;
@@ -633,10 +635,39 @@ int orc_stream(const orc_sys *s, orc_state *st)
 /* ------------------------------------------------------------------ */
 /* a2-a8: one collision at key `step`                                  */
 /* ------------------------------------------------------------------ */
+/* Gamma(a, 1) for a >= 1 by the squeeze-free rejection method of Marsaglia and
+ * Tsang (ACM Trans. Math. Softw. 26, 363 (2000)): with d = a - 1/3 and
+ * c = 1/sqrt(9 d), draw a standard normal x and a uniform u, set v = (1 + c x)^3,
+ * and accept d v when v > 0 and ln u < x^2/2 + d - d v + d ln v.  Each Philox
+ * block (counter word 3 = block index) gives two attempts: the Box-Muller pair
+ * x = r cos(2 pi u1), r sin(2 pi u1) with r = sqrt(-2 ln u0), and the uniforms
+ * of words 2 and 3.  After 64 blocks (never reached in practice: each attempt
+ * is accepted with probability > 0.95) the mode-like value d is returned. */
+#define MT_MAX_BLOCKS 64
+static double gamma_marsaglia_tsang(const orc_sys *s, int rep, int64_t step, uint32_t cell, double a)
+{
+    const double d = a - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+    for (uint32_t k = 0; k < MT_MAX_BLOCKS; ++k) {
+        uint32_t w[4];
+        draw(s, rep, step, cell, TAG_THERMO_MT, k, w);
+        const double r = sqrt(-2.0 * log(u01(w[0])));
+        const double ph = 6.283185307179586476925286766559 * u01(w[1]);
+        const double xs[2] = { r * cos(ph), r * sin(ph) };
+        for (int j = 0; j < 2; ++j) {
+            const double x = xs[j], t = 1.0 + c * x;
+            if (t <= 0.0) continue;
+            const double v = t * t * t;
+            if (log(u01(w[2 + j])) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+        }
+    }
+    return d;
+}
+
 static double thermostat_energy(const orc_sys *s, int rep, int64_t step, uint32_t cell, int64_t Nc)
 {
     /* E' ~ Gamma(n/2, kT) with n = 3(Nc - 1) (Eq. 6) */
     int64_t n = 3 * (Nc - 1), nE = n / 2;
+    if (s->thermostat == 2) return s->kT * gamma_marsaglia_tsang(s, rep, step, cell, 0.5 * (double)n);
     double g = 0.0;
     uint32_t w[4];
     for (int64_t i = 0; i < nE; ++i) {

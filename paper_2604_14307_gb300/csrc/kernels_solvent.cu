@@ -1247,6 +1247,62 @@ __device__ double gamma_half_dof(const DevReplica &r, int64_t step, uint32_t lc,
     return g;
 }
 
+// Gamma(a, 1), a = n/2 >= 3/2, by the rejection method of Marsaglia and Tsang
+// (ACM Trans. Math. Softw. 26, 363 (2000)), without their squeeze: d = a - 1/3,
+// c = 1/sqrt(9 d); a standard normal x and a uniform u give v = (1 + c x)^3,
+// accepted (d v) when v > 0 and ln u < x^2/2 + d (1 - v + ln v).  Each Philox
+// block (word 3 of the counter = block index) gives two attempts: the
+// Box-Muller pair of words 0 and 1 and the uniforms of words 2 and 3; after
+// MT_MAX_BLOCKS blocks (never reached in practice: an attempt is accepted with
+// probability > 0.95) d is returned.  FP32 form: with y = c x the test is
+// evaluated as -2 ln u > -x^2 - 2 d (log1p(dv) - dv), dv = v - 1 =
+// y (3 + y (3 + y)), which keeps the cancellation of 1 - v + ln v out of it;
+// the normals use accurate (not fast) logarithm and sine/cosine.
+constexpr uint32_t MT_MAX_BLOCKS = 64;
+__device__ float gamma_mt(const DevReplica &r, int64_t step, uint32_t lc, int n_dof, float)
+{
+    const float a = 0.5f * (float)n_dof;
+    const float d = a - 0.333333343f;
+    const float c = 1.0f / sqrtf(9.0f * d);
+    for (uint32_t k = 0; k < MT_MAX_BLOCKS; ++k) {
+        const uint4 w = draw(r, step, lc, TAG_THERMO_MT, k);
+        const float rr = sqrtf((w.x & 0x80000000u) ? -2.0f * log1pf(-u01f(~w.x)) : -2.0f * logf(u01f(w.x)));
+        float sn, cs;
+        sincospif(2.0f * u01f(w.y) - 1.0f, &sn, &cs);     // angle 2 pi u - pi: cos(2 pi u) = -cs
+        const float xs[2] = {-rr * cs, -rr * sn};
+        const uint32_t us[2] = {w.z, w.w};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float x = xs[j], y = c * x;
+            if (y <= -1.0f) continue;
+            const float dv = y * (3.0f + y * (3.0f + y));
+            const float m2lu = (us[j] & 0x80000000u) ? -2.0f * log1pf(-u01f(~us[j])) : -2.0f * logf(u01f(us[j]));
+            if (m2lu > -x * x - 2.0f * d * (log1pf(dv) - dv)) return d * (1.0f + dv);
+        }
+    }
+    return d;
+}
+__device__ double gamma_mt(const DevReplica &r, int64_t step, uint32_t lc, int n_dof, double)
+{
+    const double a = 0.5 * (double)n_dof;
+    const double d = a - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+    for (uint32_t k = 0; k < MT_MAX_BLOCKS; ++k) {
+        const uint4 w = draw(r, step, lc, TAG_THERMO_MT, k);
+        const double rr = sqrt(-2.0 * log(u01d(w.x)));
+        double sn, cs;
+        sincos(6.283185307179586476925286766559 * u01d(w.y), &sn, &cs);
+        const double xs[2] = {rr * cs, rr * sn};
+        const uint32_t us[2] = {w.z, w.w};
+        for (int j = 0; j < 2; ++j) {
+            const double x = xs[j], t = 1.0 + c * x;
+            if (t <= 0.0) continue;
+            const double v = t * t * t;
+            if (log(u01d(us[j])) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+        }
+    }
+    return d;
+}
+
 // signed 128-bit -> float by magnitude (|error| <= 2 ulp)
 __device__ __forceinline__ float i128f(__int128 x)
 {
@@ -1326,7 +1382,8 @@ __device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplic
             float kappa = 1.0f;
             if (a.thermostat) {
                 const float erel = rel_energy_fixed(Mq, S1, w[3], M, u);
-                const float g = gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
+                const float g = a.thermostat == 2 ? gamma_mt(r, step, lc, 3 * (n - 1), 0.0f)
+                                                  : gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
                 kappa = erel > 0.0f ? sqrtf(kT * g / erel) : 1.0f;
             }
             rec[3] = kappa;
@@ -1451,7 +1508,8 @@ __global__ void __launch_bounds__(256) k_params(StepArgs a)
                     Real kappa = Real(1);
                     if (a.thermostat) {
                         Real erel = Real(0.5) * (s2 - (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) / M);
-                        Real g = gamma_half_dof(r, step, lc, 3 * (n - 1), Real(0));
+                        Real g = a.thermostat == 2 ? gamma_mt(r, step, lc, 3 * (n - 1), Real(0))
+                                                   : gamma_half_dof(r, step, lc, 3 * (n - 1), Real(0));
                         kappa = erel > Real(0) ? sqrt(kT * g / erel) : Real(1);
                     }
                     rec[3] = kappa;

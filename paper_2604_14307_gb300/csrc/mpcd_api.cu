@@ -659,7 +659,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     const mpcd_params &p = *params;
     if (!(p.kT > 0) || !(p.dt > 0) || !(p.m_solvent > 0) || !std::isfinite(p.alpha_deg) ||
         (p.rule != MPCD_SRD && p.rule != MPCD_AT) || (p.precision != MPCD_P32 && p.precision != MPCD_P64) ||
-        (p.angular != 0 && p.angular != 1))
+        (p.angular != 0 && p.angular != 1) || p.thermostat < 0 || p.thermostat > 2)
         return MPCD_ERR_ARG;
     if (allocator && (!allocator->alloc || !allocator->free)) return MPCD_ERR_ARG;
     int ndev = 0;

@@ -32,7 +32,7 @@ namespace mpcd {
 
 // Counter word 2 of every random draw (stream tags).
 enum : uint32_t { TAG_SHIFT = 1, TAG_AXIS = 2, TAG_THERMO = 3, TAG_THERMO_ODD = 4,
-                  TAG_SITE = 5, TAG_AT = 6 };
+                  TAG_SITE = 5, TAG_AT = 6, TAG_THERMO_MT = 7 };
 // Bits of the device error word.
 enum : int { ERR_POSITION = 1, ERR_CELL = 2, ERR_TIMEOUT = 4, ERR_INDEX = 8, ERR_RNEMD = 16 };
 

@@ -97,8 +97,8 @@ extern "C" int mpcd_collide_solvent_static(const mpcd_params *p, const int32_t L
         return reject(msg, msg_len, "only the P32 form (FP32 state, fixed-point cell sums) is supported");
     if (p->rule != MPCD_SRD && p->rule != MPCD_AT) return reject(msg, msg_len, "rule must be MPCD_SRD or MPCD_AT");
     if (!(p->kT > 0.0) || !(p->m_solvent > 0.0) || !(p->alpha_deg == p->alpha_deg) ||
-        (p->thermostat != 0 && p->thermostat != 1) || p->angular != 0)
-        return reject(msg, msg_len, "invalid params (kT > 0, m_solvent > 0, thermostat 0/1, angular 0)");
+        p->thermostat < 0 || p->thermostat > 2 || p->angular != 0)
+        return reject(msg, msg_len, "invalid params (kT > 0, m_solvent > 0, thermostat 0/1/2, angular 0)");
     // the binning rule forms floor(x 2^20) in 32 bits, so an edge must stay below 2048 cells
     if (L[0] < 3 || L[1] < 3 || L[2] < 3 || L[0] > 2047 || L[1] > 2047 || L[2] > 2047)
         return reject(msg, msg_len, "every box edge L must be 3 to 2047 cells");

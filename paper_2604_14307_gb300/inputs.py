@@ -571,10 +571,11 @@ def suspension_L50(precision: int = P32, seed: int = 1) -> System:
     return suspension(50, 5.0, 0.2, 3.0, 3, 5.0, AT, 1, precision, seed, "suspension_L50_phi0.2")
 
 
-def suspension_L200(precision: int = P32, seed: int = 1) -> System:
+def suspension_L200(precision: int = P32, seed: int = 1, thermostat: int = 2) -> System:
     """L=200, density 10, ~8950 radius-4 spheres of 642 sites (phi~0.3),
-    SRD with the cell-level thermostat."""
-    return suspension(200, 10.0, 0.3, 4.0, 3, 10.0, SRD, 1, precision, seed, "suspension_L200_phi0.3")
+    SRD with the cell-level thermostat (E' drawn by Marsaglia-Tsang rejection
+    by default, 1: as a sum of exponentials)."""
+    return suspension(200, 10.0, 0.3, 4.0, 3, 10.0, SRD, thermostat, precision, seed, "suspension_L200_phi0.3")
 
 
 def batched_single_sphere(n_rep: int = 4096, precision: int = P32, seed: int = 1,

@@ -198,9 +198,12 @@ def verify_step(system, st, gx, gv_all, d, p_before, p_after, n_sample=2000, see
     return sample.size, sel.size
 
 
-def test_full_size_suspension_L200(B):
-    """The benchmark workload: L=200, 80 M solvent, 8952 642-site spheres, SRD + thermostat."""
-    ns, np_ = check_full_step(B, I.suspension_L200(I.P32, seed=1))
+@pytest.mark.parametrize("thermostat", [2, 1])
+def test_full_size_suspension_L200(B, thermostat):
+    """The benchmark workload: L=200, 80 M solvent, 8952 642-site spheres, SRD +
+    thermostat (E' by Marsaglia-Tsang rejection, as bench.py times it, and as a
+    sum of exponentials)."""
+    ns, np_ = check_full_step(B, I.suspension_L200(I.P32, seed=1, thermostat=thermostat))
     assert ns >= 1000 and np_ >= 5000
 
 

@@ -162,7 +162,7 @@ def test_one_step_single_sphere_L10(B, prec):
 
 
 @pytest.mark.parametrize("prec", [I.P64, I.P32])
-@pytest.mark.parametrize("rule,thermo", [(I.SRD, 1), (I.AT, 0)])
+@pytest.mark.parametrize("rule,thermo", [(I.SRD, 1), (I.SRD, 2), (I.AT, 0)])
 def test_one_step_small_suspension(B, prec, rule, thermo):
     system = I.suspension(16, 5.0, 0.15, 2.0, 2, 5.0, rule, thermo, prec, seed=3, name="small")
     assert system.n_bodies >= 3

@@ -287,10 +287,12 @@ def test_p32_thermostat_energy_is_the_relative_energy_of_the_stored_state():
     assert n_checked > 40
 
 
-def test_thermostat_energy_follows_eq6_gamma():
+@pytest.mark.parametrize("sampler", [1, 2])
+def test_thermostat_energy_follows_eq6_gamma(sampler):
     """Huang cell thermostat: the post-collision relative KE of a cell with Nc
-    particles is Gamma(3(Nc-1)/2, kT) distributed (Eq. 6, n = 3(Nc-1))."""
-    prm = I.Params(rule=I.SRD, thermostat=1, seed=11)
+    particles is Gamma(3(Nc-1)/2, kT) distributed (Eq. 6, n = 3(Nc-1)), with E'
+    drawn as a sum of exponentials (1) or by Marsaglia-Tsang rejection (2)."""
+    prm = I.Params(rule=I.SRD, thermostat=sampler, seed=11)
     s = I.build_system(prm, [I.sphere_shape(1.0, 0, 1.0)], [(14, 14, 14)], 4.0, [[]], "bulk")
     st = I.initial_state(s)
     osys, ost, pre, tr = run_collision(s, st)
@@ -306,6 +308,25 @@ def test_thermostat_energy_follows_eq6_gamma():
     # velocities are rotated and scaled about the preserved cell velocity
     kap = tr["cell_kappa"][sel]
     assert np.all(kap > 0) and abs(np.median(kap) - 1) < 0.2
+
+
+@pytest.mark.parametrize("nc", [2, 3, 6, 11, 30])
+def test_marsaglia_tsang_draws_follow_eq6(nc):
+    """orc_thermostat_energy with the rejection sampler: 4000 cells of Nc
+    particles, E'/kT against Gamma(3(Nc-1)/2) (Eq. 6) by KS, mean and variance
+    against n kT/2 and n (kT)^2/2; kT = 1.7 scales the draw."""
+    prm = I.Params(rule=I.SRD, thermostat=2, seed=21, kT=1.7)
+    s = I.build_system(prm, [I.sphere_shape(1.0, 0, 1.0)], [(20, 20, 10)], 1.0, [[]], "bulk")
+    osys = O.OracleSystem(s)
+    E = np.array([O.thermostat_energy(osys, 0, 3, c, nc) for c in range(4000)]) / 1.7
+    a = 1.5 * (nc - 1)
+    assert stats.kstest(E, stats.gamma(a).cdf).pvalue > 1e-3
+    assert abs(E.mean() - a) < 4 * math.sqrt(a / len(E))
+    assert abs(E.var() / a - 1) < 0.15
+    # not the exponential-sum draws (independent streams): the samplers differ
+    o1 = O.OracleSystem(s, thermostat=1)
+    E1 = np.array([O.thermostat_energy(o1, 0, 3, c, nc) for c in range(50)]) / 1.7
+    assert not np.allclose(E1, E[:50])
 
 
 def test_at_rule_momentum_and_relative_variance():
