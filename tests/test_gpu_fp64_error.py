@@ -9,11 +9,15 @@ bodies) against the plain FP64 method, and its per-cell momentum.
    (a particle within one float32 rounding of a shifted cell face lands in
    another cell in the two runs) are counted, not compared; there may be only
    a handful of them.
-2. Per-cell momentum of the plain rules on the GPU's own data: in every cell
-   that holds no colloid site, sum m (v' - v) stays within the float32
-   rounding of the new velocities, N_c m ulp(max |v|, |v'|) per component
-   (Sec. II.A: the collision conserves each cell's momentum; the FP32 form adds
-   only the rounding of the stored result).
+2. Per-cell momentum of the plain rules on the GPU's own data (Sec. II.A: the
+   collision conserves each cell's momentum; with the exact fixed-point sums
+   the FP32 form adds only the float32 evaluation of the rule).  In every cell
+   that holds no colloid site, |sum m (v' - v)| is measured in units of
+   N_c m ulp(max |v|, |v'|): each new velocity comes from about ten float32
+   operations on values no larger than that maximum, which bounds the ratio by
+   a few units; the test asserts a mean below 1/2 and a maximum of 4
+   (measured 0.23-0.29 and 1.6-2.4; with the former 2^-20 momentum words,
+   1.4-1.5 and 10-19).
 """
 import numpy as np
 import pytest
@@ -123,4 +127,4 @@ def test_per_cell_momentum_is_conserved_to_float_rounding(B, rule, thermo):
     ratio = np.abs(dp[sel]).max(1) / bound[sel]
     print(rule, thermo, "cells", int(sel.sum()), "max |dP| / (N m ulp)", float(ratio.max()),
           "mean", float(ratio.mean()))
-    assert ratio.max() <= 1.0, float(ratio.max())
+    assert ratio.mean() <= 0.5 and ratio.max() <= 4.0, (float(ratio.mean()), float(ratio.max()))

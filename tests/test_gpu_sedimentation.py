@@ -70,19 +70,29 @@ def test_one_forced_step_matches_oracle(B, pipelined, precision, rule):
 
 
 def test_forced_box_stays_force_free(B):
+    """Total momentum stays constant under the balanced force, while the bodies'
+    momentum along f, averaged over the second half of the run, is positive.
+    The thermal momentum of the four bodies fluctuates by about sqrt(4 M kT) ~ 57
+    around a mean of ~100 at this force (oracle runs, four seeds: time averages
+    101-162), so the average over 20 samples, not one instant, is tested."""
     system = box(I.P32, n_bodies=4, seed=9)
     st = I.initial_state(system)
     sim = B.Simulation(system)
     sim.set_state(st)
-    sim.set_body_force(10 * F)      # strong enough to beat the bodies' thermal momentum
+    sim.set_body_force(40 * F)      # strong enough to beat the bodies' thermal momentum
     d0 = sim.diagnostics()
     p0 = np.asarray(d0["p_solvent"]) + np.asarray(d0["p_bodies"])
-    sim.step(400)
+    sim.step(200)
+    pb = []
+    for _ in range(20):
+        sim.step(10)
+        pb.append(sim.diagnostics()["p_bodies"][0])
     d1 = sim.diagnostics()
     p1 = np.asarray(d1["p_solvent"]) + np.asarray(d1["p_bodies"])
     sim.close()
     assert np.all(np.abs(p1 - p0) < 1e-2 * np.sqrt(system.n_solvent + system.n_sites))
-    assert d1["p_bodies"][0] - d0["p_bodies"][0] > 0.0
+    print("time-averaged body momentum along f:", np.mean(pb), "+-", np.std(pb))
+    assert np.mean(pb) > 0.0
 
 
 def test_force_needs_one_replica_with_solvent(B):
