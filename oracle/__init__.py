@@ -36,7 +36,9 @@ def build(force: bool = False) -> str:
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.check_call(cmd)
+        # with OpenMP where the compiler has it (orc_set_threads; one thread by default)
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -91,6 +93,8 @@ def lib():
             _lib.orc_rotation_matrix.argtypes = [C.c_void_p, C.c_void_p]
             _lib.orc_normals.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_uint32,
                                          C.c_uint32, C.c_void_p]
+            _lib.orc_set_threads.argtypes = [C.c_int]
+            _lib.orc_set_threads.restype = C.c_int
     return _lib
 
 
@@ -248,6 +252,13 @@ def body_energies(osys: OracleSystem, st: OracleState):
     cs = st.c()
     lib().orc_body_energies(C.byref(osys.c), C.byref(cs), _ptr(ET), _ptr(ER))
     return ET[: osys.n_bodies], ER[: osys.n_bodies]
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's independent per-particle and per-cell loops
+    (OpenMP; the results do not depend on it).  Returns the count in use: 1 if
+    the oracle was built without OpenMP."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def philox(ctr, key) -> np.ndarray:

@@ -52,6 +52,27 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the loops whose iterations are independent (one particle, one
+ * cell): every output is computed by the same arithmetic in the same order as
+ * with one thread, so the results do not depend on the thread count.  One
+ * thread unless orc_set_threads() asks for more (and the file was compiled
+ * with OpenMP). */
+static int g_threads = 1;
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
 
 #define ORC_P64 0
 #define ORC_P32 1
@@ -570,6 +591,8 @@ int orc_stream(const orc_sys *s, orc_state *st)
                 const double g = -((double)nb * s->f_ext[a]) / ((double)ns * s->m_solvent);
                 half[a] = 0.5 * g * dt;
             }
+        int bad = 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static) reduction(|| : bad)
         for (int64_t i = s->solv_off[r]; i < s->solv_off[r + 1]; ++i) {
             for (int a = 0; a < 3; ++a) {
                 if (s->precision == ORC_P32) {
@@ -578,7 +601,7 @@ int orc_stream(const orc_sys *s, orc_state *st)
                     if (accel) v = v + h;
                     float step = v * dtf;
                     float y = x + step;
-                    if (wrap_f(&y, (float)L[a])) return -1;
+                    if (wrap_f(&y, (float)L[a])) bad = 1;
                     if (accel) v = v + h;
                     st->x[3 * i + a] = (double)y;
                     st->v[3 * i + a] = (double)v;
@@ -586,13 +609,14 @@ int orc_stream(const orc_sys *s, orc_state *st)
                     double v = st->v[3 * i + a];
                     if (accel) v = v + half[a];
                     double y = st->x[3 * i + a] + v * dt;
-                    if (wrap_d(&y, (double)L[a])) return -1;
+                    if (wrap_d(&y, (double)L[a])) bad = 1;
                     if (accel) v = v + half[a];
                     st->x[3 * i + a] = y;
                     st->v[3 * i + a] = v;
                 }
             }
         }
+        if (bad) return -1;
     }
     /* bodies: first half kick, drift, rotor */
     for (int r = 0; r < s->n_rep; ++r) {
@@ -748,7 +772,10 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
         if (tr && tr->shift) memcpy(tr->shift + 3 * r, S, sizeof S);
         const int64_t ns_r = s->solv_off[r + 1] - s->solv_off[r];
 
-        /* a3 + a4: site positions from the pose, thermalisation (Eq. 7) */
+        /* a3 + a4: site positions from the pose, thermalisation (Eq. 7); the
+         * bodies are independent */
+        int berr = 0;
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 4) reduction(min : berr)
         for (int64_t i = s->body_off[r]; i < s->body_off[r + 1]; ++i) {
             int sh = s->body_shape[i];
             body_props bp = shape_props(s, sh);
@@ -757,7 +784,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
             space_inertia(s, sh, Q, I);
             double V[3], om[3];
             for (int a = 0; a < 3; ++a) V[a] = st->P[3 * i + a] / bp.M;
-            if (solve3(I, st->Lm + 3 * i, om)) { status = -2; goto done; }
+            if (solve3(I, st->Lm + 3 * i, om)) { berr = -2; continue; }
             double mvt[3] = { 0, 0, 0 }, Lt[3] = { 0, 0, 0 };
             int64_t nsite = s->site_off[sh + 1] - s->site_off[sh];
             double *vt = (double *)malloc(3 * nsite * sizeof(double));
@@ -779,13 +806,13 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                         float t2 = Qf[a][2] * bf[2];
                         float dd = (t0 + t1) + t2;
                         float y = f32(st->R[3 * i + a]) + dd;
-                        if (wrap_f(&y, (float)L[a])) { status = -1; free(vt); goto done; }
+                        if (wrap_f(&y, (float)L[a])) { berr = -1; goto body_done; }
                         rr[a] = y;
                     }
                 } else {
                     for (int a = 0; a < 3; ++a) {
                         double y = st->R[3 * i + a] + d[a];
-                        if (wrap_d(&y, (double)L[a])) { status = -1; free(vt); goto done; }
+                        if (wrap_d(&y, (double)L[a])) { berr = -1; goto body_done; }
                         rr[a] = y;
                     }
                 }
@@ -806,7 +833,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
             double Vt[3] = { 0, 0, 0 }, omt[3] = { 0, 0, 0 };
             if (!s->naive_transfer) {
                 for (int a = 0; a < 3; ++a) Vt[a] = mvt[a] / bp.M;
-                if (solve3(I, Lt, omt)) { status = -2; free(vt); goto done; }
+                if (solve3(I, Lt, omt)) { berr = -2; goto body_done; }
             }
             for (int64_t j = 0; j < nsite; ++j) {
                 int64_t g = site_base[i] + j;
@@ -817,26 +844,64 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
                     sv[3 * g + a] = p32 ? (double)f32(vj) : vj;
                 }
             }
+        body_done:
             free(vt);
         }
+        if (berr) { status = berr; goto done; }
 
         /* a5: bin the solvent */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
         for (int64_t i = s->solv_off[r]; i < s->solv_off[r + 1]; ++i)
             cell_of[i] = cbase[r] + local_cell(st->x + 3 * i, S, L);
     }
 
     /* a5: counting sort into the canonical order (solvent, then sites) */
-    for (int64_t k = 0; k < Ns + Nsite; ++k) start[cell_of[k] + 1]++;
-    for (int64_t c = 0; c < Ctot; ++c) start[c + 1] += start[c];
-    {
+    if (g_threads == 1) {
+        for (int64_t k = 0; k < Ns + Nsite; ++k) start[cell_of[k] + 1]++;
+        for (int64_t c = 0; c < Ctot; ++c) start[c + 1] += start[c];
         int64_t *fill = (int64_t *)malloc((Ctot + 1) * sizeof(int64_t));
         memcpy(fill, start, (Ctot + 1) * sizeof(int64_t));
         for (int64_t k = 0; k < Ns + Nsite; ++k) order[fill[cell_of[k]]++] = k;
         free(fill);
+    } else {
+        /* the same stable sort on several threads: thread t counts and then
+         * places the members of its contiguous chunk of ids, after the members
+         * of the same cell from the chunks before it */
+        const int T = g_threads;
+        const int64_t NT = Ns + Nsite;
+        int64_t *cnt = (int64_t *)calloc((size_t)T * (Ctot + 1), sizeof(int64_t));
+#pragma omp parallel num_threads(T)
+        {
+#ifdef _OPENMP
+            const int t = omp_get_thread_num();
+#else
+            const int t = 0;
+#endif
+            int64_t *my = cnt + (size_t)t * (Ctot + 1);
+            for (int64_t k = NT * t / T; k < NT * (t + 1) / T; ++k) my[cell_of[k]]++;
+#pragma omp barrier
+#pragma omp single
+            {
+                int64_t run = 0;
+                for (int64_t c = 0; c < Ctot; ++c) {
+                    start[c] = run;
+                    for (int u = 0; u < T; ++u) {
+                        const int64_t n = cnt[(size_t)u * (Ctot + 1) + c];
+                        cnt[(size_t)u * (Ctot + 1) + c] = run;
+                        run += n;
+                    }
+                }
+                start[Ctot] = run;
+            }
+            for (int64_t k = NT * t / T; k < NT * (t + 1) / T; ++k) order[my[cell_of[k]]++] = k;
+        }
+        free(cnt);
     }
 
-    /* a6 + a7: per-cell sums, collision parameters and new velocities */
+    /* a6 + a7: per-cell sums, collision parameters and new velocities (each
+     * cell reads only its own members and writes only their new velocities) */
     for (int r = 0; r < s->n_rep; ++r) {
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1024)
         for (int64_t c = cbase[r]; c < cbase[r + 1]; ++c) {
             uint32_t lc = (uint32_t)(c - cbase[r]);
             int64_t n = start[c + 1] - start[c];
@@ -992,6 +1057,7 @@ int orc_collide(const orc_sys *s, orc_state *st, orc_trace *tr)
     }
 
     /* solvent takes its new velocities */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t i = 0; i < Ns; ++i)
         for (int a = 0; a < 3; ++a)
             st->v[3 * i + a] = p32 ? (double)f32(vnew[3 * i + a]) : vnew[3 * i + a];
