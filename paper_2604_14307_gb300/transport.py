@@ -138,3 +138,106 @@ def velocity_autocorrelation(X: np.ndarray, n_lags: int) -> np.ndarray:
     for k in range(min(n_lags, n)):
         out[:, k] = np.mean(np.sum(X[k:] * X[: n - k], axis=-1), axis=0)
     return out
+
+
+# --------------------------------------------------------------------------
+# Hydrodynamic theory of the single-sphere autocorrelations (Sec. III.A,
+# Eqs. 10-13): a neutrally buoyant no-slip sphere of radius R in a compressible
+# solvent of density rho0, shear viscosity eta0, bulk viscosity eta_b and
+# isothermal speed of sound c0.  Reading of Eq. 11: the variable s in the
+# definition of zeta is the Laplace variable s = -i omega of the transform.
+# --------------------------------------------------------------------------
+def friction_translational(omega, R: float, eta0: float, rho0: float, c0: float, eta_b: float):
+    """Frequency-dependent translational friction gamma_T(omega) (Eq. 11) with
+    x = R sqrt(-i omega / nu0), zeta = s R / sqrt(c0^2 - i omega (4 eta0/3 +
+    eta_b) / rho0), s = -i omega (principal square roots, Re >= 0).  For
+    c0 -> infinity it is the incompressible 6 pi eta0 R (1 + x + x^2/9)."""
+    w = np.asarray(omega, dtype=np.complex128)
+    s = -1j * w
+    nu = eta0 / rho0
+    x = R * np.sqrt(s / nu)
+    zeta = s * R / np.sqrt(c0 * c0 + s * (4.0 * eta0 / 3.0 + eta_b) / rho0)
+    num = (1.0 + x) * (9.0 - 9.0j * zeta - 2.0 * zeta * zeta) + x * x * (1.0 - 1j * zeta)
+    den = 2.0 * x * x * (1.0 - 1j * zeta) - (1.0 + x) * zeta * zeta - x * x * zeta * zeta
+    with np.errstate(invalid="ignore", divide="ignore"):
+        g = (4.0 * np.pi / 3.0) * eta0 * R * x * x * num / den
+    # omega = 0: the Stokes limit (x, zeta -> 0)
+    return np.where(w == 0, 6.0 * np.pi * eta0 * R + 0j, g)
+
+
+def friction_rotational(s, R: float, eta0: float, rho0: float):
+    """Frequency-dependent rotational friction gamma_R(s) in the Laplace variable
+    s (Eq. 13): 8 pi eta0 R^3 [1 + (R^2 s / nu0) / (3 (1 + sqrt(R^2 s / nu0)))]."""
+    s = np.asarray(s, dtype=np.complex128)
+    y = R * R * s / (eta0 / rho0)
+    return 8.0 * np.pi * eta0 * R ** 3 * (1.0 + y / (3.0 * (1.0 + np.sqrt(y))))
+
+
+def vacf_translational_theory(t, kT: float, R: float, eta0: float, rho0: float, c0: float, eta_b: float,
+                              M: float = None, d_omega: float = 1e-3, omega_max: float = 1e3) -> np.ndarray:
+    """C_T(t) = <V(0).V(t)> of Eq. 10 for t > 0, by the trapezoid rule on
+    [-omega_max, omega_max] with step d_omega (the paper's 1e-3 and 1e3).  M is
+    the sphere's mass, M_S = 4 pi R^3 rho0 / 3 (neutrally buoyant) by default.
+    The integrand is the transform of a real function, so the integral is
+    twice the real part over omega >= 0."""
+    if M is None:
+        M = 4.0 * np.pi * R ** 3 * rho0 / 3.0
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    w = np.arange(0.0, omega_max + 0.5 * d_omega, d_omega)
+    F = 1.0 / (friction_translational(w, R, eta0, rho0, c0, eta_b) - 1j * w * M)
+    wt = np.full(w.size, d_omega)
+    wt[0] = wt[-1] = 0.5 * d_omega            # trapezoid weights (the omega = 0 point counts once)
+    out = np.empty(t.size)
+    Fr, Fi = (F.real * wt), (F.imag * wt)
+    for i0 in range(0, t.size, 16):            # e^{-i w t} F: Re = Fr cos + Fi sin
+        tt = t[i0:i0 + 16, None]
+        ph = w[None, :] * tt
+        out[i0:i0 + 16] = (np.cos(ph) @ Fr + np.sin(ph) @ Fi)
+    return 3.0 * kT / np.pi * out
+
+
+def talbot_inverse(F, t, n: int = 32) -> np.ndarray:
+    """Inverse Laplace transform f(t) of F(s) for t > 0 by the fixed Talbot
+    contour method (Talbot 1979; Abate and Valko 2004): with r = 2n/(5t),
+    theta_k = k pi / n and s(theta) = r theta (cot theta + i),
+    f(t) = (r/n) [F(r) e^{r t}/2 + sum_k Re(e^{t s_k} F(s_k) (1 + i sigma_k))],
+    sigma(theta) = theta + (theta cot theta - 1) cot theta.  F is called on
+    complex arrays; its singularities must lie on or left of the negative real
+    axis (a branch cut there is allowed)."""
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    k = np.arange(1, n)
+    th = k * np.pi / n
+    cot = 1.0 / np.tan(th)
+    sig = th + (th * cot - 1.0) * cot
+    out = np.empty(t.size)
+    for i, ti in enumerate(t):
+        r = 2.0 * n / (5.0 * ti)
+        sk = r * th * (cot + 1j)
+        term = np.real(np.exp(ti * sk) * F(sk) * (1.0 + 1j * sig))
+        out[i] = (r / n) * (0.5 * np.real(F(np.array([r + 0j]))[0]) * np.exp(r * ti) + term.sum())
+    return out
+
+
+def vacf_rotational_theory(t, kT: float, R: float, eta0: float, rho0: float, I: float = None,
+                           n: int = 32) -> np.ndarray:
+    """C_R(t) = <omega(0).omega(t)> of Eq. 12: (3 kT / I) times the inverse
+    Laplace transform of 1/(s + gamma_R(s)/I) (Eq. 13), for t > 0, by the fixed
+    Talbot method.  I is the sphere's moment of inertia, I_S = 2 M_S R^2 / 5 of a
+    solid neutrally buoyant sphere by default."""
+    if I is None:
+        I = 2.0 * (4.0 * np.pi * R ** 3 * rho0 / 3.0) * R * R / 5.0
+    return 3.0 * kT / I * talbot_inverse(lambda s: 1.0 / (s + friction_rotational(s, R, eta0, rho0) / I), t, n)
+
+
+def vacf_translational_tail(t, kT: float, eta0: float, rho0: float):
+    """Long-time tail of C_T: kT / (4 rho0 (pi nu0 t)^{3/2}), from the sqrt(s)
+    term of the low-frequency friction 6 pi eta0 R (1 + R sqrt(s/nu0) + ...)."""
+    nu = eta0 / rho0
+    return kT / (4.0 * rho0 * (np.pi * nu * np.asarray(t, dtype=np.float64)) ** 1.5)
+
+
+def vacf_rotational_tail(t, kT: float, eta0: float, rho0: float):
+    """Long-time tail of C_R: 3 pi kT / (32 rho0 (pi nu0 t)^{5/2}), from the
+    s^{3/2} term of gamma_R(s) at small s (Eq. 13)."""
+    nu = eta0 / rho0
+    return 3.0 * np.pi * kT / (32.0 * rho0 * (np.pi * nu * np.asarray(t, dtype=np.float64)) ** 2.5)
