@@ -370,9 +370,6 @@ typedef struct {
                                ring, CTA barriers); 2: warp-specialised - a producer warp drives
                                a three-stage ring of bulk copies for the computing warps;
                                3: a three-stage ring per warp (tile = particles per warp tile);
-                               4: form 3 with each warp adding the cell words of its 128 particles
-                               into a shared-memory table of the 16 x 2 x 2 shifted cells they fall
-                               in before one global addition per cell (P32; identical sums);
                                0: direct 128-bit loads; -1 keeps the current value */
 } mpcd_tuning;
 int mpcd_get_tuning(const mpcd_ctx *ctx, mpcd_tuning *out);

@@ -284,92 +284,6 @@ __device__ __forceinline__ void bin4(const StepArgs &a, const Real (&x)[4], cons
     }
 }
 
-// Warp-private accumulation of the P32 cell words (launch form 4).  A warp's
-// 128 consecutive particles in cell-sorted storage lie in about 13 plain cells
-// of one row of the box; under a grid shift below one cell they fall into at
-// most two shifted cells per plain cell along y and z, i.e. into a window of
-// AGG_X x 2 x 2 shifted cells anchored at the warp's smallest shifted cell
-// coordinates.  Runs inside the window are added to a table of that window in
-// shared memory; runs outside it (a warp that crosses a row or the periodic
-// edge) go to the global words directly.  After the chunk, each used entry is
-// added once to the global words and cleared.  Integer addition keeps the sums
-// identical to the direct form.
-constexpr int AGG_X = 16, AGG_N = AGG_X * 4;
-__device__ __forceinline__ int agg_pack(int cx, int cy, int cz) { return cx | (cy << 11) | (cz << 22); }
-
-// all 32 lanes of the warp call it (warp-wide minimum and table flush)
-template <int RULE, bool COLLIDE>
-__device__ __forceinline__ void bin4_agg(const StepArgs &a, const float (&x)[4], const float (&y)[4],
-                                         const float (&z)[4], const float (&vx)[4], const float (&vy)[4],
-                                         const float (&vz)[4], const uint32_t (&tg)[4], int nv, const int32_t *S,
-                                         int L0, int L1, int L2, int base, const DevReplica &rr, int64_t step,
-                                         float m, float sc, long long *sums, int64_t C, long long *tab)
-{
-    constexpr int NW = Words32<RULE>::n;
-    int pk[4];
-    float xi[4][3];
-    int mx = 0x7FFFFFFF, my = 0x7FFFFFFF, mz = 0x7FFFFFFF;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int cx = cell_axis(x[j], S[0], L0), cy = cell_axis(y[j], S[1], L1), cz = cell_axis(z[j], S[2], L2);
-        pk[j] = agg_pack(cx, cy, cz);
-        if (j < nv) { mx = min(mx, cx); my = min(my, cy); mz = min(mz, cz); }
-        xi[j][0] = xi[j][1] = xi[j][2] = 0.0f;
-        if (RULE == 1) {   // for every slot, so that the four draws interleave; runs past nv are dropped
-            normals3(draw(rr, step + (COLLIDE ? 1 : 0), tg[j], TAG_AT, 0u), xi[j]);
-            xi[j][0] *= sc; xi[j][1] *= sc; xi[j][2] *= sc;
-        }
-    }
-    mx = __reduce_min_sync(0xffffffffu, mx);
-    my = __reduce_min_sync(0xffffffffu, my);
-    mz = __reduce_min_sync(0xffffffffu, mz);
-    auto flush = [&](int p, const long long (&acc)[MAX_WORDS32]) {
-        const int dx = (p & 2047) - mx, dy = ((p >> 11) & 2047) - my, dz = (p >> 22) - mz;
-        if (dx < AGG_X && dy < 2 && dz < 2) {
-            const int e = dx + AGG_X * (dy + 2 * dz);
-#pragma unroll
-            for (int k = 0; k < NW; ++k)
-                atomicAdd(reinterpret_cast<unsigned long long *>(tab + k * AGG_N + e), (unsigned long long)acc[k]);
-        } else {
-            const int64_t c = base + (p & 2047) + L0 * (((p >> 11) & 2047) + L1 * (p >> 22));
-#pragma unroll
-            for (int k = 0; k < NW; ++k) red_add(sums + k * C + c, acc[k]);
-        }
-    };
-    long long acc[MAX_WORDS32];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        long long w[MAX_WORDS32];
-        record_terms<RULE>(m, vx[j], vy[j], vz[j], xi[j], false, w);
-        if (j > 0 && j < nv && pk[j] == pk[j - 1]) {
-#pragma unroll
-            for (int k = 0; k < NW; ++k) acc[k] += w[k];
-        } else {
-            if (j > 0 && j - 1 < nv) flush(pk[j - 1], acc);
-#pragma unroll
-            for (int k = 0; k < NW; ++k) acc[k] = w[k];
-        }
-    }
-    if (nv == 4) flush(pk[3], acc);
-    __syncwarp();
-    // each lane takes two window entries: add the used ones to the global words
-#pragma unroll
-    for (int h = 0; h < AGG_N / 32; ++h) {
-        const int e = (threadIdx.x & 31) + 32 * h;
-        const long long w0 = tab[e];
-        if (w0 != 0) {   // a used entry: its w0 holds the solvent count 2^48 n_s and |sum p_x| < 2^47
-            const int dx = e % AGG_X, dy = (e / AGG_X) & 1, dz = e / (2 * AGG_X);
-            const int64_t c = base + (mx + dx) + L0 * ((my + dy) + L1 * (mz + dz));
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                red_add(sums + k * C + c, tab[k * AGG_N + e]);
-                tab[k * AGG_N + e] = 0;
-            }
-        }
-    }
-    __syncwarp();
-}
-
 // --------------------------------------------------------------- the pass
 template <typename Real, int RULE, int FLAGS>
 __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
@@ -965,7 +879,7 @@ template <typename Real, int RULE> struct WtRegs {
     static constexpr int n = sizeof(Real) == 4 && RULE == 0 ? 80 : 128;
 };
 
-template <typename Real, int RULE, int FLAGS, bool AGG>
+template <typename Real, int RULE, int FLAGS>
 __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, int cap)
 {
     constexpr bool COLLIDE = FLAGS & SOLV_COLLIDE;
@@ -993,14 +907,6 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
     if (lane == 0) {
         for (int q = 0; q < WT_STAGES; ++q) mbar_init(&full[warp][q], 1);
         mbar_fence_init();
-    }
-    // launch form 4: the warp's window table of the cell words, after the rings
-    constexpr bool USE_AGG = AGG && sizeof(Real) == 4 && (FLAGS & SOLV_BIN);
-    long long *tab = nullptr;
-    if constexpr (USE_AGG) {
-        tab = reinterpret_cast<long long *>(smem + (size_t)nwarps * WT_STAGES * SB) +
-              (size_t)warp * AGG_N * Words32<RULE>::n;
-        for (int e = lane; e < AGG_N * Words32<RULE>::n; e += 32) tab[e] = 0;
     }
     __syncwarp();
 
@@ -1150,12 +1056,8 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
                         }
                     }
             }
-            if constexpr (USE_AGG)
-                bin4_agg<RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step, m, sc,
-                                        sums, C, tab);
-            else if (BIN)
-                bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step, m, sc,
-                                          sums, C);
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+                                                m, sc, sums, C);
             if (nv > 0) {
                 if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
                 if (COLLIDE || (STREAM && a.accel)) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
@@ -1194,14 +1096,13 @@ static void smem_opt_in(const void *func, size_t bytes)
         have = bytes;
 }
 
-template <typename Real, int RULE, int FLAGS, bool AGG = false>
+template <typename Real, int RULE, int FLAGS>
 static void launch_wt(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
     const int warps = cfg.block / 32;
-    const size_t bytes = (size_t)warps * WT_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap) +
-                         (AGG ? solvent_agg_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.block) : 0);
-    smem_opt_in((const void *)k_solvent_wt<Real, RULE, FLAGS, AGG>, bytes);
-    k_solvent_wt<Real, RULE, FLAGS, AGG><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
+    const size_t bytes = (size_t)warps * WT_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
+    smem_opt_in((const void *)k_solvent_wt<Real, RULE, FLAGS>, bytes);
+    k_solvent_wt<Real, RULE, FLAGS><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
 }
 
 template <typename Real, int RULE, int FLAGS>
@@ -1223,19 +1124,6 @@ static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 template <typename Real, int RULE>
 static void dispatch_flags(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s)
 {
-    if (cfg.staged == 4) {
-        switch (flags) {
-        case SOLV_STREAM: launch_wt<Real, RULE, SOLV_STREAM, true>(a, cfg, s); break;
-        case SOLV_BIN: launch_wt<Real, RULE, SOLV_BIN, true>(a, cfg, s); break;
-        case SOLV_COLLIDE: launch_wt<Real, RULE, SOLV_COLLIDE, true>(a, cfg, s); break;
-        case SOLV_STREAM | SOLV_BIN: launch_wt<Real, RULE, SOLV_STREAM | SOLV_BIN, true>(a, cfg, s); break;
-        case SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN:
-            launch_wt<Real, RULE, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN, true>(a, cfg, s);
-            break;
-        default: break;
-        }
-        return;
-    }
     if (cfg.staged == 3) {
         switch (flags) {
         case SOLV_STREAM: launch_wt<Real, RULE, SOLV_STREAM>(a, cfg, s); break;
@@ -1305,12 +1193,6 @@ size_t solvent_stage_bytes(int precision, int rule, int cap)
 {
     if (precision == 1) return rule == 0 ? stage_bytes<float, 0>(cap) : stage_bytes<float, 1>(cap);
     return rule == 0 ? stage_bytes<double, 0>(cap) : stage_bytes<double, 1>(cap);
-}
-
-size_t solvent_agg_bytes(int precision, int rule, int block)
-{
-    if (precision != 1) return 0;
-    return (size_t)(block / 32) * AGG_N * (rule == 0 ? Words32<0>::n : Words32<1>::n) * sizeof(long long);
 }
 
 size_t solvent_smem_bytes(int precision, int rule, int cap, int)

@@ -363,15 +363,13 @@ size_t ring_bytes(const mpcd_ctx *c, int mode, int tile, int block)
 {
     const size_t stage = solvent_stage_bytes(c->prm.precision, c->prm.rule, tile);
     if (mode == 3) return (size_t)(block / 32) * 3 * stage;   // one three-stage ring per warp
-    if (mode == 4)   // the same rings and each warp's window table of the cell words
-        return (size_t)(block / 32) * 3 * stage + solvent_agg_bytes(c->prm.precision, c->prm.rule, block);
     return (mode == 2 ? 3 : 2) * stage;
 }
 
 bool staged_fits(const mpcd_ctx *c, int tile, int mode, int block)
 {
-    if ((mode == 3 || mode == 4) && (block > 512 || block % 32)) return false;
-    const size_t lim = (mode >= 3 ? 220 : 200) * 1024;
+    if (mode == 3 && (block > 512 || block % 32)) return false;
+    const size_t lim = (mode == 3 ? 220 : 200) * 1024;
     return ring_bytes(c, mode, tile, block) <= lim;
 }
 
@@ -921,13 +919,10 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     if (cudaMemset(c->d_bpos_build, 0, std::max<int64_t>(1, c->B) * sizeof(float4)) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_nl_dirty, 0xFF, sizeof(int)) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (cudaMemset(c->d_err, 0, 8) != cudaSuccess) st = MPCD_ERR_CUDA;
-    // default launch form: a ring per warp of 128-particle tiles (with the
-    // warp's window table of the cell words in the P32 form), else the
+    // default launch form: a ring per warp of 128-particle tiles, else the
     // warp-specialised pass with the largest tile whose ring fits in shared
     // memory (the FP64 form), else direct loads
-    if (p.precision == MPCD_P32 && staged_fits(c, 128, 4, 512)) {
-        c->tune = mpcd_tuning{512, 128, 1, c->tune.sort_period, 4};
-    } else if (staged_fits(c, 128, 3, 512)) {
+    if (staged_fits(c, 128, 3, 512)) {
         c->tune = mpcd_tuning{512, 128, 1, c->tune.sort_period, 3};
     } else {
         c->tune = mpcd_tuning{512, 2048, 1, c->tune.sort_period, 0};
@@ -1527,7 +1522,7 @@ int mpcd_set_tuning(mpcd_ctx *c, const mpcd_tuning *t)
     }
     if (t->ctas_per_sm > 0) c->tune.ctas_per_sm = std::min(t->ctas_per_sm, 32);
     if (t->sort_period > 0) c->tune.sort_period = t->sort_period;
-    if (t->staged >= 0) c->tune.staged = std::min(t->staged, 4);
+    if (t->staged >= 0) c->tune.staged = std::min(t->staged, 3);
     CK(c, cudaSetDevice(c->device));
     build_tiles(c);
     int e = upload_tiles(c);
@@ -1589,11 +1584,10 @@ int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
         for (int tl : {1024, 2048})
             for (int ct : {1, 2})
                 if (staged_fits(c, tl, 2, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 2});
-    for (int mode : {3, 4})
-        for (int bl : {256, 384, 512})
-            for (int tl : {128, 256})
-                for (int ct : {1, 2, 3})
-                    if (staged_fits(c, tl, mode, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, mode});
+    for (int bl : {256, 384, 512})
+        for (int tl : {128, 256})
+            for (int ct : {1, 2, 3})
+                if (staged_fits(c, tl, 3, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 3});
     for (int bl : {256, 512})
         for (int ct : {2, 4})
             cand.push_back(mpcd_tuning{bl, 8192, ct, c->tune.sort_period, 0});

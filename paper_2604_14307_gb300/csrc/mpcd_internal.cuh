@@ -327,7 +327,6 @@ struct LaunchCfg {
 void launch_solvent(const StepArgs &a, int flags, LaunchCfg cfg, cudaStream_t s);
 void launch_params(const StepArgs &a, int grid, cudaStream_t s);
 size_t solvent_stage_bytes(int precision, int rule, int cap);
-size_t solvent_agg_bytes(int precision, int rule, int block);   // window tables of launch form 4
 size_t solvent_smem_bytes(int precision, int rule, int cap, int block);  // dynamic smem of the staged pass
 void launch_aos_to_soa(const StepArgs &a, const void *xaos, const void *vaos, cudaStream_t s);
 void launch_soa_to_aos(const StepArgs &a, void *xaos, void *vaos, const int64_t *out_off,
