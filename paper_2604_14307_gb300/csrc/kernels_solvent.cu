@@ -875,8 +875,11 @@ constexpr int WT_STAGES = 3, WT_MAX_WARPS = 16;
 // loop).  The AT form draws two Philox normals per particle and is latency-
 // bound on their rounds: it gains more from registers (ILP) than from the
 // overlap (L=200: 2.40 ms with 128, 2.69 with 112, 3.01 with 96).
+#ifndef MPCD_WT_SRD_REGS
+#define MPCD_WT_SRD_REGS 80
+#endif
 template <typename Real, int RULE> struct WtRegs {
-    static constexpr int n = sizeof(Real) == 4 && RULE == 0 ? 80 : 128;
+    static constexpr int n = sizeof(Real) == 4 && RULE == 0 ? MPCD_WT_SRD_REGS : 128;
 };
 
 template <typename Real, int RULE, int FLAGS>
