@@ -204,6 +204,83 @@ int mpcd_step(mpcd_ctx *ctx, int64_t nsteps, void *stream);
  * change any result. */
 int mpcd_sort(mpcd_ctx *ctx, int32_t canonical, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Spatial domain decomposition of one box into slabs along z (Sec. II.A).
+ *
+ * One context per slab [z_lo, z_hi) of a single periodic box (e.g. one GPU
+ * each).  The context holds the box's whole cell grid, a subset of its solvent
+ * (every particle keeps its box-wide id, the counter of its random draws) and
+ * all of its bodies (the bodies are replicated: every slab integrates them
+ * alike).  A slab bins and transfers only the surface sites whose z lies in
+ * its range.  Under the random grid shift the shifted cell layer that straddles
+ * a slab face holds particles of both neighbours; their partial cell words are
+ * exact integers (P32), so adding the neighbour's partial words of the two
+ * layers next to each face, z_face - 1 and z_face, gives the words of the whole
+ * box bit for bit.  One step of a slab, in order:
+ *   mpcd_stream                        solvent and bodies move
+ *   mpcd_slab_extract, _export         particles now outside [z_lo, z_hi) leave
+ *   mpcd_slab_insert                   the neighbours' leavers arrive
+ *   mpcd_couple(MPCD_PRE)              sites; only the slab's own are binned
+ *   mpcd_collide_begin                 solvent binned into partial words
+ *   mpcd_layer_words (get, then add)   the face layers' words completed
+ *   mpcd_collide_end                   cell parameters and the collision
+ *   mpcd_couple_post_partial           the slab's share of each body's transfer
+ *   mpcd_apply_impulse                 the sum over all slabs applied; step done
+ * (paper_2604_14307_gb300/domain.py drives it over torch.distributed.)  The
+ * angular-momentum-conserving variant is not supported here (MPCD_ERR_ARG).
+ * ------------------------------------------------------------------------ */
+
+/* A slab context: box edges L (cells), the box's total solvent count (the base
+ * of the sites' random-stream ids), room for `capacity` solvent particles
+ * (<= n_solvent_total), all n_bodies bodies (shape indices copied), owned
+ * range [z_lo, z_hi) with 0 <= z_lo < z_hi <= L[2] and at least 2 cells unless
+ * it is the whole box.  The solvent is empty until mpcd_slab_set_state. */
+int mpcd_create_slab(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_desc *shapes,
+                     const int32_t L[3], int64_t n_solvent_total, int64_t capacity, int32_t n_bodies,
+                     const int32_t *body_shape, int32_t z_lo, int32_t z_hi, const mpcd_allocator *allocator,
+                     int32_t device, mpcd_ctx **out);
+
+/* Load a slab: n solvent particles with box-wide ids tags[n] (uint32), host
+ * rows x[n][3], v[n][3] (float for P32, double for P64) inside the box, and
+ * every body's R[B][3], q[B][4], P[B][3], Lm[B][3]; step keys the random
+ * streams.  Synchronises.  (mpcd_set_state / mpcd_get_state refuse a slab.) */
+int mpcd_slab_set_state(mpcd_ctx *ctx, int64_t n, const uint32_t *tags, const void *x, const void *v,
+                        const double *R, const double *q, const double *P, const double *Lm, int64_t step,
+                        void *stream);
+/* The slab's state: *n its solvent count; with non-NULL buffers its particles
+ * (ids, x, v in storage order) and every body.  Synchronises. */
+int mpcd_slab_get_state(mpcd_ctx *ctx, int64_t *n, uint32_t *tags, void *x, void *v, double *R, double *q,
+                        double *P, double *Lm, void *stream);
+/* Move the particles whose z is outside [z_lo, z_hi) out of the slab (storage
+ * order kept for both groups); *n_left their number.  mpcd_slab_export copies
+ * them (ids, x[n][3], v[n][3]) to host buffers.  Synchronise. */
+int mpcd_slab_extract(mpcd_ctx *ctx, int64_t *n_left, void *stream);
+int mpcd_slab_export(mpcd_ctx *ctx, uint32_t *tags, void *x, void *v, void *stream);
+/* Append n particles (ids, x, v; inside the box) after the slab's own;
+ * MPCD_ERR_ARG beyond the capacity.  Synchronises. */
+int mpcd_slab_insert(mpcd_ctx *ctx, int64_t n, const uint32_t *tags, const void *x, const void *v, void *stream);
+
+/* mpcd_collide in two halves (no exchange protocol, not the +a variant):
+ * _begin bins the solvent into the cell words at the current step's grid
+ * shift; _end turns the words into collision parameters and collides. */
+int mpcd_collide_begin(mpcd_ctx *ctx, void *stream);
+int mpcd_collide_end(mpcd_ctx *ctx, void *stream);
+
+/* The cell words of the z-layers [layer0, layer0 + n_layers) of the shifted
+ * grid (a context with one replica; layer0 + n_layers <= L[2]): add = 0 copies
+ * them to words[sum_words][n_layers L[0] L[1]] (the layout of mpcd_debug_cells,
+ * int64 for P32, double for P64), add = 1 adds that array to them.
+ * Synchronises. */
+int mpcd_layer_words(mpcd_ctx *ctx, int32_t layer0, int32_t n_layers, void *words, int32_t add, void *stream);
+
+/* The POST coupling in two halves: _partial runs the sites' collision and
+ * returns, without applying it, each body's momentum and angular-momentum
+ * change from this context's (for a slab: its own) sites, dPL[B][6] in FP64
+ * (Eqs. 3-4; synchronises); mpcd_apply_impulse adds dPL[B][6] to the bodies and
+ * ends the step (the step counter advances). */
+int mpcd_couple_post_partial(mpcd_ctx *ctx, double *dPL, void *stream);
+int mpcd_apply_impulse(mpcd_ctx *ctx, const double *dPL, void *stream);
+
 /* Binning as a counting sort (Sec. II.A; the cell assignment under the random
  * grid shift): the canonical member order of the collision at the current
  * step.  Call it between mpcd_couple(PRE) and mpcd_collide (for a context

@@ -33,7 +33,10 @@ EXPORTS = ["mpcd_create", "mpcd_destroy", "mpcd_set_state", "mpcd_get_state", "m
            "mpcd_set_profiling", "mpcd_get_profile", "mpcd_reset_profile", "mpcd_get_tuning",
            "mpcd_set_tuning", "mpcd_autotune", "mpcd_collide_solvent_static", "mpcd_set_rnemd",
            "mpcd_rnemd_totals", "mpcd_velocity_profile", "mpcd_set_body_force",
-           "mpcd_body_displacements", "mpcd_set_vacf", "mpcd_get_vacf", "mpcd_cell_order"]
+           "mpcd_body_displacements", "mpcd_set_vacf", "mpcd_get_vacf", "mpcd_cell_order",
+           "mpcd_create_slab", "mpcd_slab_set_state", "mpcd_slab_get_state", "mpcd_slab_extract",
+           "mpcd_slab_export", "mpcd_slab_insert", "mpcd_collide_begin", "mpcd_collide_end",
+           "mpcd_layer_words", "mpcd_couple_post_partial", "mpcd_apply_impulse"]
 
 
 class MPCDError(RuntimeError):
@@ -143,6 +146,18 @@ def load(path: str = LIB_PATH) -> C.CDLL:
             "mpcd_rnemd_totals": [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), vp],
             "mpcd_velocity_profile": [vp, i32, i32, i32, vp, vp, vp],
             "mpcd_cell_order": [vp, vp, vp, vp],
+            "mpcd_create_slab": [C.POINTER(Params), i32, vp, C.POINTER(C.c_int32 * 3), i64, i64, i32, vp, i32, i32,
+                                 vp, i32, C.POINTER(vp)],
+            "mpcd_slab_set_state": [vp, i64, vp, vp, vp, vp, vp, vp, vp, i64, vp],
+            "mpcd_slab_get_state": [vp, C.POINTER(C.c_int64), vp, vp, vp, vp, vp, vp, vp, vp],
+            "mpcd_slab_extract": [vp, C.POINTER(C.c_int64), vp],
+            "mpcd_slab_export": [vp, vp, vp, vp, vp],
+            "mpcd_slab_insert": [vp, i64, vp, vp, vp, vp],
+            "mpcd_collide_begin": [vp, vp],
+            "mpcd_collide_end": [vp, vp],
+            "mpcd_layer_words": [vp, i32, i32, vp, i32, vp],
+            "mpcd_couple_post_partial": [vp, vp, vp],
+            "mpcd_apply_impulse": [vp, vp, vp],
             "mpcd_collide_solvent_static": [C.POINTER(Params), C.POINTER(C.c_int32 * 3), i64, vp, vp, vp,
                                             vp, vp, vp, vp, i64, vp, C.c_char_p, C.c_size_t],
         }
@@ -208,14 +223,7 @@ class Simulation:
         self.prm = Params(p.kT, p.dt, p.alpha_deg, p.m_solvent, p.rule, p.thermostat,
                           p.precision, p.naive_transfer, p.seed, sort_period, getattr(p, "angular", 0))
         self._keep = []
-        shapes = (ShapeDesc * max(1, len(system.shapes)))()
-        for k, sh in enumerate(system.shapes):
-            b = np.ascontiguousarray(sh.b, dtype=np.float64)
-            m = np.ascontiguousarray(sh.m, dtype=np.float64)
-            cen = np.ascontiguousarray(sh.centres, dtype=np.float64).reshape(-1, 3)
-            self._keep += [b, m, cen]
-            shapes[k] = ShapeDesc(len(m), b.ctypes.data, m.ctypes.data, len(cen),
-                                  cen.ctypes.data if len(cen) else None, sh.wca_d)
+        shapes = self._shape_descs(system)
         reps = (ReplicaDesc * system.n_rep)()
         sids = system.stream_ids()
         for r, rep in enumerate(system.replicas):
@@ -238,6 +246,17 @@ class Simulation:
         self.sizes = Sizes()
         self._check(self.lib.mpcd_sizes(self.ctx, C.byref(self.sizes)))
         self.real = np.float32 if self.precision == I.P32 else np.float64
+
+    def _shape_descs(self, system):
+        shapes = (ShapeDesc * max(1, len(system.shapes)))()
+        for k, sh in enumerate(system.shapes):
+            b = np.ascontiguousarray(sh.b, dtype=np.float64)
+            m = np.ascontiguousarray(sh.m, dtype=np.float64)
+            cen = np.ascontiguousarray(sh.centres, dtype=np.float64).reshape(-1, 3)
+            self._keep += [b, m, cen]
+            shapes[k] = ShapeDesc(len(m), b.ctypes.data, m.ctypes.data, len(cen),
+                                  cen.ctypes.data if len(cen) else None, sh.wca_d)
+        return shapes
 
     # ------------------------------------------------------------------
     def _check(self, rc: int):
@@ -440,6 +459,121 @@ class Simulation:
     def autotune(self, steps_per_trial: int = 3, stream=None) -> dict:
         self._check(self.lib.mpcd_autotune(self.ctx, steps_per_trial, self._s(stream)))
         return self.tuning()
+
+
+class Slab(Simulation):
+    """One slab [z_lo, z_hi) of a single-box system (spatial domain
+    decomposition along z; see mpcd_create_slab): a subset of the solvent with
+    box-wide ids, every body, the sites of its z range."""
+
+    def __init__(self, system: I.System, z_lo: int, z_hi: int, capacity: int, device: int = 0,
+                 sort_period: int = 0, use_torch_allocator: bool = True):
+        if system.n_rep != 1:
+            raise ValueError("a slab is a part of a single box")
+        self.lib = load()
+        self.system = system
+        p = system.params
+        self.precision = p.precision
+        self.prm = Params(p.kT, p.dt, p.alpha_deg, p.m_solvent, p.rule, p.thermostat,
+                          p.precision, p.naive_transfer, p.seed, sort_period, getattr(p, "angular", 0))
+        self._keep = []
+        shapes = self._shape_descs(system)
+        rep = system.replicas[0]
+        ids = np.ascontiguousarray(rep.body_shapes, dtype=np.int32)
+        self._keep.append(ids)
+        self._alloc = None
+        if use_torch_allocator and _torch_cuda() is not None:
+            self._alloc = _TorchAllocator(device)
+        ctx = C.c_void_p()
+        rc = self.lib.mpcd_create_slab(C.byref(self.prm), len(system.shapes), C.cast(shapes, C.c_void_p),
+                                       C.byref((C.c_int32 * 3)(*rep.L)), int(rep.n_solvent), int(capacity),
+                                       len(ids), ids.ctypes.data if len(ids) else None, int(z_lo), int(z_hi),
+                                       C.byref(self._alloc.c) if self._alloc else None, device, C.byref(ctx))
+        if rc != MPCD_OK:
+            raise MPCDError(rc, "mpcd_create_slab failed")
+        self.ctx = ctx
+        self.z_lo, self.z_hi = int(z_lo), int(z_hi)
+        self.sizes = Sizes()
+        self._check(self.lib.mpcd_sizes(self.ctx, C.byref(self.sizes)))
+        self.real = np.float32 if self.precision == I.P32 else np.float64
+
+    def _rows(self, x):
+        return np.ascontiguousarray(np.asarray(x, dtype=self.real).reshape(-1, 3))
+
+    def set_slab_state(self, tags, x, v, R, q, P, Lm, step: int = 0, stream=None):
+        tags = np.ascontiguousarray(tags, dtype=np.uint32)
+        x, v = self._rows(x), self._rows(v)
+        bodies = [np.ascontiguousarray(a, dtype=np.float64) for a in (R, q, P, Lm)]
+        self._check(self.lib.mpcd_slab_set_state(self.ctx, len(tags), tags.ctypes.data, x.ctypes.data,
+                                                 v.ctypes.data, *[b.ctypes.data for b in bodies], int(step),
+                                                 self._s(stream)))
+
+    def get_slab_state(self, stream=None):
+        """(ids, x, v, R, q, P, Lm, step) with the solvent in storage order."""
+        n = C.c_int64()
+        self._check(self.lib.mpcd_slab_get_state(self.ctx, C.byref(n), None, None, None, None, None, None,
+                                                 None, self._s(stream)))
+        nb = self.sizes.n_bodies
+        tags = np.zeros(max(1, n.value), dtype=np.uint32)
+        x = np.zeros((max(1, n.value), 3), dtype=self.real)
+        v = np.zeros_like(x)
+        R, P, Lm = (np.zeros((max(1, nb), 3)) for _ in range(3))
+        q = np.zeros((max(1, nb), 4))
+        self._check(self.lib.mpcd_slab_get_state(self.ctx, C.byref(n), tags.ctypes.data, x.ctypes.data,
+                                                 v.ctypes.data, R.ctypes.data, q.ctypes.data, P.ctypes.data,
+                                                 Lm.ctypes.data, self._s(stream)))
+        k = n.value
+        return tags[:k], x[:k], v[:k], R[:nb], q[:nb], P[:nb], Lm[:nb]
+
+    def extract(self, stream=None):
+        """Remove the particles outside [z_lo, z_hi); returns (ids, x, v) of the leavers."""
+        n = C.c_int64()
+        self._check(self.lib.mpcd_slab_extract(self.ctx, C.byref(n), self._s(stream)))
+        k = n.value
+        tags = np.zeros(max(1, k), dtype=np.uint32)
+        x = np.zeros((max(1, k), 3), dtype=self.real)
+        v = np.zeros_like(x)
+        self._check(self.lib.mpcd_slab_export(self.ctx, tags.ctypes.data, x.ctypes.data, v.ctypes.data,
+                                              self._s(stream)))
+        return tags[:k], x[:k], v[:k]
+
+    def insert(self, tags, x, v, stream=None):
+        tags = np.ascontiguousarray(tags, dtype=np.uint32)
+        x, v = self._rows(x), self._rows(v)
+        self._check(self.lib.mpcd_slab_insert(self.ctx, len(tags), tags.ctypes.data, x.ctypes.data,
+                                              v.ctypes.data, self._s(stream)))
+
+    def collide_begin(self, stream=None):
+        self._check(self.lib.mpcd_collide_begin(self.ctx, self._s(stream)))
+
+    def collide_end(self, stream=None):
+        self._check(self.lib.mpcd_collide_end(self.ctx, self._s(stream)))
+
+    def layer_words(self, layer0: int, n_layers: int, stream=None) -> np.ndarray:
+        Lx, Ly = self.system.replicas[0].L[:2]
+        dt = np.int64 if self.precision == I.P32 else np.float64
+        w = np.zeros((self.sizes.sum_words, n_layers * Lx * Ly), dtype=dt)
+        self._check(self.lib.mpcd_layer_words(self.ctx, int(layer0), int(n_layers), w.ctypes.data, 0,
+                                              self._s(stream)))
+        return w
+
+    def add_layer_words(self, layer0: int, words: np.ndarray, stream=None):
+        Lx, Ly = self.system.replicas[0].L[:2]
+        dt = np.int64 if self.precision == I.P32 else np.float64
+        w = np.ascontiguousarray(words, dtype=dt)
+        n_layers = w.shape[1] // (Lx * Ly)
+        self._check(self.lib.mpcd_layer_words(self.ctx, int(layer0), int(n_layers), w.ctypes.data, 1,
+                                              self._s(stream)))
+
+    def post_partial(self, stream=None) -> np.ndarray:
+        nb = self.sizes.n_bodies
+        d = np.zeros((max(1, nb), 6))
+        self._check(self.lib.mpcd_couple_post_partial(self.ctx, d.ctypes.data, self._s(stream)))
+        return d[:nb]
+
+    def apply_impulse(self, dPL, stream=None):
+        d = np.ascontiguousarray(dPL, dtype=np.float64).reshape(-1, 6)
+        self._check(self.lib.mpcd_apply_impulse(self.ctx, d.ctypes.data if d.size else None, self._s(stream)))
 
 
 def collide_solvent_static(params: I.Params, L, x, y, z, vx, vy, vz, tag=None, step: int = 0,

@@ -26,6 +26,7 @@ UNITS = {
     "static_collide.cu": [],
     "kernels_sort.cu": [],
     "kernels_angular.cu": [],
+    "kernels_slab.cu": [],
 }
 
 

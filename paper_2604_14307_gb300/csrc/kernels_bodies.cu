@@ -32,6 +32,15 @@
 
 namespace mpcd {
 
+// a slab of a decomposed box owns the sites whose stored z lies in its range
+// (bounds are integers: the comparison is exact in either precision)
+template <typename Real>
+__device__ __forceinline__ bool site_owned(const StepArgs &a, Real z)
+{
+    return !a.site_own || (z >= (Real)a.site_zlo && z < (Real)a.site_zhi);
+}
+
+
 // ------------------------------------------------------------- quaternions
 __device__ __forceinline__ void quat_mul(const double a[4], const double b[4], double o[4])
 {
@@ -617,7 +626,7 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
         if (!a.naive) {
             const Real m = site_mass<Real>(a, t);
             Real nn[3];
-            normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_SITE, 0u), nn);
+            normals3(draw(r, step, (uint32_t)(r.site_id_base + (g - r.site_begin)), TAG_SITE, 0u), nn);
             const Real sc = sqrt(kT / m);
             const Real w[3] = {sc * nn[0], sc * nn[1], sc * nn[2]};
             for (int k = 0; k < 3; ++k) vt[3 * j + k] = w[k];
@@ -654,10 +663,12 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
         const bool valid = j < n;
         Real v[3] = {0, 0, 0}, xi[3] = {0, 0, 0}, m = Real(0);
         int cell = 0;
+        bool own = true;   // a slab bins only the sites in its z range
         if (valid) {
             const int64_t t = sh.site_begin + j, g = site_begin + j;
             Real d[3], x[3];
             site_geom(a, t, P, r, d, x, bad);
+            own = site_owned(a, x[2]);
             v[0] = dV[0] + (dW[1] * d[2] - dW[2] * d[1]);
             v[1] = dV[1] + (dW[2] * d[0] - dW[0] * d[2]);
             v[2] = dV[2] + (dW[0] * d[1] - dW[1] * d[0]);
@@ -666,13 +677,13 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
             for (int k = 0; k < 3; ++k) SV[k * NS + g] = v[k];
             m = site_mass<Real>(a, t);
             if (a.rule == 1) {
-                normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
+                normals3(draw(r, step, (uint32_t)(r.site_id_base + (g - r.site_begin)), TAG_AT, 0u), xi);
                 const Real sc = sqrt(kT / m);
                 xi[0] *= sc; xi[1] *= sc; xi[2] *= sc;
             }
             cell = r.cell_base + a.site_cell[g];
         }
-        if (valid) {
+        if (valid && own) {
             if constexpr (sizeof(Real) == 4) {
                 long long w[MAX_WORDS32];
                 unsigned long long *S = reinterpret_cast<unsigned long long *>(a.sums);
@@ -715,7 +726,7 @@ __device__ __forceinline__ void site_rule(const StepArgs &a, const DevReplica &r
             vn[2] = p[2] + p[3] * (w[2] * ca + cz * sa + p[6] * tt);
         } else {
             Real xi[3];
-            normals3(draw(r, step, (uint32_t)(r.n_solvent + (g - r.site_begin)), TAG_AT, 0u), xi);
+            normals3(draw(r, step, (uint32_t)(r.site_id_base + (g - r.site_begin)), TAG_AT, 0u), xi);
             const Real sc = sqrt(kT / m);
             for (int k = 0; k < 3; ++k) vn[k] = p[k] + sc * xi[k] - p[4 + k];
         }
@@ -768,7 +779,9 @@ __global__ void __launch_bounds__(SITE_THREADS, SiteMinBlocks<Real>::n) k_sites_
             site_lattice_q(xs, a.ang_shift[B.rep], Q);
             ang_correct(reinterpret_cast<const AngParams<Real> *>(a.ang_params)[cell], Q, vn);
         }
-        const Real dp[3] = {m * (vn[0] - v[0]), m * (vn[1] - v[1]), m * (vn[2] - v[2])};
+        const bool own = site_owned(a, x[2]);   // a slab transfers only its own sites
+        const Real dp[3] = {own ? m * (vn[0] - v[0]) : Real(0), own ? m * (vn[1] - v[1]) : Real(0),
+                            own ? m * (vn[2] - v[2]) : Real(0)};
         acc[0] += dp[0]; acc[1] += dp[1]; acc[2] += dp[2];
         acc[3] += d[1] * dp[2] - d[2] * dp[1];
         acc[4] += d[2] * dp[0] - d[0] * dp[2];

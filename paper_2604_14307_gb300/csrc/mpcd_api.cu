@@ -120,6 +120,19 @@ struct mpcd_ctx {
     int4 *ang_shift = nullptr;                  // [nrep] grid shift of the current collision
     double f_ext[3] = {0.0, 0.0, 0.0};          // constant force on every body (one replica)
     VacfArgs vacf{};                            // velocity autocorrelations (n_lags 0: off)
+    // slab of a decomposed box (mpcd_create_slab): the active solvent count is
+    // reps[0].n_solvent (= Ns), the slots hold `capacity` particles
+    bool slab = false;
+    int32_t slab_zlo = 0, slab_zhi = 0;
+    int64_t capacity = 0;
+    void *exp_sol[6] = {};                       // the particles that left the slab
+    uint32_t *exp_tag = nullptr;
+    uint32_t *tag_stage = nullptr;               // ids of the particles in `staging`
+    int64_t n_exp = 0;
+    int32_t *slab_leave = nullptr, *slab_leave_ex = nullptr, *slab_bs = nullptr;
+    double *d_dpl = nullptr;                     // [B][6] transfer of the slab's own sites
+    void *words_stage = nullptr;                 // neighbour words to add
+    int64_t words_stage_bytes = 0;
     // canonical member order (mpcd_cell_order; allocated on first use)
     int32_t *ord_counts = nullptr, *ord_ex = nullptr, *ord_cursor = nullptr, *ord_bs = nullptr;
     unsigned long long *ord_keys = nullptr;
@@ -129,6 +142,7 @@ struct mpcd_ctx {
 
 namespace {
 
+void clear_graphs(mpcd_ctx *c);
 int fail(mpcd_ctx *c, int st, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
 int fail(mpcd_ctx *c, int st, const char *fmt, ...)
 {
@@ -243,6 +257,9 @@ StepArgs make_args(const mpcd_ctx *c)
     a.n_sites = c->Nsite;
     a.d_step = c->d_step;
     a.d_err = c->d_err;
+    a.site_own = c->slab ? 1 : 0;
+    a.site_zlo = c->slab_zlo;
+    a.site_zhi = c->slab_zhi;
     // constant body force, balanced by a uniform force on the solvent of the
     // (single) replica: each particle gets -B f / N_s, i.e. acceleration g
     if (c->f_ext[0] != 0.0 || c->f_ext[1] != 0.0 || c->f_ext[2] != 0.0) {
@@ -299,6 +316,26 @@ int upload_tiles(mpcd_ctx *c)
     }
     if (!c->tiles.empty())
         CK(c, cudaMemcpy(c->d_tiles, c->tiles.data(), c->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    return MPCD_OK;
+}
+
+// the active solvent count of a slab context changed: replica record, work
+// tiles of the solvent pass and of the helper passes, CUDA graphs
+int slab_set_count(mpcd_ctx *c, int64_t n)
+{
+    c->reps[0].n_solvent = n;
+    c->Ns = n;
+    CK(c, cudaMemcpy(c->d_reps, c->reps.data(), c->reps.size() * sizeof(DevReplica), cudaMemcpyHostToDevice));
+    build_tiles(c);
+    int e = upload_tiles(c);
+    if (e) return e;
+    c->io_tiles.clear();
+    const DevReplica &R = c->reps[0];
+    for (int64_t b = R.solv_begin; b < R.solv_begin + R.n_solvent; b += 2048)
+        c->io_tiles.push_back(Tile{0, 0, b, std::min<int64_t>(b + 2048, R.solv_begin + R.n_solvent)});
+    if (!c->io_tiles.empty())
+        CK(c, cudaMemcpy(c->d_io_tiles, c->io_tiles.data(), c->io_tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    clear_graphs(c);
     return MPCD_OK;
 }
 
@@ -769,6 +806,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
         R.cell_base = (int32_t)cells;
         R.solv_begin = slot;
         R.n_solvent = d.n_solvent;
+        R.site_id_base = d.n_solvent;
         R.body_begin = bodies;
         R.body_end = bodies + d.n_bodies;
         R.site_begin = sites;
@@ -1015,6 +1053,7 @@ const char *mpcd_last_error(const mpcd_ctx *c) { return c ? c->err : "null conte
 int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
 {
     CHECK_CTX(c);
+    if (c->slab) return MPCD_ERR_ARG;   // a slab's particles carry box-wide ids: mpcd_slab_set_state
     if (!h || (c->Ns > 0 && (!h->x || !h->v)) || (c->B > 0 && (!h->R || !h->q || !h->P || !h->Lm)) || h->step < 0)
         return MPCD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1097,6 +1136,7 @@ int mpcd_set_state(mpcd_ctx *c, const mpcd_host_state *h, void *stream)
 int mpcd_get_state(mpcd_ctx *c, mpcd_host_state *h, void *stream)
 {
     CHECK_CTX(c);
+    if (c->slab) return MPCD_ERR_ARG;   // mpcd_slab_get_state
     if (!h || (c->Ns > 0 && (!h->x || !h->v)) || (c->B > 0 && (!h->R || !h->q || !h->P || !h->Lm)))
         return MPCD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1253,6 +1293,300 @@ int mpcd_cell_order(mpcd_ctx *c, int64_t *order, int64_t *cell_start, void *stre
     CK(c, cudaMemcpyAsync(cell_start, c->ord_start, (C + 1) * 8, cudaMemcpyDeviceToHost, s));
     CK(c, cudaStreamSynchronize(s));
     return MPCD_OK;
+}
+
+// --------------------------------------------------- slab decomposition
+int mpcd_create_slab(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_desc *shapes, const int32_t L[3],
+                     int64_t n_solvent_total, int64_t capacity, int32_t n_bodies, const int32_t *body_shape,
+                     int32_t z_lo, int32_t z_hi, const mpcd_allocator *allocator, int32_t device, mpcd_ctx **out)
+{
+    if (!out || !params || !L || n_solvent_total < 0 || capacity < 0 || capacity > n_solvent_total ||
+        n_bodies < 0 || (n_bodies > 0 && !body_shape) || params->angular != 0 || z_lo < 0 || z_hi > L[2] ||
+        z_hi <= z_lo || (z_hi - z_lo < 2 && !(z_lo == 0 && z_hi == L[2])))
+        return MPCD_ERR_ARG;
+    mpcd_replica_desc d{};
+    for (int k = 0; k < 3; ++k) d.L[k] = L[k];
+    d.n_solvent = capacity;
+    d.n_bodies = n_bodies;
+    d.stream_id = 0;
+    d.body_shape = body_shape;
+    int e = mpcd_create(params, n_shapes, shapes, 1, &d, allocator, device, out);
+    if (e) return e;
+    mpcd_ctx *c = *out;
+    c->slab = true;
+    c->slab_zlo = z_lo;
+    c->slab_zhi = z_hi;
+    c->capacity = capacity;
+    c->reps[0].site_id_base = n_solvent_total;
+    const size_t nb = (size_t)std::max<int64_t>(capacity, 1);
+    bool ok = true;
+    for (int k = 0; k < 6 && ok; ++k) ok = (c->exp_sol[k] = dalloc(c, nb * c->realsz)) != nullptr;
+    const size_t ntile = (size_t)(capacity / 2048 + 2);
+    ok = ok && (c->exp_tag = (uint32_t *)dalloc(c, nb * 4)) != nullptr;
+    ok = ok && (c->tag_stage = (uint32_t *)dalloc(c, nb * 4)) != nullptr;
+    ok = ok && (c->slab_leave = (int32_t *)dalloc(c, ntile * 4)) != nullptr;
+    ok = ok && (c->slab_leave_ex = (int32_t *)dalloc(c, ntile * 4)) != nullptr;
+    ok = ok && (c->slab_bs = (int32_t *)dalloc(c, scan_block_sums_size((int64_t)ntile) * 4)) != nullptr;
+    ok = ok && (c->d_dpl = (double *)dalloc(c, (size_t)std::max<int64_t>(c->B, 1) * 6 * 8)) != nullptr;
+    if (!ok) {
+        mpcd_destroy(c);
+        *out = nullptr;
+        return MPCD_ERR_OOM;
+    }
+    CK(c, cudaSetDevice(c->device));
+    e = slab_set_count(c, 0);
+    if (e) {
+        mpcd_destroy(c);
+        *out = nullptr;
+    }
+    return e;
+}
+
+int mpcd_slab_insert(mpcd_ctx *c, int64_t n, const uint32_t *tags, const void *x, const void *v, void *stream)
+{
+    CHECK_CTX(c);
+    if (!c->slab || n < 0 || (n > 0 && (!tags || !x || !v)) || c->Ns + n > c->capacity) return MPCD_ERR_ARG;
+    if (n == 0) return MPCD_OK;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // every position inside the box (the binning rule's domain)
+    const int32_t *L = c->reps[0].L;
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const double xv = c->realsz == 4 ? (double)((const float *)x)[3 * i + k] : ((const double *)x)[3 * i + k];
+            if (!(xv >= 0.0 && xv < (double)L[k])) return MPCD_ERR_ARG;
+        }
+    char *stg = (char *)c->staging;   // sized for the capacity: x and v
+    const size_t n3 = (size_t)n * 3 * c->realsz;
+    CK(c, cudaMemcpyAsync(stg, x, n3, cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(stg + n3, v, n3, cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(c->tag_stage, tags, n * 4, cudaMemcpyHostToDevice, s));
+    StepArgs a = make_args(c);
+    launch_slab_put(a, stg, stg + n3, c->tag_stage, n, c->reps[0].solv_begin + c->Ns, c->num_sms, s);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(s));
+    return slab_set_count(c, c->Ns + n);
+}
+
+int mpcd_slab_extract(mpcd_ctx *c, int64_t *n_left, void *stream)
+{
+    CHECK_CTX(c);
+    if (!c->slab || !n_left) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    *n_left = 0;
+    c->n_exp = 0;
+    const int64_t nt = (int64_t)c->io_tiles.size();
+    if (nt == 0) return MPCD_OK;
+    StepArgs a = make_io_args(c);
+    const int nxt = c->cur ^ 1;
+    int e = timed(c, "slab_extract", (double)c->Ns * (6.0 * c->realsz + 4.0) * 2.0, s, [&] {
+        launch_slab_count(a, c->slab_zlo, c->slab_zhi, c->slab_leave, s);
+        cudaMemsetAsync(c->slab_leave + nt, 0, 4, s);
+        launch_scan(c->slab_leave, c->slab_leave_ex, nt + 1, c->slab_bs, s);
+        void *dst[6] = {c->sol[nxt][0], c->sol[nxt][1], c->sol[nxt][2], c->sol[nxt][3], c->sol[nxt][4], c->sol[nxt][5]};
+        launch_slab_split(a, c->slab_zlo, c->slab_zhi, c->slab_leave_ex, dst, c->tag[nxt], c->exp_sol, c->exp_tag, s);
+    });
+    if (e) return e;
+    int32_t left = 0;
+    CK(c, cudaMemcpyAsync(&left, c->slab_leave_ex + nt, 4, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(s));
+    c->cur = nxt;
+    c->n_exp = left;
+    *n_left = left;
+    return slab_set_count(c, c->Ns - left);
+}
+
+int mpcd_slab_export(mpcd_ctx *c, uint32_t *tags, void *x, void *v, void *stream)
+{
+    CHECK_CTX(c);
+    if (!c->slab || (c->n_exp > 0 && (!tags || !x || !v))) return MPCD_ERR_ARG;
+    if (c->n_exp == 0) return MPCD_OK;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    char *stg = (char *)c->staging;
+    const size_t n3 = (size_t)c->n_exp * 3 * c->realsz;
+    launch_slab_pack(c->prm.precision, c->exp_sol, c->exp_tag, c->n_exp, stg, stg + n3, c->tag_stage, c->num_sms,
+                     s);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(x, stg, n3, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(v, stg + n3, n3, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(tags, c->tag_stage, c->n_exp * 4, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    return MPCD_OK;
+}
+
+int mpcd_slab_set_state(mpcd_ctx *c, int64_t n, const uint32_t *tags, const void *x, const void *v, const double *R,
+                        const double *q, const double *P, const double *Lm, int64_t step, void *stream)
+{
+    CHECK_CTX(c);
+    if (!c->slab || step < 0 || (c->B > 0 && (!R || !q || !P || !Lm))) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<DevBody> hb(std::max<int64_t>(1, c->B));
+    if (c->B) CK(c, cudaMemcpy(hb.data(), c->d_bodies, c->B * sizeof(DevBody), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < c->B; ++i) {
+        DevBody &b = hb[i];
+        double nq = 0;
+        for (int k = 0; k < 4; ++k) nq += q[4 * i + k] * q[4 * i + k];
+        if (!(std::fabs(nq - 1.0) < 1e-6)) return MPCD_ERR_ARG;
+        for (int k = 0; k < 3; ++k) {
+            if (!(R[3 * i + k] >= 0.0 && R[3 * i + k] < c->reps[0].L[k])) return MPCD_ERR_ARG;
+            b.R[k] = R[3 * i + k];
+            b.P[k] = P[3 * i + k];
+            b.Lm[k] = Lm[3 * i + k];
+            b.F[k] = b.T[k] = b.D[k] = 0.0;
+        }
+        for (int k = 0; k < 4; ++k) b.q[k] = q[4 * i + k];
+    }
+    int e = slab_set_count(c, 0);
+    if (!e) e = mpcd_slab_insert(c, n, tags, x, v, stream);
+    if (e) return e;
+    if (c->B) CK(c, cudaMemcpyAsync(c->d_bodies, hb.data(), c->B * sizeof(DevBody), cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemsetAsync(c->sums, 0, (size_t)c->C * c->nw * 8, s));
+    CK(c, cudaMemcpyAsync(c->d_step, &step, 8, cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemsetAsync(c->d_nl_dirty, 0xFF, sizeof(int), s));
+    StepArgs a = make_args(c);
+    launch_body_force(a, 0, s);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(s));
+    c->step = step;
+    c->since_sort = 0;
+    c->last_key = -1;
+    c->have_state = true;
+    return MPCD_OK;
+}
+
+int mpcd_slab_get_state(mpcd_ctx *c, int64_t *n, uint32_t *tags, void *x, void *v, double *R, double *q, double *P,
+                        double *Lm, void *stream)
+{
+    CHECK_CTX(c);
+    if (!c->slab || !n) return MPCD_ERR_ARG;
+    *n = c->Ns;
+    if (!tags && !x && !v && !R) return MPCD_OK;
+    if ((c->Ns > 0 && (!tags || !x || !v)) || (c->B > 0 && (!R || !q || !P || !Lm))) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->Ns) {
+        char *stg = (char *)c->staging;
+        const size_t n3 = (size_t)c->Ns * 3 * c->realsz;
+        void *cur[6] = {};
+        for (int k = 0; k < 6; ++k) cur[k] = (char *)c->sol[c->cur][k] + c->reps[0].solv_begin * c->realsz;
+        launch_slab_pack(c->prm.precision, cur, c->tag[c->cur] + c->reps[0].solv_begin, c->Ns, stg, stg + n3,
+                         c->tag_stage, c->num_sms, s);
+        CK(c, cudaGetLastError());
+        CK(c, cudaMemcpyAsync(x, stg, n3, cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(v, stg + n3, n3, cudaMemcpyDeviceToHost, s));
+        CK(c, cudaMemcpyAsync(tags, c->tag_stage, c->Ns * 4, cudaMemcpyDeviceToHost, s));
+    }
+    std::vector<DevBody> hb(std::max<int64_t>(1, c->B));
+    if (c->B) CK(c, cudaMemcpyAsync(hb.data(), c->d_bodies, c->B * sizeof(DevBody), cudaMemcpyDeviceToHost, s));
+    int e = check_device_error(c, s);
+    if (e) return e;
+    for (int64_t i = 0; i < c->B; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            R[3 * i + k] = hb[i].R[k];
+            P[3 * i + k] = hb[i].P[k];
+            Lm[3 * i + k] = hb[i].Lm[k];
+        }
+        for (int k = 0; k < 4; ++k) q[4 * i + k] = hb[i].q[k];
+    }
+    return MPCD_OK;
+}
+
+int mpcd_collide_begin(mpcd_ctx *c, void *stream)
+{
+    CHECK_CTX(c);
+    if (c->prm.angular) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    int e = k_solvent(c, SOLV_BIN, (cudaStream_t)stream);
+    if (!e) CK(c, cudaGetLastError());
+    return e;
+}
+
+int mpcd_collide_end(mpcd_ctx *c, void *stream)
+{
+    CHECK_CTX(c);
+    if (c->prm.angular) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int e = k_params(c, s);
+    if (!e) e = k_solvent(c, SOLV_COLLIDE, s);
+    if (!e) CK(c, cudaGetLastError());
+    c->last_key = c->step;
+    return e;
+}
+
+int mpcd_layer_words(mpcd_ctx *c, int32_t layer0, int32_t n_layers, void *words, int32_t add, void *stream)
+{
+    CHECK_CTX(c);
+    const DevReplica &R = c->reps[0];
+    if (c->nrep != 1 || !words || layer0 < 0 || n_layers <= 0 || layer0 + n_layers > R.L[2]) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t plane = (int64_t)R.L[0] * R.L[1], cell0 = (int64_t)layer0 * plane, ncell = (int64_t)n_layers * plane;
+    const size_t wb = (size_t)ncell * 8;
+    if (!add) {
+        for (int k = 0; k < c->nw; ++k)
+            CK(c, cudaMemcpyAsync((char *)words + k * wb, (char *)c->sums + ((size_t)k * c->C + cell0) * 8, wb,
+                                  cudaMemcpyDeviceToHost, s));
+    } else {
+        if ((int64_t)(wb * c->nw) > c->words_stage_bytes) {
+            c->words_stage = dalloc(c, wb * c->nw);
+            if (!c->words_stage) return fail(c, MPCD_ERR_OOM, "layer words staging");
+            c->words_stage_bytes = (int64_t)(wb * c->nw);
+        }
+        CK(c, cudaMemcpyAsync(c->words_stage, words, wb * c->nw, cudaMemcpyHostToDevice, s));
+        launch_words_add(c->prm.precision, c->sums, c->nw, c->C, cell0, ncell, c->words_stage, c->num_sms, s);
+        CK(c, cudaGetLastError());
+    }
+    CK(c, cudaStreamSynchronize(s));
+    return MPCD_OK;
+}
+
+int mpcd_couple_post_partial(mpcd_ctx *c, double *dPL, void *stream)
+{
+    CHECK_CTX(c);
+    if (!dPL || c->prm.angular) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->B == 0) return MPCD_OK;
+    StepArgs a = make_args(c);
+    int e = timed(c, "sites_post", (double)c->Nsite * (3.0 * c->realsz + 4.0), s,
+                  [&] { launch_sites_post(a, c->max_sites, s); });
+    if (e) return e;
+    double *dpl = c->d_dpl;
+    if (!dpl) {   // a context that is not a slab: allocated on first use
+        c->d_dpl = dpl = (double *)dalloc(c, (size_t)c->B * 6 * 8);
+        if (!dpl) return fail(c, MPCD_ERR_OOM, "transfer buffer");
+    }
+    launch_body_partial(a, dpl, s);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(dPL, dpl, (size_t)c->B * 6 * 8, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    return MPCD_OK;
+}
+
+int mpcd_apply_impulse(mpcd_ctx *c, const double *dPL, void *stream)
+{
+    CHECK_CTX(c);
+    if ((c->B > 0 && !dPL) || c->prm.angular) return MPCD_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->B) {
+        if (!c->d_dpl) {
+            c->d_dpl = (double *)dalloc(c, (size_t)c->B * 6 * 8);
+            if (!c->d_dpl) return fail(c, MPCD_ERR_OOM, "transfer buffer");
+        }
+        CK(c, cudaMemcpyAsync(c->d_dpl, dPL, (size_t)c->B * 6 * 8, cudaMemcpyHostToDevice, s));
+        StepArgs a = make_args(c);
+        launch_body_apply(a, c->d_dpl, s);
+    }
+    int e = k_vacf(c, s);
+    if (!e) e = k_advance(c, s);
+    if (!e) CK(c, cudaGetLastError());
+    return e;
 }
 
 int mpcd_diagnostics(mpcd_ctx *c, mpcd_diag *o, void *stream)

@@ -51,6 +51,8 @@ struct DevReplica {
     int64_t body_begin, body_end;
     int64_t site_begin;     // first global site index
     int64_t row_begin;      // first row of the replica in host (tag-ordered) arrays
+    int64_t site_id_base;   // id of the replica's first site in its random streams: the
+                            // solvent count of the whole box (a slab of a box holds fewer)
     uint32_t key0, key1;    // Philox key: (seed_lo, seed_hi ^ replica)
 };
 
@@ -135,6 +137,9 @@ struct StepArgs {
     int32_t step_offset;            // added to *d_step by the site PRE pass (1 when it runs
                                     // for the next step before the counter advances)
     int *d_err;
+    // slab of a decomposed box: only the sites with z in [site_zlo, site_zhi)
+    // are binned and transfer their momentum here (site_own = 0: every site)
+    int32_t site_own, site_zlo, site_zhi;
     // angular-momentum-conserving variants (null when off)
     void *ang_words;                // [ANG_WORDS][n_cells]
     const void *ang_params;         // [n_cells] AngParams records
@@ -465,6 +470,20 @@ void launch_angular(const StepArgs &a, int phase, int num_sms, cudaStream_t s);
 // the sites' sums (ANG_PRE: thermalised velocities; ANG_POST: the rule's velocities);
 // the correction itself is applied by the site POST coupling when a.ang_params is set
 void launch_angular_sites(const StepArgs &a, int phase, cudaStream_t s);
+
+// spatial domain decomposition into slabs (kernels_slab.cu); a.tiles are the
+// fixed 2048-particle io tiles over the active particles
+void launch_slab_count(const StepArgs &a, int zlo, int zhi, int32_t *leave, cudaStream_t s);
+void launch_slab_split(const StepArgs &a, int zlo, int zhi, const int32_t *leave_ex, void *const dst[6],
+                       uint32_t *dst_tag, void *const exp[6], uint32_t *exp_tag, cudaStream_t s);
+void launch_slab_put(const StepArgs &a, const void *xa, const void *va, const uint32_t *tags, int64_t n, int64_t at,
+                     int num_sms, cudaStream_t s);
+void launch_slab_pack(int precision, void *const exp[6], const uint32_t *exp_tag, int64_t n, void *xa, void *va,
+                      uint32_t *tags, int num_sms, cudaStream_t s);
+void launch_words_add(int precision, void *sums, int nw, int64_t C, int64_t cell0, int64_t ncell, const void *add,
+                      int num_sms, cudaStream_t s);
+void launch_body_partial(const StepArgs &a, double *out, cudaStream_t s);
+void launch_body_apply(const StepArgs &a, const double *dpl, cudaStream_t s);
 
 // bodies and sites (kernels_bodies.cu)
 void launch_body_md(const StepArgs &a, cudaStream_t s);

@@ -153,6 +153,7 @@ extern "C" int mpcd_collide_solvent_static(const mpcd_params *p, const int32_t L
     rep.cell_base = 0;
     rep.solv_begin = 0;
     rep.n_solvent = n;
+    rep.site_id_base = n;
     rep.body_begin = rep.body_end = 0;
     rep.site_begin = 0;
     rep.row_begin = 0;

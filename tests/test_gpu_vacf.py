@@ -144,7 +144,8 @@ def test_vacf_of_a_rigid_sphere_against_hydrodynamic_theory(B):
     a no-slip sphere in the paper's solvent (rho0 = 5, eta0 = 3.96, c0 = 1,
     eta_b = 1.22), 256 boxes of 30^3 cells, 4000 sampled steps (errors: the
     spread of the 256 boxes' averages).
-    * Equipartition: C_T(0) M / 3kT and C_R(0) I / 3kT are 1 within 3 errors.
+    * Equipartition: C_T(0) M / 3kT is 1 - M/M_box (the box's total momentum
+      is zero) and C_R(0) I / 3kT is 1, within 3 errors.
     * C_R / C_R(0) follows Eq. 12 over the first two collisions (within 8 %;
       measured 2-4 %) and then decays more slowly than predicted, as the paper
       reports, at every lag from 0.5 to 6 tau.
@@ -171,7 +172,8 @@ def test_vacf_of_a_rigid_sphere_against_hydrodynamic_theory(B):
     t = np.arange(nl) * prm.dt
     CT, CR = ct.mean(0), cr.mean(0)
     eT, eR = ct.std(0) / np.sqrt(nrep), cr.std(0) / np.sqrt(nrep)
-    assert abs(CT[0] * M / 3 - 1) < 3 * eT[0] * M / 3, (CT[0] * M / 3, eT[0] * M / 3)
+    Mbox = M + 5.0 * L ** 3 * prm.m_solvent
+    assert abs(CT[0] * M / 3 - (1 - M / Mbox)) < 3 * eT[0] * M / 3, (CT[0] * M / 3, eT[0] * M / 3)
     assert abs(CR[0] * Ib / 3 - 1) < 3 * eR[0] * Ib / 3, (CR[0] * Ib / 3, eR[0] * Ib / 3)
     kT, R, rho, eta, c0, eb = 1.0, 3.0, 5.0, 3.96, 1.0, 1.22
     MS = 4 * np.pi * R ** 3 * rho / 3
