@@ -47,6 +47,9 @@ def args_():
     ap.add_argument("--no-p64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--tuning", default="",
+                    help="block,tile,ctas_per_sm,staged of the solvent pass instead of the autotuner "
+                         "(staged: 0 direct, 1 CTA ring, 2 warp-specialised, 3 ring per warp)")
     ap.add_argument("--L", type=int, default=200, help="box edge (tests use smaller boxes)")
     ap.add_argument("--workload", default="suspension",
                     choices=["suspension", "single_sphere_L10", "suspension_L50", "batched_single_sphere",
@@ -413,7 +416,12 @@ def main():
 
     sim = Bd.Simulation(system, device=local)
     sim.set_state(state)
-    tuning = sim.tuning() if a.no_tune else sim.autotune(steps_per_trial=10)
+    if a.tuning:
+        tb, tt, tc, tsg = (int(v) for v in a.tuning.split(","))
+        sim.set_tuning(block=tb, tile=tt, ctas_per_sm=tc, staged=tsg)
+        tuning = sim.tuning()
+    else:
+        tuning = sim.tuning() if a.no_tune else sim.autotune(steps_per_trial=10)
     sim.step(a.warmup)
     # mpcd_step(n) replays a CUDA graph keyed by (n, solvent buffer parity,
     # steps since the last re-sort); a call of n steps counts n - 1 of them

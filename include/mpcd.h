@@ -322,8 +322,9 @@ const char *mpcd_last_error(const mpcd_ctx *ctx);
  *              the momentum words are the exact sums of the stored float32
  *              momenta.  P64: doubles N, M, m v (3), then m v.v (SRD) or m xi
  *              (3) (AT).  The P32 form needs one site mass per context, at most
- *              65535 solvent particles and 65535 sites per cell and
- *              |sum m v_a| < 2^15 per cell (not checked).
+ *              65535 solvent particles and 65535 sites per cell,
+ *              |sum m v_a| < 2^15 per cell, and |m v_a| < 2^14 and
+ *              m |v|^2 < 2^27 per particle (the last three not checked).
  * params:    [n_cells][param_bytes] collision parameters (u, kappa, axis / xibar).
  * site_cell: [n_sites] replica-local cell of every site.
  * site_v:    [n_sites][3] site velocities entering the collision (float/double).
@@ -443,8 +444,8 @@ typedef struct {
     int32_t tile;           /* particles per work tile */
     int32_t ctas_per_sm;    /* persistent CTAs per SM (capped by shared memory) */
     int32_t sort_period;    /* steps between re-sorts */
-    int32_t staged;         /* 1: stage tiles in shared memory with bulk async copies (two-stage
-                               ring, CTA barriers); 2: warp-specialised - a producer warp drives
+    int32_t staged;         /* 1: stage tiles in shared memory with bulk async copies (three-
+                               stage ring, one CTA barrier per tile); 2: warp-specialised - a producer warp drives
                                a three-stage ring of bulk copies for the computing warps;
                                3: a three-stage ring per warp (tile = particles per warp tile);
                                0: direct 128-bit loads; -1 keeps the current value */
@@ -487,7 +488,8 @@ int mpcd_autotune(mpcd_ctx *ctx, int32_t steps_per_trial, void *stream);
  *   msg        optional host buffer of msg_len bytes for an error message
  * Every device array must be 16-byte aligned.  The P32 per-cell limits of
  * mpcd_debug_cells apply (at most 65535 particles and |sum m v_a| < 2^15 per
- * cell); this call does not check them: a cell beyond them gets wrong
+ * cell, |m v_a| < 2^14 and m |v|^2 < 2^27 per particle); this call does not
+ * check them: a cell beyond them gets wrong
  * velocities and no error is reported.
  *
  * Scratch: the cell sums and collision parameters live in one statically

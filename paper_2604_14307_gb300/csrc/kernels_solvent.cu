@@ -17,7 +17,7 @@
 //             optional per-cell order by tag) for memory locality; it changes
 //             no result.
 // The solvent pass has four launch forms that give bit-identical results:
-// direct loads (k_solvent), a CTA-wide two-stage bulk-copy ring
+// direct loads (k_solvent), a CTA-wide three-stage bulk-copy ring
 // (k_solvent_staged), a warp-specialised three-stage ring (k_solvent_ws) and a
 // three-stage ring per warp (k_solvent_wt).  Streaming takes an optional
 // constant force (the balancing force of the sedimentation protocol).
@@ -91,6 +91,31 @@ __device__ __forceinline__ int cell_axis(double x, int S, int L)
     return ((unsigned)c < (unsigned)L) ? c : 0;   // only a non-finite position gets here; it is flagged
 
 }
+// The same rule in float32 without a conversion instruction (the solvent
+// passes).  With S an integer, floor((floor(x 2^20) - S) / 2^20) =
+// floor(x - s) for s = S 2^-20, which float32 holds exactly.  x - s rounded
+// toward -inf has the floor of the exact difference (the rounding is monotone
+// and keeps integers), and floor_magic reads that floor off the mantissa
+// (|x - s| < 2^11 here).
+// For x in [0, L) and |s| <= 1/2 the floor lies in [-1, L]: the top is wrapped
+// by one select and -1 by an unsigned minimum with L - 1, which also keeps a
+// non-finite position's cell inside the box (such a position is flagged).
+__device__ __forceinline__ int cell_axis_f(float x, float s, int L)
+{
+    int c = floor_magic_int(floor_magic(__fsub_rd(x, s)));
+    c = c == L ? 0 : c;
+    return (int)min((unsigned)c, (unsigned)(L - 1));
+}
+// grid shift of one axis in the form the binning of a precision takes
+template <typename Real> struct ShiftT { typedef int32_t type; };
+template <> struct ShiftT<float> { typedef float type; };
+__device__ __forceinline__ int32_t shift_as(int32_t S, int32_t) { return S; }
+__device__ __forceinline__ float shift_as(int32_t S, float)
+{
+    return __fmul_rn(__int2float_rn(S), 9.5367431640625e-07f);   // S 2^-20, exact for |S| <= 2^19
+}
+__device__ __forceinline__ int cell_bin(float x, float s, int L) { return cell_axis_f(x, s, L); }
+__device__ __forceinline__ int cell_bin(double x, int32_t S, int L) { return cell_axis(x, S, L); }
 
 // streaming x + v dt with periodic wrap, unfused (same rounding as the oracle)
 __device__ __forceinline__ float drift(float x, float v, float dt, float L, int &bad)
@@ -231,10 +256,10 @@ __device__ __forceinline__ void red_add(double *p, double v) { atomicAdd(p, v); 
 // Binning of a thread's 4 consecutive particles: cell under the shift S,
 // per-particle fixed-point (P32) or double (P64) terms, runs of equal cells
 // merged in registers, then one atomic per word and run.
-template <typename Real, int RULE, bool COLLIDE, typename W>
+template <typename Real, int RULE, bool COLLIDE, typename W, typename SH>
 __device__ __forceinline__ void bin4(const StepArgs &a, const Real (&x)[4], const Real (&y)[4], const Real (&z)[4],
                                      const Real (&vx)[4], const Real (&vy)[4], const Real (&vz)[4],
-                                     const uint32_t (&tg)[4], int nv, const int32_t *S, int L0, int L1, int L2,
+                                     const uint32_t (&tg)[4], int nv, const SH *S, int L0, int L1, int L2,
                                      int base, const DevReplica &rr, int64_t step, Real m, Real sc, W *sums,
                                      int64_t C)
 {
@@ -242,7 +267,7 @@ __device__ __forceinline__ void bin4(const StepArgs &a, const Real (&x)[4], cons
     Real xi[4][3];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        cc[j] = base + cell_axis(x[j], S[0], L0) + L0 * (cell_axis(y[j], S[1], L1) + L1 * cell_axis(z[j], S[2], L2));
+        cc[j] = base + cell_bin(x[j], S[0], L0) + L0 * (cell_bin(y[j], S[1], L1) + L1 * cell_bin(z[j], S[2], L2));
         xi[j][0] = xi[j][1] = xi[j][2] = Real(0);
         if (RULE == 1) {   // for every slot, so that the four draws interleave; runs past nv are dropped
             normals3(draw(rr, step + (COLLIDE ? 1 : 0), tg[j], TAG_AT, 0u), xi[j]);
@@ -294,6 +319,7 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
     typedef typename SumWord<Real>::type W;
 
     __shared__ int32_t sS[6];
+    __shared__ typename ShiftT<Real>::type sF[6];   // sS in the binning's form
     __shared__ int32_t sL[3];
     __shared__ int32_t sbase;
     __shared__ int64_t sbeg, send;
@@ -323,6 +349,7 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
             skey[1] = r.key1;
             if (COLLIDE) grid_shift(r, step, &sS[0]);
             if (BIN) grid_shift(r, step + (COLLIDE ? 1 : 0), &sS[3]);
+            for (int c = 0; c < 6; ++c) sF[c] = shift_as(sS[c], typename ShiftT<Real>::type());
         }
         __syncthreads();
         const int L0 = sL[0], L1 = sL[1], L2 = sL[2], base = sbase;
@@ -346,8 +373,8 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
             for (int j = 0; j < 4; ++j) {
                 if (j >= nv) break;
                 if (COLLIDE) {
-                    int c = base + cell_axis(x[j], sS[0], L0) +
-                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    int c = base + cell_bin(x[j], sF[0], L0) +
+                            L0 * (cell_bin(y[j], sF[1], L1) + L1 * cell_bin(z[j], sF[2], L2));
                     CellParams<Real> p = get_params<Real>(a.params, c);
                     if (p.kappa >= Real(0)) {
                         if (RULE == 0) {
@@ -377,7 +404,7 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
                     }
                 }
             }
-            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sF + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (STREAM) { st4(X + i, x); st4(Y + i, y); st4(Z + i, z); }
             if (COLLIDE || (STREAM && a.accel)) { st4(VX + i, vx); st4(VY + i, vy); st4(VZ + i, vz); }
@@ -388,11 +415,13 @@ __global__ void __launch_bounds__(512) k_solvent(StepArgs a)
 
 // ------------------------------------------- staged pass (bulk async copies)
 // The same per-particle arithmetic as k_solvent, but each CTA streams its
-// tiles through a two-stage shared-memory ring: thread 0 issues one
+// tiles through a three-stage shared-memory ring: thread 0 issues one
 // cp.async.bulk per SoA array (completion counted on an mbarrier) for tile
-// k+1 while the CTA computes tile k, and writes results back with bulk
+// k+2 while the CTA computes tile k+1 and tile k is written back with bulk
 // stores.  Memory-level parallelism is then set by the copy engine, not by
-// the number of resident warps.  Every mbarrier wait is bounded.
+// the number of resident warps.  One CTA barrier per tile; the tile records,
+// replica fields and grid shifts are read ahead by thread 0 after it, so no
+// serial set-up stands between two tiles.  Every mbarrier wait is bounded.
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -466,14 +495,46 @@ __device__ __forceinline__ void sst4(double *p, const double (&o)[4])
     reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
 }
 
+struct TileMeta {
+    int32_t S[6];     // grid shifts: collision (0..2), binning (3..5)
+    float Sf[6];      // the same as s = S 2^-20 (FP32 form)
+    int32_t L[3];
+    int32_t base;     // first global cell of the replica
+    int32_t n;        // particles in the tile
+    uint32_t key0, key1;
+    int32_t pad;
+    int64_t beg;      // first slot
+};
+
+__device__ __forceinline__ int32_t tile_shift(const TileMeta &m, int c, int32_t) { return m.S[c]; }
+__device__ __forceinline__ float tile_shift(const TileMeta &m, int c, float) { return m.Sf[c]; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+
 template <typename Real, int RULE>
 __host__ __device__ constexpr size_t stage_bytes(int cap)
 {
     return ((size_t)cap * (6 * sizeof(Real) + (RULE == 1 ? 4 : 0)) + 127) & ~(size_t)127;
 }
 
+constexpr int ST_STAGES = 3;
+
+// Register cap of the FP32 SRD form of the staged pass (threads of all its
+// CTAs on an SM times the cap leave the rest to the site/body kernels that run
+// beside it); the other forms take up to 128.
+#ifndef MPCD_ST_SRD_REGS
+#define MPCD_ST_SRD_REGS 96
+#endif
+template <typename Real, int RULE> struct StRegs {
+    static constexpr int n = sizeof(Real) == 4 && RULE == 0 ? MPCD_ST_SRD_REGS : 128;
+};
+
 template <typename Real, int RULE, int FLAGS>
-__global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
+__global__ void __maxnreg__((StRegs<Real, RULE>::n)) k_solvent_staged(StepArgs a, int cap)
 {
     constexpr bool COLLIDE = FLAGS & SOLV_COLLIDE;
     constexpr bool STREAM = FLAGS & SOLV_STREAM;
@@ -481,83 +542,93 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
     typedef typename SumWord<Real>::type W;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int32_t sS[6];
-    __shared__ int32_t sL[3];
-    __shared__ int32_t sbase, scount;
-    __shared__ uint32_t skey[2];
+    __shared__ __align__(8) uint64_t full[ST_STAGES];
+    __shared__ TileMeta meta[ST_STAGES];
+    __shared__ TileMeta rcache;   // fields and grid shifts of the last replica met
+    __shared__ int rcache_rep;
 
     const size_t SB = stage_bytes<Real, RULE>(cap);
     const int64_t step = *a.d_step;
     const Real dt = Consts<Real>::dt(a), m = Consts<Real>::m(a), kT = Consts<Real>::kT(a);
     const Real ca = Consts<Real>::ca(a), sa = Consts<Real>::sa(a);
     const Real sc = sqrt(kT / m);
-    Real *G[6] = {reinterpret_cast<Real *>(a.x), reinterpret_cast<Real *>(a.y), reinterpret_cast<Real *>(a.z),
-                  reinterpret_cast<Real *>(a.vx), reinterpret_cast<Real *>(a.vy), reinterpret_cast<Real *>(a.vz)};
+    auto garr = [&](int c) -> Real * {
+        void *p = c == 0 ? a.x : c == 1 ? a.y : c == 2 ? a.z : c == 3 ? a.vx : c == 4 ? a.vy : a.vz;
+        return reinterpret_cast<Real *>(p);
+    };
     W *sums = reinterpret_cast<W *>(a.sums);
     const int64_t C = a.n_cells;
+    const int K = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     int bad = 0;
 
-    auto issue_load = [&](int tile, int stage) {
-        const Tile tl = a.tiles[tile];
-        const int n4 = (int)((tl.end - tl.begin + 3) & ~(int64_t)3);
+    // thread 0 only: the record of the next tile to issue is loaded one issue
+    // ahead, so that no load of a tile record stands between two tiles
+    int32_t nrep = 0;
+    int64_t nbeg = 0, nend = 0;
+    auto issue = [&](int j) {   // local tile j into stage j % ST_STAGES
+        const int q = j % ST_STAGES;
+        const int rep = nrep;
+        const int64_t tbeg = nbeg, tend = nend;
+        if (j + 1 < K) {
+            const Tile tn = a.tiles[blockIdx.x + (j + 1) * gridDim.x];
+            nrep = tn.rep; nbeg = tn.begin; nend = tn.end;
+        }
+        if (rep != rcache_rep) {
+            const DevReplica cr = a.reps[rep];
+            if (COLLIDE) grid_shift(cr, step, &rcache.S[0]);
+            if (BIN) grid_shift(cr, step + (COLLIDE ? 1 : 0), &rcache.S[3]);
+            for (int c = 0; c < 6; ++c) rcache.Sf[c] = shift_as(rcache.S[c], 0.0f);
+            rcache.L[0] = cr.L[0]; rcache.L[1] = cr.L[1]; rcache.L[2] = cr.L[2];
+            rcache.base = cr.cell_base;
+            rcache.key0 = cr.key0;
+            rcache.key1 = cr.key1;
+            rcache_rep = rep;
+        }
+        TileMeta &mt = meta[q];
+        mt = rcache;
+        mt.n = (int)(tend - tbeg);
+        mt.beg = tbeg;
+        const int n4 = (mt.n + 3) & ~3;
         const uint32_t nb = (uint32_t)(n4 * sizeof(Real));
-        unsigned char *base = smem + stage * SB;
-        mbar_expect_tx(&bar[stage], 6 * nb + (RULE == 1 ? (uint32_t)(n4 * 4) : 0u));
-        for (int k = 0; k < 6; ++k) bulk_load(base + (size_t)k * cap * sizeof(Real), G[k] + tl.begin, nb, &bar[stage]);
-        if (RULE == 1) bulk_load(base + (size_t)6 * cap * sizeof(Real), a.tag + tl.begin, (uint32_t)(n4 * 4), &bar[stage]);
+        unsigned char *base = smem + q * SB;
+        mbar_expect_tx(&full[q], 6 * nb + (RULE == 1 ? (uint32_t)(n4 * 4) : 0u));
+        for (int c = 0; c < 6; ++c) bulk_load(base + (size_t)c * cap * sizeof(Real), garr(c) + tbeg, nb, &full[q]);
+        if (RULE == 1) bulk_load(base + (size_t)6 * cap * sizeof(Real), a.tag + tbeg, (uint32_t)(n4 * 4), &full[q]);
     };
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int q = 0; q < ST_STAGES; ++q) mbar_init(&full[q], 1);
         mbar_fence_init();
+        rcache_rep = -1;
+        if (K > 0) {
+            const Tile t0 = a.tiles[blockIdx.x];
+            nrep = t0.rep; nbeg = t0.begin; nend = t0.end;
+        }
+        for (int j = 0; j < ST_STAGES - 1 && j < K; ++j) issue(j);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < a.n_tiles) issue_load(blockIdx.x, 0);
-    uint32_t phase0 = 0, phase1 = 0;
-    int k = 0;
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++k) {
-        const int st = k & 1;
-        int64_t beg = 0;
-        if (threadIdx.x == 0) {
-            const int tn = t + gridDim.x;
-            if (tn < a.n_tiles) {
-                bulk_wait_read_all();          // stage st^1 was last stored from; reuse it
-                issue_load(tn, st ^ 1);
-            }
-            const Tile tl = a.tiles[t];
-            const DevReplica r = a.reps[tl.rep];
-            sL[0] = r.L[0]; sL[1] = r.L[1]; sL[2] = r.L[2];
-            sbase = r.cell_base;
-            scount = (int)(tl.end - tl.begin);
-            skey[0] = r.key0;
-            skey[1] = r.key1;
-            if (COLLIDE) grid_shift(r, step, &sS[0]);
-            if (BIN) grid_shift(r, step + (COLLIDE ? 1 : 0), &sS[3]);
-        }
-        __syncthreads();
-        const bool got = mbar_wait_bounded(&bar[st], st ? phase1 : phase0);
-        if (!__syncthreads_and(got)) {
-            if (threadIdx.x == 0) {
-                atomicOr(a.d_err, ERR_TIMEOUT);
-                bulk_wait_all();
-                mbar_wait_bounded(&bar[st ^ 1], st ? phase0 : phase1);
-            }
-            return;
-        }
-        if (st) phase1 ^= 1; else phase0 ^= 1;
-        const int L0 = sL[0], L1 = sL[1], L2 = sL[2], base = sbase, n = scount;
+
+    for (int k = 0; k < K; ++k) {
+        const int q = k % ST_STAGES;
+        // a timed-out wait is folded into the barrier at the end of the tile:
+        // the arithmetic on a stage that did not land is memory-safe (every
+        // index it forms is bounded) and its results are discarded
+        const bool got = mbar_wait_bounded(&full[q], (uint32_t)((k / ST_STAGES) & 1));
+        const TileMeta &mt = meta[q];
+        typename ShiftT<Real>::type sF[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sF[c] = tile_shift(mt, c, typename ShiftT<Real>::type());
+        const int L0 = mt.L[0], L1 = mt.L[1], L2 = mt.L[2], base = mt.base, n = mt.n;
         const Real Lx = (Real)L0, Ly = (Real)L1, Lz = (Real)L2;
         DevReplica rr;
-        rr.key0 = skey[0];
-        rr.key1 = skey[1];
+        rr.key0 = mt.key0;
+        rr.key1 = mt.key1;
         Real *S[6];
-        for (int q = 0; q < 6; ++q) S[q] = reinterpret_cast<Real *>(smem + st * SB + (size_t)q * cap * sizeof(Real));
-        const uint32_t *stag = reinterpret_cast<const uint32_t *>(smem + st * SB + (size_t)6 * cap * sizeof(Real));
+        for (int c = 0; c < 6; ++c) S[c] = reinterpret_cast<Real *>(smem + q * SB + (size_t)c * cap * sizeof(Real));
+        const uint32_t *stag = reinterpret_cast<const uint32_t *>(smem + q * SB + (size_t)6 * cap * sizeof(Real));
 
         // uniform trip count: every lane of a warp reaches the warp-wide flush
-        for (int i0 = 0; i0 < n; i0 += 4 * blockDim.x) {
+        for (int i0 = 0; i0 < n && got; i0 += 4 * blockDim.x) {
             const int i = i0 + 4 * threadIdx.x;
             const int nv = max(0, min(4, n - i));
             Real x[4], y[4], z[4], vx[4], vy[4], vz[4];
@@ -578,8 +649,8 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
                 CellParams<Real> p[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    int c = base + cell_axis(x[j], sS[0], L0) +
-                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    int c = base + cell_bin(x[j], sF[0], L0) +
+                            L0 * (cell_bin(y[j], sF[1], L1) + L1 * cell_bin(z[j], sF[2], L2));
                     c = j < nv ? c : base;
                     p[j] = get_params<Real>(a.params, c);
                 }
@@ -593,15 +664,21 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j < nv && p[j].kappa >= Real(0)) {
-                        if (RULE == 0) {
-                            srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
-                        } else {
-                            vx[j] = p[j].ux + sc * nn[j][0] - p[j].ax;
-                            vy[j] = p[j].uy + sc * nn[j][1] - p[j].ay;
-                            vz[j] = p[j].uz + sc * nn[j][2] - p[j].az;
-                        }
+                    // the rule is applied to every slot and kept where it
+                    // applies (no branch): a member of a cell that collides
+                    const bool on = j < nv && p[j].kappa >= Real(0);
+                    Real rx, ry, rz;
+                    if (RULE == 0) {
+                        rx = vx[j]; ry = vy[j]; rz = vz[j];
+                        srd_rotate<Real>(p[j], ca, sa, rx, ry, rz);
+                    } else {
+                        rx = p[j].ux + sc * nn[j][0] - p[j].ax;
+                        ry = p[j].uy + sc * nn[j][1] - p[j].ay;
+                        rz = p[j].uz + sc * nn[j][2] - p[j].az;
                     }
+                    vx[j] = on ? rx : vx[j];
+                    vy[j] = on ? ry : vy[j];
+                    vz[j] = on ? rz : vz[j];
                 }
             }
             if (STREAM) {
@@ -623,24 +700,38 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
                         }
                     }
             }
-            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sF + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (nv > 0) {
                 if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
                 if (COLLIDE || (STREAM && a.accel)) { sst4(S[3] + i, vx); sst4(S[4] + i, vy); sst4(S[5] + i, vz); }
             }
         }
-        fence_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0 && (STREAM || COLLIDE)) {
-            const Tile tl = a.tiles[t];
-            beg = tl.begin;
-            const uint32_t nb = (uint32_t)(((n + 3) & ~3) * sizeof(Real));
-            if (STREAM)
-                for (int q = 0; q < 3; ++q) bulk_store(G[q] + beg, S[q], nb);
-            if (COLLIDE || (STREAM && a.accel))
-                for (int q = 3; q < 6; ++q) bulk_store(G[q] + beg, S[q], nb);
+        fence_async_smem();   // results visible to the bulk stores
+        if (__syncthreads_or(!got)) {
+            if (threadIdx.x == 0) {
+                atomicOr(a.d_err, ERR_TIMEOUT);
+                // let the copies in flight land before the CTA leaves (bounded)
+                bulk_wait_all();
+                for (int j = k; j < K && j < k + ST_STAGES - 1; ++j)
+                    mbar_wait_bounded(&full[j % ST_STAGES], (uint32_t)((j / ST_STAGES) & 1));
+            }
+            return;
+        }
+        if (threadIdx.x == 0) {
+            if (STREAM || COLLIDE) {
+                const uint32_t nb = (uint32_t)(((n + 3) & ~3) * sizeof(Real));
+                const int64_t beg = mt.beg;
+                if (STREAM)
+                    for (int c = 0; c < 3; ++c) bulk_store(garr(c) + beg, S[c], nb);
+                if (COLLIDE || (STREAM && a.accel))
+                    for (int c = 3; c < 6; ++c) bulk_store(garr(c) + beg, S[c], nb);
+            }
             bulk_commit();
+            if (k + ST_STAGES - 1 < K) {
+                bulk_wait_read_1();   // the store of tile k - 1 has read the stage that tile k + 2 takes
+                issue(k + ST_STAGES - 1);
+            }
         }
     }
     if (threadIdx.x == 0) bulk_wait_all();
@@ -658,22 +749,6 @@ __global__ void __launch_bounds__(512) k_solvent_staged(StepArgs a, int cap)
 // store issued from it two tiles earlier has finished reading it.  Every wait
 // is bounded; on a timeout the error word gets ERR_TIMEOUT and the CTA drains.
 constexpr int WS_STAGES = 3;
-
-struct TileMeta {
-    int32_t S[6];     // grid shifts: collision (0..2), binning (3..5)
-    int32_t L[3];
-    int32_t base;     // first global cell of the replica
-    int32_t n;        // particles in the tile
-    uint32_t key0, key1;
-    int32_t pad;
-    int64_t beg;      // first slot
-};
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
-}
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 
 template <typename Real, int RULE, int FLAGS>
 __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
@@ -731,6 +806,7 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
             TileMeta &m = meta[q];
             if (COLLIDE) grid_shift(r, step, &m.S[0]);
             if (BIN) grid_shift(r, step + (COLLIDE ? 1 : 0), &m.S[3]);
+            for (int c = 0; c < 6; ++c) m.Sf[c] = shift_as(m.S[c], 0.0f);
             m.L[0] = r.L[0]; m.L[1] = r.L[1]; m.L[2] = r.L[2];
             m.base = r.cell_base;
             m.n = (int)(tl.end - tl.begin);
@@ -766,9 +842,9 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
             break;
         }
         const TileMeta &mt = meta[q];
-        int32_t sS[6];
+        typename ShiftT<Real>::type sF[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) sS[c] = mt.S[c];
+        for (int c = 0; c < 6; ++c) sF[c] = tile_shift(mt, c, typename ShiftT<Real>::type());
         const int L0 = mt.L[0], L1 = mt.L[1], L2 = mt.L[2], base = mt.base, n = mt.n;
         const Real Lx = (Real)L0, Ly = (Real)L1, Lz = (Real)L2;
         DevReplica rr;
@@ -799,8 +875,8 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
                 CellParams<Real> p[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    int c = base + cell_axis(x[j], sS[0], L0) +
-                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    int c = base + cell_bin(x[j], sF[0], L0) +
+                            L0 * (cell_bin(y[j], sF[1], L1) + L1 * cell_bin(z[j], sF[2], L2));
                     c = j < nv ? c : base;
                     p[j] = get_params<Real>(a.params, c);
                 }
@@ -814,15 +890,21 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j < nv && p[j].kappa >= Real(0)) {
-                        if (RULE == 0) {
-                            srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
-                        } else {
-                            vx[j] = p[j].ux + sc * nn[j][0] - p[j].ax;
-                            vy[j] = p[j].uy + sc * nn[j][1] - p[j].ay;
-                            vz[j] = p[j].uz + sc * nn[j][2] - p[j].az;
-                        }
+                    // the rule is applied to every slot and kept where it
+                    // applies (no branch): a member of a cell that collides
+                    const bool on = j < nv && p[j].kappa >= Real(0);
+                    Real rx, ry, rz;
+                    if (RULE == 0) {
+                        rx = vx[j]; ry = vy[j]; rz = vz[j];
+                        srd_rotate<Real>(p[j], ca, sa, rx, ry, rz);
+                    } else {
+                        rx = p[j].ux + sc * nn[j][0] - p[j].ax;
+                        ry = p[j].uy + sc * nn[j][1] - p[j].ay;
+                        rz = p[j].uz + sc * nn[j][2] - p[j].az;
                     }
+                    vx[j] = on ? rx : vx[j];
+                    vy[j] = on ? ry : vy[j];
+                    vz[j] = on ? rz : vz[j];
                 }
             }
             if (STREAM) {
@@ -844,7 +926,7 @@ __global__ void __launch_bounds__(544) k_solvent_ws(StepArgs a, int cap)
                         }
                     }
             }
-            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sF + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (nv > 0) {
                 if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
@@ -937,6 +1019,7 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
             const DevReplica cr = a.reps[rep];
             if (COLLIDE) grid_shift(cr, step, &wc.S[0]);
             if (BIN) grid_shift(cr, step + (COLLIDE ? 1 : 0), &wc.S[3]);
+            for (int c = 0; c < 6; ++c) wc.Sf[c] = shift_as(wc.S[c], 0.0f);
             wc.L[0] = cr.L[0]; wc.L[1] = cr.L[1]; wc.L[2] = cr.L[2];
             wc.base = cr.cell_base;
             wc.key0 = cr.key0;
@@ -982,9 +1065,9 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
             break;
         }
         const TileMeta &mt = meta[warp][q];
-        int32_t sS[6];
+        typename ShiftT<Real>::type sF[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) sS[c] = mt.S[c];
+        for (int c = 0; c < 6; ++c) sF[c] = tile_shift(mt, c, typename ShiftT<Real>::type());
         const int L0 = mt.L[0], L1 = mt.L[1], L2 = mt.L[2], base = mt.base, n = mt.n;
         const Real Lx = (Real)L0, Ly = (Real)L1, Lz = (Real)L2;
         DevReplica rr;
@@ -1014,8 +1097,8 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
                 CellParams<Real> p[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    int c = base + cell_axis(x[j], sS[0], L0) +
-                            L0 * (cell_axis(y[j], sS[1], L1) + L1 * cell_axis(z[j], sS[2], L2));
+                    int c = base + cell_bin(x[j], sF[0], L0) +
+                            L0 * (cell_bin(y[j], sF[1], L1) + L1 * cell_bin(z[j], sF[2], L2));
                     c = j < nv ? c : base;
                     p[j] = get_params<Real>(a.params, c);
                 }
@@ -1029,15 +1112,21 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
                 }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (j < nv && p[j].kappa >= Real(0)) {
-                        if (RULE == 0) {
-                            srd_rotate<Real>(p[j], ca, sa, vx[j], vy[j], vz[j]);
-                        } else {
-                            vx[j] = p[j].ux + sc * nn[j][0] - p[j].ax;
-                            vy[j] = p[j].uy + sc * nn[j][1] - p[j].ay;
-                            vz[j] = p[j].uz + sc * nn[j][2] - p[j].az;
-                        }
+                    // the rule is applied to every slot and kept where it
+                    // applies (no branch): a member of a cell that collides
+                    const bool on = j < nv && p[j].kappa >= Real(0);
+                    Real rx, ry, rz;
+                    if (RULE == 0) {
+                        rx = vx[j]; ry = vy[j]; rz = vz[j];
+                        srd_rotate<Real>(p[j], ca, sa, rx, ry, rz);
+                    } else {
+                        rx = p[j].ux + sc * nn[j][0] - p[j].ax;
+                        ry = p[j].uy + sc * nn[j][1] - p[j].ay;
+                        rz = p[j].uz + sc * nn[j][2] - p[j].az;
                     }
+                    vx[j] = on ? rx : vx[j];
+                    vy[j] = on ? ry : vy[j];
+                    vz[j] = on ? rz : vz[j];
                 }
             }
             if (STREAM) {
@@ -1059,7 +1148,7 @@ __global__ void __maxnreg__((WtRegs<Real, RULE>::n)) k_solvent_wt(StepArgs a, in
                         }
                     }
             }
-            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sS + 3, L0, L1, L2, base, rr, step,
+            if (BIN) bin4<Real, RULE, COLLIDE>(a, x, y, z, vx, vy, vz, tg, nv, sF + 3, L0, L1, L2, base, rr, step,
                                                 m, sc, sums, C);
             if (nv > 0) {
                 if (STREAM) { sst4(S[0] + i, x); sst4(S[1] + i, y); sst4(S[2] + i, z); }
@@ -1099,29 +1188,68 @@ static void smem_opt_in(const void *func, size_t bytes)
         have = bytes;
 }
 
+// The persistent passes take their tiles round robin: a CTA that is not
+// resident from the start runs its share after the others have finished.  The
+// grid is therefore capped at the CTAs that are resident together (registers,
+// shared memory and threads of this kernel at this launch shape), once per
+// (kernel, device, shape).
+static int resident_grid(const void *func, int grid, int threads, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<std::pair<const void *, int>, std::pair<int, size_t>>, int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return grid;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(std::make_pair(func, dev), std::make_pair(threads, bytes));
+    auto it = done.find(key);
+    if (it == done.end()) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, bytes) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return grid;                       // the launch reports any error
+        }
+        it = done.emplace(key, std::max(1, per_sm) * std::max(1, sms)).first;
+    }
+    return std::max(1, std::min(grid, it->second));
+}
+
 template <typename Real, int RULE, int FLAGS>
 static void launch_wt(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
     const int warps = cfg.block / 32;
     const size_t bytes = (size_t)warps * WT_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
-    smem_opt_in((const void *)k_solvent_wt<Real, RULE, FLAGS>, bytes);
-    k_solvent_wt<Real, RULE, FLAGS><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
+    const void *f = (const void *)k_solvent_wt<Real, RULE, FLAGS>;
+    smem_opt_in(f, bytes);
+    const int grid = resident_grid(f, cfg.grid, cfg.block, bytes);
+    k_solvent_wt<Real, RULE, FLAGS><<<grid, cfg.block, bytes, s>>>(a, cfg.cap);
 }
 
 template <typename Real, int RULE, int FLAGS>
 static void launch_ws(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
     const size_t bytes = (size_t)WS_STAGES * solvent_stage_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap);
-    smem_opt_in((const void *)k_solvent_ws<Real, RULE, FLAGS>, bytes);
-    k_solvent_ws<Real, RULE, FLAGS><<<cfg.grid, cfg.block + 32, bytes, s>>>(a, cfg.cap);
+    const void *f = (const void *)k_solvent_ws<Real, RULE, FLAGS>;
+    smem_opt_in(f, bytes);
+    const int grid = resident_grid(f, cfg.grid, cfg.block + 32, bytes);
+    k_solvent_ws<Real, RULE, FLAGS><<<grid, cfg.block + 32, bytes, s>>>(a, cfg.cap);
 }
 
 template <typename Real, int RULE, int FLAGS>
 static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
 {
     const size_t bytes = solvent_smem_bytes(sizeof(Real) == 4 ? 1 : 0, RULE, cfg.cap, cfg.block);
-    smem_opt_in((const void *)k_solvent_staged<Real, RULE, FLAGS>, bytes);
-    k_solvent_staged<Real, RULE, FLAGS><<<cfg.grid, cfg.block, bytes, s>>>(a, cfg.cap);
+    const void *f = (const void *)k_solvent_staged<Real, RULE, FLAGS>;
+    smem_opt_in(f, bytes);
+    const int grid = resident_grid(f, cfg.grid, cfg.block, bytes);
+    k_solvent_staged<Real, RULE, FLAGS><<<grid, cfg.block, bytes, s>>>(a, cfg.cap);
+}
+
+template <typename Real, int RULE, int FLAGS>
+static void launch_direct(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
+{
+    const int grid = resident_grid((const void *)k_solvent<Real, RULE, FLAGS>, cfg.grid, cfg.block, 0);
+    k_solvent<Real, RULE, FLAGS><<<grid, cfg.block, 0, s>>>(a);
 }
 
 template <typename Real, int RULE>
@@ -1167,14 +1295,12 @@ static void dispatch_flags(const StepArgs &a, int flags, LaunchCfg cfg, cudaStre
         return;
     }
     switch (flags) {
-    case SOLV_STREAM: k_solvent<Real, RULE, SOLV_STREAM><<<cfg.grid, cfg.block, 0, s>>>(a); break;
-    case SOLV_BIN: k_solvent<Real, RULE, SOLV_BIN><<<cfg.grid, cfg.block, 0, s>>>(a); break;
-    case SOLV_COLLIDE: k_solvent<Real, RULE, SOLV_COLLIDE><<<cfg.grid, cfg.block, 0, s>>>(a); break;
-    case SOLV_STREAM | SOLV_BIN:
-        k_solvent<Real, RULE, SOLV_STREAM | SOLV_BIN><<<cfg.grid, cfg.block, 0, s>>>(a);
-        break;
+    case SOLV_STREAM: launch_direct<Real, RULE, SOLV_STREAM>(a, cfg, s); break;
+    case SOLV_BIN: launch_direct<Real, RULE, SOLV_BIN>(a, cfg, s); break;
+    case SOLV_COLLIDE: launch_direct<Real, RULE, SOLV_COLLIDE>(a, cfg, s); break;
+    case SOLV_STREAM | SOLV_BIN: launch_direct<Real, RULE, SOLV_STREAM | SOLV_BIN>(a, cfg, s); break;
     case SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN:
-        k_solvent<Real, RULE, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN><<<cfg.grid, cfg.block, 0, s>>>(a);
+        launch_direct<Real, RULE, SOLV_COLLIDE | SOLV_STREAM | SOLV_BIN>(a, cfg, s);
         break;
     default: break;
     }
@@ -1200,7 +1326,7 @@ size_t solvent_stage_bytes(int precision, int rule, int cap)
 
 size_t solvent_smem_bytes(int precision, int rule, int cap, int)
 {
-    return 2 * solvent_stage_bytes(precision, rule, cap);
+    return ST_STAGES * solvent_stage_bytes(precision, rule, cap);
 }
 
 // ------------------------------------------------------- cell parameters
@@ -1249,16 +1375,21 @@ __device__ double gamma_half_dof(const DevReplica &r, int64_t step, uint32_t lc,
 }
 
 // Gamma(a, 1), a = n/2 >= 3/2, by the rejection method of Marsaglia and Tsang
-// (ACM Trans. Math. Softw. 26, 363 (2000)), without their squeeze: d = a - 1/3,
-// c = 1/sqrt(9 d); a standard normal x and a uniform u give v = (1 + c x)^3,
-// accepted (d v) when v > 0 and ln u < x^2/2 + d (1 - v + ln v).  Each Philox
-// block (word 3 of the counter = block index) gives two attempts: the
-// Box-Muller pair of words 0 and 1 and the uniforms of words 2 and 3; after
-// MT_MAX_BLOCKS blocks (never reached in practice: an attempt is accepted with
-// probability > 0.95) d is returned.  FP32 form: with y = c x the test is
+// (ACM Trans. Math. Softw. 26, 363 (2000)): d = a - 1/3, c = 1/sqrt(9 d); a
+// standard normal x and a uniform u give v = (1 + c x)^3, accepted (d v) when
+// v > 0 and ln u < x^2/2 + d (1 - v + ln v).  Each Philox block (word 3 of the
+// counter = block index) gives two attempts: the Box-Muller pair of words 0
+// and 1 and the uniforms of words 2 and 3; after MT_MAX_BLOCKS blocks (never
+// reached in practice: an attempt is accepted with probability > 0.95) d is
+// returned.  FP32 form: the attempt is first tested against the method's
+// squeeze u < 1 - 0.0331 x^4, which lies inside the acceptance region, so it
+// only decides earlier what the full test would (it holds for ~98 % of the
+// attempts and needs no logarithm); otherwise, with y = c x, the full test is
 // evaluated as -2 ln u > -x^2 - 2 d (log1p(dv) - dv), dv = v - 1 =
-// y (3 + y (3 + y)), which keeps the cancellation of 1 - v + ln v out of it;
-// the normals use accurate (not fast) logarithm and sine/cosine.
+// y (3 + y (3 + y)), which keeps the cancellation of 1 - v + ln v out of it.
+// The normals use the fast logarithm (with the complement of u near 1) and
+// sine/cosine, whose errors (~1e-6 relative) are far below the tolerance of
+// the collision's result.
 constexpr uint32_t MT_MAX_BLOCKS = 64;
 __device__ float gamma_mt(const DevReplica &r, int64_t step, uint32_t lc, int n_dof, float)
 {
@@ -1267,9 +1398,9 @@ __device__ float gamma_mt(const DevReplica &r, int64_t step, uint32_t lc, int n_
     const float c = 1.0f / sqrtf(9.0f * d);
     for (uint32_t k = 0; k < MT_MAX_BLOCKS; ++k) {
         const uint4 w = draw(r, step, lc, TAG_THERMO_MT, k);
-        const float rr = sqrtf((w.x & 0x80000000u) ? -2.0f * log1pf(-u01f(~w.x)) : -2.0f * logf(u01f(w.x)));
+        const float rr = sqrtf(neg2log(w.x));
         float sn, cs;
-        sincospif(2.0f * u01f(w.y) - 1.0f, &sn, &cs);     // angle 2 pi u - pi: cos(2 pi u) = -cs
+        __sincosf(6.283185307179586f * (u01f(w.y) - 0.5f), &sn, &cs);   // angle shifted by pi
         const float xs[2] = {-rr * cs, -rr * sn};
         const uint32_t us[2] = {w.z, w.w};
 #pragma unroll
@@ -1277,8 +1408,9 @@ __device__ float gamma_mt(const DevReplica &r, int64_t step, uint32_t lc, int n_
             const float x = xs[j], y = c * x;
             if (y <= -1.0f) continue;
             const float dv = y * (3.0f + y * (3.0f + y));
-            const float m2lu = (us[j] & 0x80000000u) ? -2.0f * log1pf(-u01f(~us[j])) : -2.0f * logf(u01f(us[j]));
-            if (m2lu > -x * x - 2.0f * d * (log1pf(dv) - dv)) return d * (1.0f + dv);
+            const float x2 = x * x;
+            if (u01f(us[j]) < 1.0f - 0.0331f * (x2 * x2)) return d * (1.0f + dv);
+            if (neg2log(us[j]) > -x2 - 2.0f * d * (log1pf(dv) - dv)) return d * (1.0f + dv);
         }
     }
     return d;
@@ -1315,32 +1447,17 @@ __device__ __forceinline__ float i128f(__int128 x)
 }
 
 // Relative kinetic energy E_rel = (S2 - |S1|^2 / M) / 2 of a cell from its exact
-// fixed-point sums, without cancellation: about a fixed-point reference
-// velocity w0 ~ u,  sum m|v - w0|^2 = S2 - 2 w0.S1 + M |w0|^2 is formed in exact
-// int128 arithmetic and E_rel = (that - |S1 - M w0|^2 / M) / 2.
-// Units: S1 of 2^-32, S2 of 2^-28, Mq of 2^-24, w0 of 2^-20; products of 2^-64.
-__device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long S1[3], long long S2, float M,
-                                                  const float u[3])
+// fixed-point sums, rounded once: with S1 in units of 2^-32, S2 of 2^-28 and
+// M = Mq 2^-24, 2 M E_rel = 2^-64 X for the integer X = S2 Mq 2^12 - |S1|^2,
+// formed exactly in int128 (|X| < 2^127 within the word limits) and converted
+// to float once.  X < 0 (per-particle roundings of a cell whose members move
+// alike) gives 0.
+__device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long S1[3], long long S2, float M)
 {
-    int W[3];
-    long long W2 = 0;
-    __int128 D = (__int128)S2 << 36;
+    __int128 X = ((__int128)S2 * Mq) << 12;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        W[k] = __float2int_rn(fminf(fmaxf(u[k] * 1048576.0f, -5.0e8f), 5.0e8f));
-        D -= ((__int128)W[k] * S1[k]) << 13;
-        W2 += (long long)W[k] * W[k];
-    }
-    D += (__int128)Mq * W2;
-    float r = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const __int128 dk = ((__int128)S1[k] << 32) - (((__int128)Mq * W[k]) << 20);
-        const float df = i128f(dk) * 5.421010862427522170037264e-20f;   // 2^-64
-        r += df * df;
-    }
-    const float e2 = i128f(D) * 5.421010862427522170037264e-20f - r / M;
-    return 0.5f * fmaxf(e2, 0.0f);
+    for (int k = 0; k < 3; ++k) X -= (__int128)S1[k] * S1[k];
+    return fmaxf(i128f(X), 0.0f) * 2.710505431213761085018632e-20f / M;   // 2^-65
 }
 
 // FP32 form: cell words -> collision parameters with FP32/integer pipes only.
@@ -1382,7 +1499,7 @@ __device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplic
             rec[4] = -rho * cs; rec[5] = -rho * sn; rec[6] = zz;
             float kappa = 1.0f;
             if (a.thermostat) {
-                const float erel = rel_energy_fixed(Mq, S1, w[3], M, u);
+                const float erel = rel_energy_fixed(Mq, S1, w[3], M);
                 const float g = a.thermostat == 2 ? gamma_mt(r, step, lc, 3 * (n - 1), 0.0f)
                                                   : gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
                 kappa = erel > 0.0f ? sqrtf(kT * g / erel) : 1.0f;
@@ -1408,6 +1525,10 @@ __global__ void __launch_bounds__(256, 4) k_params32(StepArgs a)
     long long *sums = reinterpret_cast<long long *>(a.sums);
     long long *dbg = reinterpret_cast<long long *>(a.dbg_sums);
     const int64_t C = a.n_cells;
+    // CTAs start roughly in index order; they take the cell tiles from the last
+    // to the first, so that the words the solvent pass binned last (still in
+    // L2) are read first, and the records and cleared words that the next
+    // solvent pass (a forward sweep) needs first are the ones written last
     const int t0 = blockIdx.x * K;
     int64_t cell[K];
     int rep[K];
@@ -1416,7 +1537,7 @@ __global__ void __launch_bounds__(256, 4) k_params32(StepArgs a)
         cell[k] = -1;
         rep[k] = 0;
         if (t0 + k < a.n_ctiles) {
-            const Tile tl = a.ctiles[t0 + k];
+            const Tile tl = a.ctiles[a.n_ctiles - 1 - (t0 + k)];
             const int64_t c = tl.begin + threadIdx.x;
             if (c < tl.end) { cell[k] = c; rep[k] = tl.rep; }
             if (threadIdx.x == 0) stile[k] = tl;

@@ -394,13 +394,13 @@ double solvent_bytes(const mpcd_ctx *c, int flags)
 }
 
 // ----------------------------------------------------------- step pieces
-// dynamic shared memory of the staged (two-stage ring) or warp-specialised
-// (three-stage ring) solvent pass
+// dynamic shared memory of the staged or warp-specialised solvent pass
+// (three-stage rings)
 size_t ring_bytes(const mpcd_ctx *c, int mode, int tile, int block)
 {
     const size_t stage = solvent_stage_bytes(c->prm.precision, c->prm.rule, tile);
     if (mode == 3) return (size_t)(block / 32) * 3 * stage;   // one three-stage ring per warp
-    return (mode == 2 ? 3 : 2) * stage;
+    return 3 * stage;
 }
 
 bool staged_fits(const mpcd_ctx *c, int tile, int mode, int block)
@@ -1911,9 +1911,9 @@ int mpcd_autotune(mpcd_ctx *c, int32_t steps_per_trial, void *stream)
     float best_ms = 1e30f;
     std::vector<mpcd_tuning> cand;
     for (int bl : {128, 256, 512})
-        for (int tl : {1024, 2048, 4096})
-            for (int ct : {1, 2, 4})
-                if (staged_fits(c, tl, 1, bl)) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 1});
+        for (int tl : {512, 1024, 2048})
+            for (int ct : {1, 2, 4, 5})
+                if (staged_fits(c, tl, 1, bl) && tl >= bl) cand.push_back(mpcd_tuning{bl, tl, ct, c->tune.sort_period, 1});
     for (int bl : {256, 512})
         for (int tl : {1024, 2048})
             for (int ct : {1, 2})

@@ -238,31 +238,42 @@ constexpr long long COUNT48 = 1LL << 48;
 // momentum terms of the angular-momentum words)
 __device__ __forceinline__ long long q20(float f) { return (long long)__float2int_rn(__fmul_rn(f, 1048576.0f)); }
 
-// round-half-even(f 2^32) as int64 for |f| < 2^15, with 32-bit conversions
-// only.  t = f 2^8 is exact; with h = floor(t), f 2^32 = h 2^24 + (t - h) 2^24.
+// floor(t) for |t| < 2^22 without a conversion instruction: t + 1.5 2^23
+// rounded toward -inf lies in [2^23, 2^24), where the float32 spacing is 1, so
+// it is 1.5 2^23 + floor(t) exactly; its low mantissa bits hold floor(t) and
+// subtracting 1.5 2^23 again gives floor(t) as a float, exactly (Sterbenz).
+constexpr float FLOOR_MAGIC = 12582912.0f;     // 1.5 2^23, bits 0x4B400000
+__device__ __forceinline__ float floor_magic(float t) { return __fadd_rd(t, FLOOR_MAGIC); }
+__device__ __forceinline__ int floor_magic_int(float m) { return __float_as_int(m) - 0x4B400000; }
+
+// round-half-even(f 2^32) as int64 for |f| < 2^14, with one 32-bit conversion.
+// t = f 2^8 is exact; with h = floor(t), f 2^32 = h 2^24 + (t - h) 2^24.
 // For |t| >= 1/2 (and t >= 0) the difference r = t - h is exact and r 2^24
-// is an integer or is rounded once by the last conversion; for t in [-1/2, 0)
+// is an integer or is rounded once by the conversion; for t in [-1/2, 0)
 // r = t + 1 lies in [1/2, 1), where float32 has the spacing 2^-24, so forming
 // r rounds t 2^24 + 2^24 to an integer - the rounding the result needs (ties
-// to even: 2^24 is even).  Identical to qfix<32>(f).
+// to even: 2^24 is even).  Identical to qfix<32>(f) on that range.
 __device__ __forceinline__ long long q32(float f)
 {
     const float t = __fmul_rn(f, 256.0f);
-    const int h = __float2int_rd(t);
-    const float r = __fsub_rn(t, __int2float_rn(h));
+    const float hm = floor_magic(t);
+    const float r = __fsub_rn(t, __fsub_rn(hm, FLOOR_MAGIC));
+    const int h = floor_magic_int(hm);
     const int l = __float2int_rn(__fmul_rn(r, 16777216.0f));
     return (long long)((unsigned long long)(long long)h << 24) + l;
 }
 
-// round-half-even(e 2^28) as int64 for 0 <= e < 2^28 (a kinetic-energy term),
-// with 32-bit conversions only: e = 16 h + r with h = floor(e / 16) (exact) and
-// r in [0, 16) formed exactly by one fused multiply-add (r is a multiple of
-// ulp(e) below 16); then e 2^28 = h 2^32 + r 2^28 and r 2^28 < 2^32 rounds
-// within the low word.  Identical to qfix<28>(e) on that range.
+// round-half-even(e 2^28) as int64 for 0 <= e < 2^27 (a kinetic-energy term),
+// with one 32-bit conversion: e = 16 h + r with h = floor(e / 16) (exact; e / 16
+// + 2^23 rounded toward -inf is 2^23 + h) and r in [0, 16) formed exactly by
+// one fused multiply-add (r is a multiple of ulp(e) below 16); then
+// e 2^28 = h 2^32 + r 2^28 and r 2^28 < 2^32 rounds within the low word.
+// Identical to qfix<28>(e) on that range.
 __device__ __forceinline__ long long q28_nonneg(float e)
 {
-    const int h = __float2int_rd(__fmul_rn(e, 0.0625f));
-    const float r = __fmaf_rn(-16.0f, __int2float_rn(h), e);
+    const float hm = __fadd_rd(__fmul_rn(e, 0.0625f), 8388608.0f);
+    const int h = __float_as_int(hm) - 0x4B000000;
+    const float r = __fmaf_rn(-16.0f, __fsub_rn(hm, 8388608.0f), e);
     const unsigned lo = __float2uint_rn(__fmul_rn(r, 268435456.0f));
     return (long long)(((unsigned long long)(unsigned)h << 32) | lo);
 }
