@@ -1449,15 +1449,25 @@ __device__ __forceinline__ float i128f(__int128 x)
 // Relative kinetic energy E_rel = (S2 - |S1|^2 / M) / 2 of a cell from its exact
 // fixed-point sums, rounded once: with S1 in units of 2^-32, S2 of 2^-28 and
 // M = Mq 2^-24, 2 M E_rel = 2^-64 X for the integer X = S2 Mq 2^12 - |S1|^2,
-// formed exactly in int128 (|X| < 2^127 within the word limits) and converted
-// to float once.  X < 0 (per-particle roundings of a cell whose members move
+// formed exactly in int128 (|X| < 2^127 within the word limits), converted to
+// float once and scaled by 2^-65 / M (iM = 1/M).  X < 0 (per-particle roundings of a cell whose members move
 // alike) gives 0.
-__device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long S1[3], long long S2, float M)
+__device__ __forceinline__ float rel_energy_fixed(long long Mq, const long long S1[3], long long S2, float iM)
 {
     __int128 X = ((__int128)S2 * Mq) << 12;
 #pragma unroll
     for (int k = 0; k < 3; ++k) X -= (__int128)S1[k] * S1[k];
-    return fmaxf(i128f(X), 0.0f) * 2.710505431213761085018632e-20f / M;   // 2^-65
+    return fmaxf(i128f(X), 0.0f) * 2.710505431213761085018632e-20f * iM;   // 2^-65 / M
+}
+
+// int64 -> float for |w| < 2^48 (a momentum or noise sum), rounded once: the
+// magnitude's high 24 and low 24 bits convert exactly and one fused
+// multiply-add joins them
+__device__ __forceinline__ float ll2f48(long long w)
+{
+    const unsigned long long m = w < 0 ? 0ull - (unsigned long long)w : (unsigned long long)w;
+    const float f = fmaf(__uint2float_rn((uint32_t)(m >> 24)), 16777216.0f, __uint2float_rn((uint32_t)m & 0xFFFFFFu));
+    return w < 0 ? -f : f;
 }
 
 // FP32 form: cell words -> collision parameters with FP32/integer pipes only.
@@ -1486,7 +1496,7 @@ __device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplic
         const float iM = 1.0f / M;
         float u[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) u[k] = ll2f(S1[k]) * s32 * iM;
+        for (int k = 0; k < 3; ++k) u[k] = ll2f48(S1[k]) * s32 * iM;
         rec[0] = u[0]; rec[1] = u[1]; rec[2] = u[2];
         const uint32_t lc = (uint32_t)(c - r.cell_base);
         if (RULE == 0) {
@@ -1499,15 +1509,15 @@ __device__ __forceinline__ void params32_cell(const StepArgs &a, const DevReplic
             rec[4] = -rho * cs; rec[5] = -rho * sn; rec[6] = zz;
             float kappa = 1.0f;
             if (a.thermostat) {
-                const float erel = rel_energy_fixed(Mq, S1, w[3], M);
+                const float erel = rel_energy_fixed(Mq, S1, w[3], iM);
                 const float g = a.thermostat == 2 ? gamma_mt(r, step, lc, 3 * (n - 1), 0.0f)
                                                   : gamma_half_dof(r, step, lc, 3 * (n - 1), 0.0f);
-                kappa = erel > 0.0f ? sqrtf(kT * g / erel) : 1.0f;
+                kappa = erel > 0.0f ? sqrtf(kT * g) * rsqrtf(erel) : 1.0f;
             }
             rec[3] = kappa;
         } else {
             rec[3] = 1.0f;
-            rec[4] = ll2f(w[3]) * s32 * iM; rec[5] = ll2f(w[4]) * s32 * iM; rec[6] = ll2f(w[5]) * s32 * iM;
+            rec[4] = ll2f48(w[3]) * s32 * iM; rec[5] = ll2f48(w[4]) * s32 * iM; rec[6] = ll2f48(w[5]) * s32 * iM;
         }
     }
     float4 *o = reinterpret_cast<float4 *>(a.params) + 2 * c;
@@ -1766,23 +1776,52 @@ __device__ __forceinline__ int plain_cell(const DevReplica &r, Real x, Real y, R
            r.L[0] * (cell_axis(y, 0, r.L[1]) + r.L[1] * cell_axis(z, 0, r.L[2]));
 }
 
+// four consecutive elements from i (a multiple of 4 inside a tile that starts
+// on an 8-element boundary): one vector load when all four are in the tile
+__device__ __forceinline__ void load4_tail(const float *p, int64_t i, int64_t end, float (&o)[4])
+{
+    if (i + 4 <= end) {
+        const float4 t = *reinterpret_cast<const float4 *>(p + i);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = i + j < end ? p[i + j] : 0.0f;
+    }
+}
+__device__ __forceinline__ void load4_tail(const double *p, int64_t i, int64_t end, double (&o)[4])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = i + j < end ? p[i + j] : 0.0;
+}
+
+// histogram of the cells (four particles per thread, 1024-particle units of
+// the state-transfer tiles)
 template <typename Real>
-__global__ void k_sort_count(StepArgs a, int32_t *counts)
+__global__ void __launch_bounds__(256) k_sort_count(StepArgs a, int32_t *counts)
 {
     const Real *X = (const Real *)a.x, *Y = (const Real *)a.y, *Z = (const Real *)a.z;
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        const Tile tl = a.tiles[t];
+    const int units = a.n_tiles * (2048 / 1024);
+    for (int w = blockIdx.x; w < units; w += gridDim.x) {
+        const Tile tl = a.tiles[w >> 1];
         const DevReplica r = a.reps[tl.rep];
-        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x)
-            atomicAdd(counts + plain_cell(r, X[i], Y[i], Z[i]), 1);
+        const int64_t i0 = tl.begin + (int64_t)(w & 1) * 1024 + 4 * threadIdx.x;
+        if (i0 >= tl.end) continue;
+        Real x[4], y[4], z[4];
+        load4_tail(X, i0, tl.end, x);
+        load4_tail(Y, i0, tl.end, y);
+        load4_tail(Z, i0, tl.end, z);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (i0 + j < tl.end) atomicAdd(counts + plain_cell(r, x[j], y[j], z[j]), 1);
     }
 }
 
-void launch_sort_count(const StepArgs &a, int32_t *counts, cudaStream_t s)
+void launch_sort_count(const StepArgs &a, int32_t *counts, int num_sms, cudaStream_t s)
 {
     if (a.n_tiles == 0) return;
-    if (a.precision == 1) k_sort_count<float><<<a.n_tiles, 256, 0, s>>>(a, counts);
-    else k_sort_count<double><<<a.n_tiles, 256, 0, s>>>(a, counts);
+    const int grid = std::min(2 * a.n_tiles, num_sms * 8);
+    if (a.precision == 1) k_sort_count<float><<<grid, 256, 0, s>>>(a, counts);
+    else k_sort_count<double><<<grid, 256, 0, s>>>(a, counts);
 }
 
 // exclusive scan: chunks of SCAN_CHUNK elements, one CTA of 1024 threads per chunk
@@ -1879,38 +1918,142 @@ void launch_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *bs, cudaSt
     k_scan_final<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, bs);
 }
 
+// Re-sort by rank and gather.  A scatter of the six state arrays and the tags
+// writes each destination sector in pieces (the particles of one cell arrive
+// from different places of the source order, at different times), and the
+// pieces that leave L2 before their sector is complete cost a read-modify-write
+// in DRAM.  Instead the rank pass scatters only one 4-byte source index per
+// particle; the gather pass then writes every destination array in order and
+// reads the sources, which lie close together (the state was cell-sorted a few
+// steps earlier), mostly from L2.
+//
+// Both passes take 1024-element units of the state-transfer tiles round robin
+// over the grid (four consecutive elements per thread, whose memory accesses
+// are independent and overlap), so that the CTAs in flight cover one compact
+// window of the state (about grid x 1024 elements) and the sources that
+// neighbouring destinations share are still in L2 when they are read again.
+constexpr int SORT_UNIT = 1024, SORT_UNITS = 2048 / SORT_UNIT;   // units per state-transfer tile
+#ifndef GATHER_CTAS_PER_SM
+#define GATHER_CTAS_PER_SM 4
+#endif
+
+// rank: destination slot = the cell's first slot + a cursor; the lanes of a
+// warp in one cell take consecutive slots with one atomic.  perm[slot] = the
+// particle's row in its replica.
 template <typename Real>
-__global__ void k_sort_scatter(StepArgs a, const int32_t *ex, int32_t *cursor, Real *d0, Real *d1, Real *d2,
-                               Real *d3, Real *d4, Real *d5, uint32_t *dtag)
+__global__ void __launch_bounds__(256) k_sort_rank(StepArgs a, const int32_t *ex, int32_t *cursor, uint32_t *perm)
 {
-    const Real *S[6] = {(const Real *)a.x, (const Real *)a.y, (const Real *)a.z,
-                        (const Real *)a.vx, (const Real *)a.vy, (const Real *)a.vz};
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
-        const Tile tl = a.tiles[t];
+    const Real *X = (const Real *)a.x, *Y = (const Real *)a.y, *Z = (const Real *)a.z;
+    const unsigned lane = threadIdx.x & 31u;
+    const int units = a.n_tiles * SORT_UNITS;
+    for (int w = blockIdx.x; w < units; w += gridDim.x) {   // uniform trip count (warp votes)
+        const Tile tl = a.tiles[w / SORT_UNITS];
         const DevReplica r = a.reps[tl.rep];
+        const int64_t i0 = tl.begin + (int64_t)(w % SORT_UNITS) * SORT_UNIT + 4 * threadIdx.x;
+        int c[4], base[4];
+        bool v[4];
+        unsigned peers[4];
+        Real x[4], y[4], z[4];
+        load4_tail(X, i0, tl.end, x);
+        load4_tail(Y, i0, tl.end, y);
+        load4_tail(Z, i0, tl.end, z);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = i0 + j < tl.end;
+            c[j] = v[j] ? plain_cell(r, x[j], y[j], z[j]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned act = __ballot_sync(0xffffffffu, v[j]);
+            peers[j] = v[j] ? __match_any_sync(act, c[j]) : 0u;
+            base[j] = 0;
+        }
+        // the leaders' atomics are independent: all four are in flight together
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (v[j] && (int)lane == __ffs(peers[j]) - 1) base[j] = atomicAdd(cursor + c[j], __popc(peers[j]));
         const int32_t ex0 = ex[r.cell_base];
-        for (int64_t i = tl.begin + threadIdx.x; i < tl.end; i += blockDim.x) {
-            int c = plain_cell(r, S[0][i], S[1][i], S[2][i]);
-            int64_t pos = r.solv_begin + (ex[c] - ex0) + atomicAdd(cursor + c, 1);
-            d0[pos] = S[0][i]; d1[pos] = S[1][i]; d2[pos] = S[2][i];
-            d3[pos] = S[3][i]; d4[pos] = S[4][i]; d5[pos] = S[5][i];
-            dtag[pos] = a.tag[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned act = __ballot_sync(0xffffffffu, v[j]);
+            if (v[j]) {
+                const int b = __shfl_sync(act, base[j], __ffs(peers[j]) - 1) + __popc(peers[j] & ((1u << lane) - 1u));
+                perm[r.solv_begin + (ex[c[j]] - ex0) + b] = (uint32_t)(i0 + j - r.solv_begin);
+            }
         }
     }
 }
 
-void launch_sort_scatter(const StepArgs &a, const int32_t *ex, int32_t *cursor, void *const d[6],
-                         uint32_t *dtag, cudaStream_t s)
+// gather: every slot of the replica reads its particle's arrays and tag
+template <typename Real>
+__global__ void __launch_bounds__(256) k_sort_gather(StepArgs a, const uint32_t *perm, Real *d0, Real *d1, Real *d2,
+                                                    Real *d3, Real *d4, Real *d5, uint32_t *dtag)
+{
+    const Real *S[6] = {(const Real *)a.x, (const Real *)a.y, (const Real *)a.z,
+                        (const Real *)a.vx, (const Real *)a.vy, (const Real *)a.vz};
+    Real *D[6] = {d0, d1, d2, d3, d4, d5};
+    const int units = a.n_tiles * SORT_UNITS;
+    for (int w = blockIdx.x; w < units; w += gridDim.x) {
+        const Tile tl = a.tiles[w / SORT_UNITS];
+        const DevReplica r = a.reps[tl.rep];
+        const int64_t j0 = tl.begin + (int64_t)(w % SORT_UNITS) * SORT_UNIT + 4 * threadIdx.x;
+        if (j0 >= tl.end) continue;
+        const int n = tl.end - j0 < 4 ? (int)(tl.end - j0) : 4;
+        int64_t src[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t q = j < n ? perm[j0 + j] : 0u;
+            ok[j] = j < n && (int64_t)q < r.n_solvent;
+            if (j < n && !ok[j]) {   // a slot no particle was ranked into: no access
+                atomicOr(a.d_err, ERR_INDEX);
+                atomicCAS(a.d_err + 1, 0, 6);
+            }
+            src[j] = r.solv_begin + (ok[j] ? q : 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            Real o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = S[k][src[j]];
+            if (n == 4 && ok[0] && ok[1] && ok[2] && ok[3]) {
+                st4(D[k] + j0, o);   // j0 is a multiple of 4 (tiles start on 8-element boundaries)
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (ok[j]) D[k][j0 + j] = o[j];
+            }
+        }
+        uint32_t tg[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tg[j] = a.tag[src[j]];
+        if (n == 4 && ok[0] && ok[1] && ok[2] && ok[3]) {
+            *reinterpret_cast<uint4 *>(dtag + j0) = make_uint4(tg[0], tg[1], tg[2], tg[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ok[j]) dtag[j0 + j] = tg[j];
+        }
+    }
+}
+
+void launch_sort_rank_gather(const StepArgs &a, const int32_t *ex, int32_t *cursor, uint32_t *perm,
+                             void *const d[6], uint32_t *dtag, int num_sms, cudaStream_t s)
 {
     if (a.n_tiles == 0) return;
-    if (a.precision == 1)
-        k_sort_scatter<float><<<a.n_tiles, 256, 0, s>>>(a, ex, cursor, (float *)d[0], (float *)d[1],
-                                                       (float *)d[2], (float *)d[3], (float *)d[4],
-                                                       (float *)d[5], dtag);
-    else
-        k_sort_scatter<double><<<a.n_tiles, 256, 0, s>>>(a, ex, cursor, (double *)d[0], (double *)d[1],
-                                                        (double *)d[2], (double *)d[3], (double *)d[4],
-                                                        (double *)d[5], dtag);
+    // rank: full occupancy (its atomics' round trips need many warps); gather:
+    // GATHER_CTAS_PER_SM CTAs per SM, so that its window of the state stays in L2
+    const int units = a.n_tiles * SORT_UNITS;
+    const int grid_r = std::min(units, num_sms * 8), grid_g = std::min(units, num_sms * GATHER_CTAS_PER_SM);
+    if (a.precision == 1) {
+        k_sort_rank<float><<<grid_r, 256, 0, s>>>(a, ex, cursor, perm);
+        k_sort_gather<float><<<grid_g, 256, 0, s>>>(a, perm, (float *)d[0], (float *)d[1], (float *)d[2],
+                                                    (float *)d[3], (float *)d[4], (float *)d[5], dtag);
+    } else {
+        k_sort_rank<double><<<grid_r, 256, 0, s>>>(a, ex, cursor, perm);
+        k_sort_gather<double><<<grid_g, 256, 0, s>>>(a, perm, (double *)d[0], (double *)d[1], (double *)d[2],
+                                                     (double *)d[3], (double *)d[4], (double *)d[5], dtag);
+    }
 }
 
 // order every cell's segment by tag (insertion sort; segments hold ~10)

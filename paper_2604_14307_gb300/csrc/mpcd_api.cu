@@ -532,16 +532,20 @@ int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
     if (c->Ns == 0) return MPCD_OK;
     StepArgs a = make_io_args(c);
     const int nxt = c->cur ^ 1;
-    double bytes = (double)c->Ns * (2.0 * (6.0 * c->realsz + 4.0) + 3.0 * c->realsz);
+    // algorithmic bytes: positions read by the count and rank passes, the
+    // source index written and read, the state and tags read and written once
+    double bytes = (double)c->Ns * (2.0 * 3.0 * c->realsz + 2.0 * 4.0 + 2.0 * (6.0 * c->realsz + 4.0));
     int e = timed(c, "sort", bytes, s, [&] {
         cudaMemsetAsync(c->counts, 0, c->C * sizeof(int32_t), s);
         cudaMemsetAsync(c->cursor, 0, c->C * sizeof(int32_t), s);
         cudaMemsetAsync(c->tag[nxt], 0xFF, c->Nslots * sizeof(uint32_t), s);
-        launch_sort_count(a, c->counts, s);
+        launch_sort_count(a, c->counts, c->num_sms, s);
         launch_scan(c->counts, c->ex, c->C, c->scan_bs, s);
         void *dst[6] = {c->sol[nxt][0], c->sol[nxt][1], c->sol[nxt][2],
                         c->sol[nxt][3], c->sol[nxt][4], c->sol[nxt][5]};
-        launch_sort_scatter(a, c->ex, c->cursor, dst, c->tag[nxt], s);
+        // the permutation lives in the state-transfer record buffer (unused
+        // between state transfers; Nslots x 32 bytes)
+        launch_sort_rank_gather(a, c->ex, c->cursor, (uint32_t *)c->rec, dst, c->tag[nxt], c->num_sms, s);
         if (canonical) launch_sort_canonical(a, dst, c->tag[nxt], c->ex, s);
     });
     if (e) return e;

@@ -349,7 +349,7 @@ void launch_soa_to_aos(const StepArgs &a, void *xaos, void *vaos, const int64_t 
                        cudaStream_t s);
 void launch_solvent_diag(const StepArgs &a, double *acc, cudaStream_t s);
 // re-sort (kernels_solvent.cu)
-void launch_sort_count(const StepArgs &a, int32_t *counts, cudaStream_t s);
+void launch_sort_count(const StepArgs &a, int32_t *counts, int num_sms, cudaStream_t s);
 void launch_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *block_sums, cudaStream_t s);
 
 // Per-body velocity autocorrelation accumulators (translational and angular).
@@ -392,8 +392,9 @@ size_t rnemd_swap_smem();
 // mass and momentum profile of replica 0 (solvent and bodies), FP64 [n_bins] each
 void launch_velocity_profile(const StepArgs &a, int bin_axis, int vel_axis, int n_bins, double *mass, double *mom,
                              int num_sms, cudaStream_t s);
-void launch_sort_scatter(const StepArgs &a, const int32_t *offsets, int32_t *cursor,
-                         void *const dst[6], uint32_t *dst_tag, cudaStream_t s);
+// re-sort by rank (perm[slot] = row in the replica) and gather into d, dtag
+void launch_sort_rank_gather(const StepArgs &a, const int32_t *ex, int32_t *cursor, uint32_t *perm,
+                             void *const d[6], uint32_t *dtag, int num_sms, cudaStream_t s);
 void launch_sort_canonical(const StepArgs &a, void *const arr[6], uint32_t *tag,
                            const int32_t *offsets, cudaStream_t s);
 size_t scan_block_sums_size(int64_t n);
