@@ -491,7 +491,7 @@ def main():
             "bytes_per_launch": pk["bytes_per_launch"], "ms_per_launch": per_launch_ms,
             "share_of_step": pk["total_ms"] / ms_prof,
             "measured_in": "profiled pass (kernel-by-kernel launches with CUDA events, same step count)"}
-    launches = a.steps + sum(v["launches"] * (5 if k == "sort" else 1) for k, v in prof.items())
+    launches = a.steps + sum(v["launches"] * (6 if k == "sort" else 1) for k, v in prof.items())
     # whole-step effective bandwidth: algorithmic bytes of every kernel / step time
     step_bytes = sum(v["bytes_per_launch"] * v["launches"] for v in prof.values()) / a.steps
     hbm_eff = {"bytes_per_update": step_bytes / n_upd, "gbs": step_bytes / (ms / a.steps / 1e3) / 1e9}

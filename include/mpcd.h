@@ -121,7 +121,10 @@ typedef struct {
 } mpcd_replica_desc;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
- * functions are called on the creating thread; alloc returns NULL on failure. */
+ * functions are called on the creating thread; alloc returns NULL on failure
+ * and otherwise device memory aligned to at least 16 bytes (the kernels' bulk
+ * copies require it; cudaMalloc and PyTorch's caching allocator give 256 and
+ * 512). */
 typedef struct {
     void *(*alloc)(size_t bytes, void *user);
     void (*free)(void *ptr, void *user);
