@@ -555,6 +555,7 @@ __global__ void __maxnreg__((StRegs<Real, RULE>::n)) k_solvent_staged(StepArgs a
     __shared__ TileMeta meta[ST_STAGES];
     __shared__ TileMeta rcache;   // fields and grid shifts of the last replica met
     __shared__ int rcache_rep;
+    __shared__ int stile[ST_STAGES];   // tile in each stage (-1: none, the pass is done)
 
     const size_t SB = stage_bytes<Real, RULE>(cap);
     const int64_t step = *a.d_step;
@@ -567,21 +568,31 @@ __global__ void __maxnreg__((StRegs<Real, RULE>::n)) k_solvent_staged(StepArgs a
     };
     W *sums = reinterpret_cast<W *>(a.sums);
     const int64_t C = a.n_cells;
-    const int K = a.n_tiles > (int)blockIdx.x ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     int bad = 0;
 
-    // thread 0 only: the record of the next tile to issue is loaded one issue
-    // ahead, so that no load of a tile record stands between two tiles
+    // Tiles are handed out by a counter (a.tile_ctr, zero at launch) when one is
+    // given, else round robin: a CTA slowed by the kernels that share its SM
+    // then takes fewer tiles instead of delaying the end of the pass.
+    // Thread 0 only: the index and record of the next tile to issue are taken
+    // one issue ahead, so that neither stands between two tiles.
+    int nt = -1;
     int32_t nrep = 0;
     int64_t nbeg = 0, nend = 0;
-    auto issue = [&](int j) {   // local tile j into stage j % ST_STAGES
-        const int q = j % ST_STAGES;
-        const int rep = nrep;
-        const int64_t tbeg = nbeg, tend = nend;
-        if (j + 1 < K) {
-            const Tile tn = a.tiles[blockIdx.x + (j + 1) * gridDim.x];
+    auto take = [&](int j) {   // the index of local tile j and its record
+        const int t = a.tile_ctr ? atomicAdd(a.tile_ctr, 1) : (int)blockIdx.x + j * (int)gridDim.x;
+        nt = t < a.n_tiles ? t : -1;
+        if (nt >= 0) {
+            const Tile tn = a.tiles[nt];
             nrep = tn.rep; nbeg = tn.begin; nend = tn.end;
         }
+    };
+    auto issue = [&](int j) {   // local tile j into stage j % ST_STAGES
+        const int q = j % ST_STAGES;
+        stile[q] = nt;
+        if (nt < 0) return;
+        const int rep = nrep;
+        const int64_t tbeg = nbeg, tend = nend;
+        take(j + 1);
         if (rep != rcache_rep) {
             const DevReplica cr = a.reps[rep];
             if (COLLIDE) grid_shift(cr, step, &rcache.S[0]);
@@ -609,16 +620,14 @@ __global__ void __maxnreg__((StRegs<Real, RULE>::n)) k_solvent_staged(StepArgs a
         for (int q = 0; q < ST_STAGES; ++q) mbar_init(&full[q], 1);
         mbar_fence_init();
         rcache_rep = -1;
-        if (K > 0) {
-            const Tile t0 = a.tiles[blockIdx.x];
-            nrep = t0.rep; nbeg = t0.begin; nend = t0.end;
-        }
-        for (int j = 0; j < ST_STAGES - 1 && j < K; ++j) issue(j);
+        take(0);
+        for (int j = 0; j < ST_STAGES - 1; ++j) issue(j);
     }
     __syncthreads();
 
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0;; ++k) {
         const int q = k % ST_STAGES;
+        if (stile[q] < 0) break;   // written before the previous barrier: uniform
         // a timed-out wait is folded into the barrier at the end of the tile:
         // the arithmetic on a stage that did not land is memory-safe (every
         // index it forms is bounded) and its results are discarded
@@ -722,7 +731,7 @@ __global__ void __maxnreg__((StRegs<Real, RULE>::n)) k_solvent_staged(StepArgs a
                 atomicOr(a.d_err, ERR_TIMEOUT);
                 // let the copies in flight land before the CTA leaves (bounded)
                 bulk_wait_all();
-                for (int j = k; j < K && j < k + ST_STAGES - 1; ++j)
+                for (int j = k; j < k + ST_STAGES - 1 && stile[j % ST_STAGES] >= 0; ++j)
                     mbar_wait_bounded(&full[j % ST_STAGES], (uint32_t)((j / ST_STAGES) & 1));
             }
             return;
@@ -737,10 +746,8 @@ __global__ void __maxnreg__((StRegs<Real, RULE>::n)) k_solvent_staged(StepArgs a
                     for (int c = 3; c < 6; ++c) bulk_store_ef(garr(c) + beg, S[c], nb);
             }
             bulk_commit();
-            if (k + ST_STAGES - 1 < K) {
-                bulk_wait_read_1();   // the store of tile k - 1 has read the stage that tile k + 2 takes
-                issue(k + ST_STAGES - 1);
-            }
+            if (nt >= 0) bulk_wait_read_1();   // the store of tile k - 1 has read the stage that tile k + 2 takes
+            issue(k + ST_STAGES - 1);
         }
     }
     if (threadIdx.x == 0) bulk_wait_all();
@@ -1251,6 +1258,7 @@ static void launch_staged(const StepArgs &a, LaunchCfg cfg, cudaStream_t s)
     const void *f = (const void *)k_solvent_staged<Real, RULE, FLAGS>;
     smem_opt_in(f, bytes);
     const int grid = resident_grid(f, cfg.grid, cfg.block, bytes);
+    if (a.tile_ctr) cudaMemsetAsync(a.tile_ctr, 0, sizeof(int), s);   // the launch reports any error
     k_solvent_staged<Real, RULE, FLAGS><<<grid, cfg.block, bytes, s>>>(a, cfg.cap);
 }
 

@@ -85,6 +85,7 @@ struct mpcd_ctx {
     int32_t *site_cell = nullptr;
     int64_t *d_step = nullptr;
     int *d_err = nullptr;
+    int *d_tile_ctr = nullptr;      // work counter of the staged solvent pass
     double *d_diag = nullptr;
     int32_t *counts = nullptr, *ex = nullptr, *cursor = nullptr, *scan_bs = nullptr;
     int32_t *rs_hist = nullptr, *rs_ex = nullptr, *rs_bs = nullptr;   // radix-sort digit counts
@@ -257,6 +258,7 @@ StepArgs make_args(const mpcd_ctx *c)
     a.n_sites = c->Nsite;
     a.d_step = c->d_step;
     a.d_err = c->d_err;
+    a.tile_ctr = c->d_tile_ctr;
     a.site_own = c->slab ? 1 : 0;
     a.site_zlo = c->slab_zlo;
     a.site_zhi = c->slab_zhi;
@@ -899,6 +901,7 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     ok &= (c->site_cell = (int32_t *)A(std::max<int64_t>(1, c->Nsite) * 4)) != nullptr;
     ok &= (c->d_step = (int64_t *)A(8)) != nullptr;
     ok &= (c->d_err = (int *)A(8)) != nullptr;
+    ok &= (c->d_tile_ctr = (int *)A(16)) != nullptr;
     ok &= (c->d_diag = (double *)A(16 * 8)) != nullptr;
     ok &= (c->counts = (int32_t *)A(c->C * 4)) != nullptr;
     ok &= (c->ex = (int32_t *)A(c->C * 4)) != nullptr;

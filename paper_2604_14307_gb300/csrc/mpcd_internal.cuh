@@ -137,6 +137,7 @@ struct StepArgs {
     int32_t step_offset;            // added to *d_step by the site PRE pass (1 when it runs
                                     // for the next step before the counter advances)
     int *d_err;
+    int *tile_ctr;                  // tile counter of the staged solvent pass (null: round robin)
     // slab of a decomposed box: only the sites with z in [site_zlo, site_zhi)
     // are binned and transfer their momentum here (site_own = 0: every site)
     int32_t site_own, site_zlo, site_zhi;
