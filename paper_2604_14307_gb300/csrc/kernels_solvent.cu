@@ -1957,15 +1957,28 @@ constexpr int SORT_UNIT = 1024, SORT_UNITS = 2048 / SORT_UNIT;   // units per st
 // rank: destination slot = the cell's first slot + a cursor; the lanes of a
 // warp in one cell take consecutive slots with one atomic.  perm[slot] = the
 // particle's row in its replica.
-template <typename Real>
-__global__ void __launch_bounds__(256) k_sort_rank(StepArgs a, const int32_t *ex, int32_t *cursor, uint32_t *perm)
+// SHIFTED: the cells are those of the next collision (the grid shift of step
+// *d_step + 1, the binning rule of the solvent pass), whose solvent counts the
+// cell words already hold; else the unshifted cells.
+template <typename Real, bool SHIFTED>
+__global__ void __launch_bounds__(256) k_sort_rank(StepArgs a, const int32_t *ex, const int32_t *counts,
+                                                   int32_t *cursor, uint32_t *perm)
 {
     const Real *X = (const Real *)a.x, *Y = (const Real *)a.y, *Z = (const Real *)a.z;
     const unsigned lane = threadIdx.x & 31u;
     const int units = a.n_tiles * SORT_UNITS;
+    const int64_t step1 = *a.d_step + 1;
+    int last_rep = -1;
+    typename ShiftT<Real>::type sh[3] = {};
     for (int w = blockIdx.x; w < units; w += gridDim.x) {   // uniform trip count (warp votes)
         const Tile tl = a.tiles[w / SORT_UNITS];
         const DevReplica r = a.reps[tl.rep];
+        if (SHIFTED && tl.rep != last_rep) {
+            int32_t S[3];
+            grid_shift(r, step1, S);
+            for (int k = 0; k < 3; ++k) sh[k] = shift_as(S[k], typename ShiftT<Real>::type());
+            last_rep = tl.rep;
+        }
         const int64_t i0 = tl.begin + (int64_t)(w % SORT_UNITS) * SORT_UNIT + 4 * threadIdx.x;
         int c[4], base[4];
         bool v[4];
@@ -1977,7 +1990,12 @@ __global__ void __launch_bounds__(256) k_sort_rank(StepArgs a, const int32_t *ex
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             v[j] = i0 + j < tl.end;
-            c[j] = v[j] ? plain_cell(r, x[j], y[j], z[j]) : 0;
+            if (SHIFTED)
+                c[j] = v[j] ? r.cell_base + cell_bin(x[j], sh[0], r.L[0]) +
+                                  r.L[0] * (cell_bin(y[j], sh[1], r.L[1]) + r.L[1] * cell_bin(z[j], sh[2], r.L[2]))
+                            : 0;
+            else
+                c[j] = v[j] ? plain_cell(r, x[j], y[j], z[j]) : 0;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -1995,7 +2013,12 @@ __global__ void __launch_bounds__(256) k_sort_rank(StepArgs a, const int32_t *ex
             const unsigned act = __ballot_sync(0xffffffffu, v[j]);
             if (v[j]) {
                 const int b = __shfl_sync(act, base[j], __ffs(peers[j]) - 1) + __popc(peers[j] & ((1u << lane) - 1u));
-                perm[r.solv_begin + (ex[c[j]] - ex0) + b] = (uint32_t)(i0 + j - r.solv_begin);
+                if (b < counts[c[j]]) {
+                    perm[r.solv_begin + (ex[c[j]] - ex0) + b] = (uint32_t)(i0 + j - r.solv_begin);
+                } else {   // more particles than the cell's count: no access
+                    atomicOr(a.d_err, ERR_INDEX);
+                    atomicCAS(a.d_err + 1, 0, 7);
+                }
             }
         }
     }
@@ -2054,8 +2077,26 @@ __global__ void __launch_bounds__(256) k_sort_gather(StepArgs a, const uint32_t 
     }
 }
 
-void launch_sort_rank_gather(const StepArgs &a, const int32_t *ex, int32_t *cursor, uint32_t *perm,
-                             void *const d[6], uint32_t *dtag, int num_sms, cudaStream_t s)
+// solvent counts of the next collision's cells from the cell words (FP32 form:
+// the high 16 bits of word 0 with the signed low 48 bits taken off)
+__global__ void k_counts_from_words(int64_t C, const long long *w0, int32_t *counts)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        long long n, lo;
+        unpack48(w0[c], n, lo);
+        counts[c] = (int32_t)n;
+    }
+}
+
+void launch_counts_from_words(int64_t C, const void *sums, int32_t *counts, int num_sms, cudaStream_t s)
+{
+    if (C == 0) return;
+    k_counts_from_words<<<num_sms * 8, 256, 0, s>>>(C, reinterpret_cast<const long long *>(sums), counts);
+}
+
+void launch_sort_rank_gather(const StepArgs &a, const int32_t *ex, const int32_t *counts, int32_t *cursor,
+                             uint32_t *perm, void *const d[6], uint32_t *dtag, bool shifted, int num_sms,
+                             cudaStream_t s)
 {
     if (a.n_tiles == 0) return;
     // rank: full occupancy (its atomics' round trips need many warps); gather:
@@ -2063,11 +2104,12 @@ void launch_sort_rank_gather(const StepArgs &a, const int32_t *ex, int32_t *curs
     const int units = a.n_tiles * SORT_UNITS;
     const int grid_r = std::min(units, num_sms * 8), grid_g = std::min(units, num_sms * GATHER_CTAS_PER_SM);
     if (a.precision == 1) {
-        k_sort_rank<float><<<grid_r, 256, 0, s>>>(a, ex, cursor, perm);
+        if (shifted) k_sort_rank<float, true><<<grid_r, 256, 0, s>>>(a, ex, counts, cursor, perm);
+        else k_sort_rank<float, false><<<grid_r, 256, 0, s>>>(a, ex, counts, cursor, perm);
         k_sort_gather<float><<<grid_g, 256, 0, s>>>(a, perm, (float *)d[0], (float *)d[1], (float *)d[2],
                                                     (float *)d[3], (float *)d[4], (float *)d[5], dtag);
     } else {
-        k_sort_rank<double><<<grid_r, 256, 0, s>>>(a, ex, cursor, perm);
+        k_sort_rank<double, false><<<grid_r, 256, 0, s>>>(a, ex, counts, cursor, perm);   // counts by the count pass
         k_sort_gather<double><<<grid_g, 256, 0, s>>>(a, perm, (double *)d[0], (double *)d[1], (double *)d[2],
                                                      (double *)d[3], (double *)d[4], (double *)d[5], dtag);
     }

@@ -529,25 +529,38 @@ int k_rnemd(mpcd_ctx *c, cudaStream_t s, int step_offset, int fix)
     return timed(c, "rnemd", 0, s, [&] { launch_rnemd(a, g, c->num_sms, members, s); });
 }
 
-int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s)
+// Counting sort of the solvent by cell.  from_words (the pipelined step, FP32
+// form, after the solvent pass has binned every particle for the next
+// collision): the cells are those of the next collision and their solvent
+// counts are read from the cell words, so the count pass is skipped; else the
+// unshifted cells, counted.  The order changes no result.
+int do_sort(mpcd_ctx *c, int canonical, cudaStream_t s, bool from_words = false)
 {
     if (c->Ns == 0) return MPCD_OK;
     StepArgs a = make_io_args(c);
     const int nxt = c->cur ^ 1;
-    // algorithmic bytes: positions read by the count and rank passes, the
-    // source index written and read, the state and tags read and written once
-    double bytes = (double)c->Ns * (2.0 * 3.0 * c->realsz + 2.0 * 4.0 + 2.0 * (6.0 * c->realsz + 4.0));
+    const bool words = from_words && !canonical && c->prm.precision == MPCD_P32;
+    // algorithmic bytes: positions read by the count and rank passes (or the
+    // count words), the source index written and read, the state and tags read
+    // and written once
+    double bytes = (double)c->Ns * (3.0 * c->realsz + 2.0 * 4.0 + 2.0 * (6.0 * c->realsz + 4.0)) +
+                   (words ? (double)c->C * (8.0 + 4.0) : (double)c->Ns * 3.0 * c->realsz);
     int e = timed(c, "sort", bytes, s, [&] {
-        cudaMemsetAsync(c->counts, 0, c->C * sizeof(int32_t), s);
         cudaMemsetAsync(c->cursor, 0, c->C * sizeof(int32_t), s);
         cudaMemsetAsync(c->tag[nxt], 0xFF, c->Nslots * sizeof(uint32_t), s);
-        launch_sort_count(a, c->counts, c->num_sms, s);
+        if (words) {
+            launch_counts_from_words(c->C, c->sums, c->counts, c->num_sms, s);
+        } else {
+            cudaMemsetAsync(c->counts, 0, c->C * sizeof(int32_t), s);
+            launch_sort_count(a, c->counts, c->num_sms, s);
+        }
         launch_scan(c->counts, c->ex, c->C, c->scan_bs, s);
         void *dst[6] = {c->sol[nxt][0], c->sol[nxt][1], c->sol[nxt][2],
                         c->sol[nxt][3], c->sol[nxt][4], c->sol[nxt][5]};
         // the permutation lives in the state-transfer record buffer (unused
         // between state transfers; Nslots x 32 bytes)
-        launch_sort_rank_gather(a, c->ex, c->cursor, (uint32_t *)c->rec, dst, c->tag[nxt], c->num_sms, s);
+        launch_sort_rank_gather(a, c->ex, c->counts, c->cursor, (uint32_t *)c->rec, dst, c->tag[nxt], words,
+                                c->num_sms, s);
         if (canonical) launch_sort_canonical(a, dst, c->tag[nxt], c->ex, s);
     });
     if (e) return e;
@@ -650,7 +663,7 @@ int run_steps(mpcd_ctx *c, int64_t n, cudaStream_t s)
             if ((e = k_rnemd(c, s, 1, 1))) break;   // before the collision of step k+1
             CK(c, cudaStreamWaitEvent(s, c->side_ev[1], 0));
             if (c->prm.sort_period >= 0 && ++c->since_sort >= c->tune.sort_period)
-                if ((e = do_sort(c, 0, s))) break;
+                if ((e = do_sort(c, 0, s, true))) break;
         }
         if ((e = k_advance(c, s))) break;
     }

@@ -394,8 +394,11 @@ size_t rnemd_swap_smem();
 void launch_velocity_profile(const StepArgs &a, int bin_axis, int vel_axis, int n_bins, double *mass, double *mom,
                              int num_sms, cudaStream_t s);
 // re-sort by rank (perm[slot] = row in the replica) and gather into d, dtag
-void launch_sort_rank_gather(const StepArgs &a, const int32_t *ex, int32_t *cursor, uint32_t *perm,
-                             void *const d[6], uint32_t *dtag, int num_sms, cudaStream_t s);
+void launch_sort_rank_gather(const StepArgs &a, const int32_t *ex, const int32_t *counts, int32_t *cursor,
+                             uint32_t *perm, void *const d[6], uint32_t *dtag, bool shifted, int num_sms,
+                             cudaStream_t s);
+// counts[c] = solvent members of cell c from the FP32 form's cell word 0
+void launch_counts_from_words(int64_t C, const void *sums, int32_t *counts, int num_sms, cudaStream_t s);
 void launch_sort_canonical(const StepArgs &a, void *const arr[6], uint32_t *tag,
                            const int32_t *offsets, cudaStream_t s);
 size_t scan_block_sums_size(int64_t n);

@@ -331,6 +331,33 @@ def test_staged_and_direct_solvent_passes_agree_bitwise(B, rule):
             assert np.array_equal(getattr(g, k), getattr(ref, k)), (staged, block, tile, k)
 
 
+def test_pipelined_resorts_over_many_replicas_equal_unfused_bitwise(B):
+    """The pipelined step's re-sort orders each replica by the cells of the next
+    collision (its own grid shift), with the counts the cell words hold: over
+    boxes of different edges, with ragged tails, a re-sort every other step gives
+    the state of the unfused sequence bit for bit."""
+    system = I.batched_single_sphere(24, I.P32, seed=6, Ls=(6, 7, 9, 12))
+    system.params.thermostat = 1
+    st = I.initial_state(system)
+    a = B.Simulation(system, sort_period=2)
+    a.set_tuning(block=128, tile=512, ctas_per_sm=2, staged=1)
+    a.set_state(st)
+    a.step(7)
+    ga = a.get_state()
+    b = B.Simulation(system, sort_period=-1)
+    b.set_state(st)
+    for _ in range(7):
+        b.stream()
+        b.couple(B.MPCD_PRE)
+        b.collide()
+        b.couple(B.MPCD_POST)
+    gb = b.get_state()
+    for k in ("x", "v", "R", "q", "P", "Lm"):
+        assert np.array_equal(getattr(ga, k), getattr(gb, k)), k
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("rule", [I.SRD, I.AT])
 def test_launch_forms_agree_bitwise_over_many_replicas(B, rule):
     """Boxes of different edges in one context: a CTA's tiles cross replica
