@@ -2003,18 +2003,26 @@ __global__ void __launch_bounds__(256) k_sort_rank(StepArgs a, const int32_t *ex
             peers[j] = v[j] ? __match_any_sync(act, c[j]) : 0u;
             base[j] = 0;
         }
-        // the leaders' atomics are independent: all four are in flight together
+        // the cells' offsets and counts are read before the atomics (whose
+        // returns the loads could not pass), and the leaders' atomics are
+        // independent: all of them are in flight together
+        const int32_t ex0 = ex[r.cell_base];
+        int32_t off[4], cnt[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            off[j] = v[j] ? ex[c[j]] - ex0 : 0;
+            cnt[j] = v[j] ? counts[c[j]] : 0;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (v[j] && (int)lane == __ffs(peers[j]) - 1) base[j] = atomicAdd(cursor + c[j], __popc(peers[j]));
-        const int32_t ex0 = ex[r.cell_base];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const unsigned act = __ballot_sync(0xffffffffu, v[j]);
             if (v[j]) {
                 const int b = __shfl_sync(act, base[j], __ffs(peers[j]) - 1) + __popc(peers[j] & ((1u << lane) - 1u));
-                if (b < counts[c[j]]) {
-                    perm[r.solv_begin + (ex[c[j]] - ex0) + b] = (uint32_t)(i0 + j - r.solv_begin);
+                if (b < cnt[j]) {
+                    perm[r.solv_begin + off[j] + b] = (uint32_t)(i0 + j - r.solv_begin);
                 } else {   // more particles than the cell's count: no access
                     atomicOr(a.d_err, ERR_INDEX);
                     atomicCAS(a.d_err + 1, 0, 7);
