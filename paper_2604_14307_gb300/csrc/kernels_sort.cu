@@ -317,12 +317,13 @@ __global__ void k_pack_slots(StepArgs a, Real *rec, int64_t nslots)
 
 // get_state gather: host row i from the record of slot vals[i], stored row by row
 template <typename Real>
-__global__ void k_gather_out(const uint32_t *vals, const Real *rec, Real *xa, Real *va, int64_t n_rows,
-                             int64_t nslots, int *err)
+__global__ void k_gather_out(const uint32_t *vals, const Real *rec, Real *xa, Real *va, int64_t row0,
+                             int64_t n_rows, int64_t nslots, int *err)
 {
-    // four records in flight per thread: all loads are issued before any store
+    // rows [row0, n_rows); four records in flight per thread: all loads are
+    // issued before any store
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n_rows; i0 += 4 * stride) {
+    for (int64_t i0 = row0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n_rows; i0 += 4 * stride) {
         Real r[4][6];
         bool ok[4];
 #pragma unroll
@@ -413,20 +414,24 @@ void launch_keys_out(const StepArgs &a, uint32_t *keys, uint32_t *vals, int64_t 
     if (a.n_tiles) k_keys_out<<<a.n_tiles, 256, 0, s>>>(a, keys, vals);
 }
 
-void launch_gather_out(const StepArgs &a, const uint32_t *vals, void *rec, void *xa, void *va, int64_t n_rows,
-                       int64_t nslots, int num_sms, cudaStream_t s)
+void launch_pack_slots(const StepArgs &a, void *rec, int64_t nslots, int num_sms, cudaStream_t s)
 {
-    if (n_rows == 0) return;
-    const int gp = grid_for(nslots, 256, num_sms * 8), grid = grid_for(n_rows, 256, num_sms * 8);
-    if (a.precision == 1) {
-        k_pack_slots<float><<<gp, 256, 0, s>>>(a, (float *)rec, nslots);
-        k_gather_out<float><<<grid, 256, 0, s>>>(vals, (const float *)rec, (float *)xa, (float *)va, n_rows, nslots,
-                                                 a.d_err);
-    } else {
-        k_pack_slots<double><<<gp, 256, 0, s>>>(a, (double *)rec, nslots);
-        k_gather_out<double><<<grid, 256, 0, s>>>(vals, (const double *)rec, (double *)xa, (double *)va, n_rows,
+    const int gp = grid_for(nslots, 256, num_sms * 8);
+    if (a.precision == 1) k_pack_slots<float><<<gp, 256, 0, s>>>(a, (float *)rec, nslots);
+    else k_pack_slots<double><<<gp, 256, 0, s>>>(a, (double *)rec, nslots);
+}
+
+void launch_gather_rows(const StepArgs &a, const uint32_t *vals, const void *rec, void *xa, void *va, int64_t row0,
+                        int64_t row1, int64_t nslots, int num_sms, cudaStream_t s)
+{
+    if (row1 <= row0) return;
+    const int grid = grid_for(row1 - row0, 256, num_sms * 8);
+    if (a.precision == 1)
+        k_gather_out<float><<<grid, 256, 0, s>>>(vals, (const float *)rec, (float *)xa, (float *)va, row0, row1,
+                                                 nslots, a.d_err);
+    else
+        k_gather_out<double><<<grid, 256, 0, s>>>(vals, (const double *)rec, (double *)xa, (double *)va, row0, row1,
                                                   nslots, a.d_err);
-    }
 }
 
 }  // namespace mpcd

@@ -106,6 +106,8 @@ struct mpcd_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t io_stream = nullptr;           // host copies that overlap with kernels
     cudaEvent_t io_ev[2] = {nullptr, nullptr};
+    static constexpr int OUT_CHUNKS = 8;         // egress: row chunks gathered and copied in turn
+    cudaEvent_t out_ev[OUT_CHUNKS + 1] = {};
     cudaStream_t side = nullptr;                // site/body chain beside the solvent pass
     cudaEvent_t side_ev[2] = {nullptr, nullptr};
 
@@ -1012,6 +1014,8 @@ int mpcd_create(const mpcd_params *params, int32_t n_shapes, const mpcd_shape_de
     if (!st && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (!st && cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
     if (!st && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) st = MPCD_ERR_CUDA;
+    for (int k = 0; k <= mpcd_ctx::OUT_CHUNKS && !st; ++k)
+        if (cudaEventCreateWithFlags(&c->out_ev[k], cudaEventDisableTiming) != cudaSuccess) st = MPCD_ERR_CUDA;
     for (int k = 0; k < 2 && !st; ++k) {
         if (cudaEventCreateWithFlags(&c->io_ev[k], cudaEventDisableTiming) != cudaSuccess) st = MPCD_ERR_CUDA;
         if (!st && cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming) != cudaSuccess)
@@ -1041,6 +1045,8 @@ int mpcd_destroy(mpcd_ctx *c)
     if (c->io_stream) cudaStreamDestroy(c->io_stream);
     if (c->side) cudaStreamDestroy(c->side);
     for (auto e : c->io_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto e : c->out_ev)
         if (e) cudaEventDestroy(e);
     for (auto e : c->side_ev)
         if (e) cudaEventDestroy(e);
@@ -1175,13 +1181,32 @@ int mpcd_get_state(mpcd_ctx *c, mpcd_host_state *h, void *stream)
         const int nb = key_bits((uint64_t)c->Ns);
         const int inB =
             launch_radix_sort(kA, vA, kB, vB, c->Nslots, nb, c->rs_hist, c->rs_ex, c->rs_bs, c->d_err, s);
-        launch_gather_out(a, inB ? vB : vA, c->rec, stg, stg + n3 * c->realsz, c->Ns, c->Nslots, c->num_sms, s);
+        launch_pack_slots(a, c->rec, c->Nslots, c->num_sms, s);
+        // the rows leave in chunks: while chunk k travels to the host on the
+        // copy stream, chunk k + 1 is gathered (one chunk for small states)
+        const uint32_t *order = inB ? vB : vA;
+        const int K = c->Ns >= ((int64_t)1 << 22) ? mpcd_ctx::OUT_CHUNKS : 1;
+        char *sx = stg, *sv = stg + n3 * c->realsz;
+        for (int k = 0; k < K && c->Ns; ++k) {
+            const int64_t r0 = c->Ns * k / K, r1 = c->Ns * (k + 1) / K;
+            launch_gather_rows(a, order, c->rec, sx, sv, r0, r1, c->Nslots, c->num_sms, s);
+            const size_t off = (size_t)r0 * 3 * c->realsz, len = (size_t)(r1 - r0) * 3 * c->realsz;
+            if (K == 1) {
+                CK(c, cudaMemcpyAsync(h->x, sx, len, cudaMemcpyDeviceToHost, s));
+                CK(c, cudaMemcpyAsync(h->v, sv, len, cudaMemcpyDeviceToHost, s));
+                continue;
+            }
+            CK(c, cudaEventRecord(c->out_ev[k], s));
+            CK(c, cudaStreamWaitEvent(c->io_stream, c->out_ev[k], 0));
+            CK(c, cudaMemcpyAsync((char *)h->x + off, sx + off, len, cudaMemcpyDeviceToHost, c->io_stream));
+            CK(c, cudaMemcpyAsync((char *)h->v + off, sv + off, len, cudaMemcpyDeviceToHost, c->io_stream));
+        }
+        if (K > 1) {
+            CK(c, cudaEventRecord(c->out_ev[mpcd_ctx::OUT_CHUNKS], c->io_stream));
+            CK(c, cudaStreamWaitEvent(s, c->out_ev[mpcd_ctx::OUT_CHUNKS], 0));
+        }
     }
     CK(c, cudaGetLastError());
-    if (c->Ns) {
-        CK(c, cudaMemcpyAsync(h->x, stg, n3 * c->realsz, cudaMemcpyDeviceToHost, s));
-        CK(c, cudaMemcpyAsync(h->v, stg + n3 * c->realsz, n3 * c->realsz, cudaMemcpyDeviceToHost, s));
-    }
     std::vector<DevBody> hb(std::max<int64_t>(1, c->B));
     if (c->B) CK(c, cudaMemcpyAsync(hb.data(), c->d_bodies, c->B * sizeof(DevBody), cudaMemcpyDeviceToHost, s));
     int e = check_device_error(c, s);

@@ -425,9 +425,11 @@ void launch_gather_in(const StepArgs &a, const void *rec, const uint32_t *vals, 
                       int num_sms, cudaStream_t s);
 void launch_keys_out(const StepArgs &a, uint32_t *keys, uint32_t *vals, int64_t nslots, uint32_t n_rows,
                      cudaStream_t s);
-// slots -> records rec[nslots][8], then host rows in order from them
-void launch_gather_out(const StepArgs &a, const uint32_t *vals, void *rec, void *xa, void *va, int64_t n_rows,
-                       int64_t nslots, int num_sms, cudaStream_t s);
+// slots -> records rec[nslots][8]; then the host rows [row0, row1) in order
+// from them (vals[row] = the row's slot)
+void launch_pack_slots(const StepArgs &a, void *rec, int64_t nslots, int num_sms, cudaStream_t s);
+void launch_gather_rows(const StepArgs &a, const uint32_t *vals, const void *rec, void *xa, void *va, int64_t row0,
+                        int64_t row1, int64_t nslots, int num_sms, cudaStream_t s);
 
 // angular-momentum-conserving collision variants (kernels_angular.cu for the
 // solvent and the per-cell solve, kernels_bodies.cu for the sites).

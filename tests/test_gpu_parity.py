@@ -389,10 +389,13 @@ def test_state_round_trip_is_exact(B, prec):
     """mpcd_set_state stores the solvent cell-sorted (radix sort of (cell, row)
     pairs, then a gather) and mpcd_get_state brings it back to row order (radix
     sort of (row, slot) pairs): with no step in between the round trip is the
-    identity, for uneven replicas with ragged tails and a box large enough for
-    three digit passes."""
+    identity, for uneven replicas with ragged tails, a box large enough for
+    three digit passes and one large enough for the chunked egress (rows gathered
+    and copied to the host in eight chunks)."""
     for system in (I.batched_single_sphere(n_rep=5, precision=prec, seed=6, Ls=(6, 8, 12)),
-                   I.suspension(60, 10.0, 0.1, 4.0, 3, 10.0, I.SRD, 1, prec, seed=2, name="rt")):
+                   I.suspension(60, 10.0, 0.1, 4.0, 3, 10.0, I.SRD, 1, prec, seed=2, name="rt"),
+                   # 4.4 M solvent particles: the egress gathers and copies in row chunks
+                   I.suspension(76, 10.0, 0.05, 4.0, 3, 10.0, I.SRD, 1, prec, seed=3, name="rt_big")):
         system.replicas[0].n_solvent -= 5
         st = I.initial_state(system)
         sim = B.Simulation(system)
