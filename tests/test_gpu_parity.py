@@ -405,3 +405,28 @@ def test_state_round_trip_is_exact(B, prec):
         real = np.float32 if prec == I.P32 else np.float64
         assert np.array_equal(g.x, st.x.astype(real)) and np.array_equal(g.v, st.v.astype(real))
         assert np.array_equal(g.R, st.R) and np.array_equal(g.P, st.P)
+
+
+def test_resorts_per_call_follow_the_fused_pass_count(B):
+    """A call of n steps runs n - 1 fused passes, each of which counts towards
+    the next re-sort, so from `since` passes after a re-sort it re-sorts
+    (since + n - 1) // period times and ends at (since + n - 1) % period;
+    bench.py places its timed call in the replay cycle by this rule."""
+    system = I.suspension(24, 5.0, 0.1, 2.0, 2, 5.0, I.SRD, 1, I.P32, seed=3, name="phase")
+    st = I.initial_state(system)
+    sim = B.Simulation(system)
+    sim.set_state(st)
+    period = 4
+    sim.set_tuning(sort_period=period)
+    sim.sort()
+    since = 0
+    for n in (3, 5, 2, 7, 4, 9, 1, 6):
+        sim.set_profiling(True)
+        sim.reset_profile()
+        sim.step(n)
+        prof = sim.profile()
+        sim.set_profiling(False)
+        got = prof["sort"]["launches"] if "sort" in prof else 0
+        assert got == (since + n - 1) // period, (since, n, got)
+        since = (since + n - 1) % period
+    sim.close()
