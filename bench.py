@@ -355,6 +355,37 @@ def run_reference(a, ws, rank):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def place_timed_call(step_call, steps: int, period: int) -> int:
+    """Run `step_call` (one mpcd_step(steps) call) from the state right after a
+    re-sort until the next call replays a recorded graph and holds its share of
+    re-sorts; returns that share.
+
+    mpcd_step(n) replays a CUDA graph keyed by (n, solvent buffer parity,
+    passes since the last re-sort); a call of n steps runs n - 1 fused passes,
+    each counting towards the next re-sort, so from `since` it re-sorts
+    (since + n - 1) // period times (each flips the parity) and ends at
+    (since + n - 1) % period.  First every key of the replay cycle is recorded;
+    then, since the call right after the re-sort would hold none, the phase is
+    moved within the cycle until the call holds ceil((n - 1) / period)."""
+    since, par, seen = 0, 0, set()
+
+    def advance():
+        nonlocal since, par
+        step_call()
+        par ^= ((since + steps - 1) // period) & 1
+        since = (since + steps - 1) % period
+
+    while steps >= 2 and (since, par) not in seen:
+        seen.add((since, par))
+        advance()
+    resorts = -(-(steps - 1) // period) if steps >= 2 else 0
+    for _ in range(2 * period):   # the cycle reaches such a phase (since = period - gcd)
+        if steps < 2 or (since + steps - 1) // period >= resorts:
+            break
+        advance()
+    return resorts
+
+
 def main():
     a = args_()
     ws, rank, local = dist_env()
@@ -423,31 +454,11 @@ def main():
     else:
         tuning = sim.tuning() if a.no_tune else sim.autotune(steps_per_trial=10)
     sim.step(a.warmup)
-    # mpcd_step(n) replays a CUDA graph keyed by (n, solvent buffer parity,
-    # steps since the last re-sort); a call of n steps counts n - 1 of them
-    # towards the next re-sort (the last step's pass is not a fused one), so
-    # after a re-sort the keys of repeated n-step calls cycle with a period of
-    # at most twice the sort period: recording every graph of the cycle before
-    # the timed call makes that call a replay
+    # every graph of the replay cycle is recorded and the timed call placed so
+    # that it replays graphs and holds its share of re-sorts
     sim.sort()
     period = max(1, int(tuning["sort_period"]))
-    since, par, seen = 0, 0, set()
-    while a.steps >= 2 and (since, par) not in seen:
-        seen.add((since, par))
-        sim.step(a.steps)
-        par ^= ((since + a.steps - 1) // period) & 1
-        since = (since + a.steps - 1) % period
-    # a call from `since` re-sorts (since + steps - 1) // period times; the call
-    # right after the explicit re-sort above would hold none, so the phase is
-    # moved (within the recorded cycle) until the timed call holds its share,
-    # ceil((steps - 1) / period) re-sorts
-    resorts = -(-(a.steps - 1) // period) if a.steps >= 2 else 0
-    for _ in range(2 * period):   # the cycle reaches such a phase (since = period - gcd)
-        if a.steps < 2 or (since + a.steps - 1) // period >= resorts:
-            break
-        sim.step(a.steps)
-        par ^= ((since + a.steps - 1) // period) & 1
-        since = (since + a.steps - 1) % period
+    resorts = place_timed_call(lambda: sim.step(a.steps), a.steps, period)
     torch.cuda.synchronize()
 
     # ------------------------------------------------------- timed (graph)
